@@ -1,0 +1,318 @@
+"""Benchmark: shift-system solves/s at relative residual 1e-10 on one GB300.
+
+Workload (N = 1): the 16^3x32 FP64 multi-shift solve of the ND twisted-mass
+doublet (kappa 0.16, mu_bar 0.1, eps_bar 0.11, antiperiodic time, seeded
+SU(3) links with roughness 0.5), 12 shifts log-spaced in 1e-5..2, one
+Gaussian right-hand side, rho = 1e-10.  A step is one complete multi-shift CG
+solve (all shifts, with the FP64 true-residual certification).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tmnd|reference]
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+this method here) on the host cores, on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank solves its own right-hand side (replicas: the
+path has no data exchange between independent solves); value = all ranks'
+solves / max-over-ranks time.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (32, 16, 16, 16)            # T, X, Y, Z
+KAPPA, MU_BAR, EPS_BAR = 0.16, 0.1, 0.11
+ROUGHNESS = 0.5
+GAUGE_SEED, RHS_SEED = 1002, 2032
+NSHIFT, SIG_LO, SIG_HI = 12, 1e-5, 2.0
+RHO = 1e-10
+METRIC = "shift-system solves/sec at rel. residual 1e-10"
+WORKLOAD = "16^3x32 ND twisted-mass doublet, FP64 multi-shift CG, 12 shifts 1e-5..2, 1 RHS, rho 1e-10"
+L2_FLUSH_BYTES = 512 << 20         # > 129 MB L2
+
+# Algorithmic counts per odd site for ONE stencil launch (both flavours):
+#   flops: 2 x 1320 (Wilson hop with spin projection, 8 directions) + 240 (A^-1 or A site term)
+#   bytes (FP64, 18-real links): even launch 240 reals (in 48, links 144, out 48),
+#   odd launch 288 reals (t 48, psi 48, links 144, out 48)
+HOP_FLOP_PER_SITE = 2 * 1320 + 240
+HOP_BYTES_PER_SITE = (240 + 288) / 2 * 8
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_tmnd(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1805_09584_gb300 as tm
+    import synth
+    from paper_1805_09584_gb300 import _build
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    _build.build()
+
+    U = synth.random_su3_field(DIMS, ROUGHNESS, GAUGE_SEED)
+    b_host = synth.gaussian_rhs(DIMS, RHS_SEED + rank)[0]
+    sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
+    g = tm.Gauge(U, DIMS, KAPPA, MU_BAR, EPS_BAR)
+    stream = torch.cuda.current_stream()
+    b_dev = g.pack(torch.from_numpy(b_host).cuda())
+    xs = [g.spinor() for _ in sig]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(profile=False):
+        return tm.mms_cg_solve(g.handle, b_dev, 1, sig, xs, rho=RHO, profile=profile, stream=stream)
+
+    for _ in range(args.warmup):
+        info = step()
+    # ---- timed region: K solves, L2 flushed between solves
+    sampler = ClockSampler(local)
+    infos = []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        infos.append(step(profile=True))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_all = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    solves = args.steps * NSHIFT * ws
+    value = solves / (ms_all / 1e3)
+    worst_res = max(max(i["true_res"]) for i in infos)
+    iters = infos[-1]["iters"]
+
+    # ---- e2e: the public API with host buffers (pinned b in, all x_i out, per step)
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    x_pin = torch.empty((NSHIFT, g.vh, 2, 4, 3), dtype=torch.complex128).pin_memory()
+    b_can = torch.empty((1, g.vh, 2, 4, 3), dtype=torch.complex128, device="cuda")
+    x_can = torch.empty((1, g.vh, 2, 4, 3), dtype=torch.complex128, device="cuda")
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        b_can.copy_(b_pin, non_blocking=True)
+        tm.tmnd_spinor_pack(g.handle, b_dev, b_can, 1, stream)
+        tm.mms_cg_solve(g.handle, b_dev, 1, sig, xs, rho=RHO, stream=stream)
+        for i in range(NSHIFT):
+            tm.tmnd_spinor_unpack(g.handle, x_can, xs[i], 1, stream)
+            x_pin[i].copy_(x_can[0], non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = solves / (e2e_ms / 1e3)
+    h2d = b_host.nbytes
+    d2h = NSHIFT * b_host.nbytes
+
+    # ---- roofline of the dominant kernel (the FP64 stencil launches), live events
+    hop_ms = sum(i["hop_ms"] for i in infos)
+    n_hop_launch = 4 * sum(i["iters"] for i in infos)
+    hop_avg_s = hop_ms / 1e3 / n_hop_launch
+    flop_per_launch = HOP_FLOP_PER_SITE * g.vh
+    achieved_tflops = flop_per_launch / hop_avg_s / 1e12
+    fp64_peak = FP64_PEAK_TFLOPS
+    upd_ms = sum(i["update_ms"] for i in infos)
+    launches = sum(i["launches"] for i in infos)
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "16^3x32", "nshift": NSHIFT, "nrhs": 1,
+                       "rho": RHO, "kappa": KAPPA, "mu_bar": MU_BAR, "eps_bar": EPS_BAR, "roughness": ROUGHNESS,
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "flushed between steps (512 MB write); solve working set > L2"},
+            "iters": iters, "max_true_rel_residual": worst_res,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "alu", "kernel": "k_hop_even/k_hop_odd (FP64 stencil)",
+                         "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / fp64_peak, "traffic": None,
+                         "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                         "hop_share_of_step": hop_ms / ms,
+                         "hop_achieved_gbs": HOP_BYTES_PER_SITE * g.vh / hop_avg_s / 1e9,
+                         "hbm_peak_gbs": _peaks().get("hbm_gbs")},
+            "update_share_of_step": upd_ms / ms,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+    g.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+# FP64 peak of a GB300 (sm_103a): 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def cpu_baseline(iters_full: int, sample_iters: int = 6):
+    """The oracle, as it stands, on the host cores: `sample_iters` MMS-CG
+    iterations of the same workload, scaled to a full solve of `iters_full`
+    iterations (the oracle's own count for this workload, tests/golden)."""
+    import oracle
+    import synth
+    U = synth.random_su3_field(DIMS, ROUGHNESS, GAUGE_SEED)
+    b = synth.gaussian_rhs(DIMS, RHS_SEED)[0]
+    sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
+    act = oracle.action(DIMS, KAPPA, MU_BAR, EPS_BAR)
+    t = time.perf_counter()
+    oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=sample_iters)
+    el = time.perf_counter() - t
+    per_iter = el / sample_iters
+    return {"value": NSHIFT / (per_iter * iters_full), "unit": "solves/s", "cores": oracle.nthreads(),
+            "kind": "oracle",
+            "sample": f"{sample_iters} MMS-CG iterations of the full 16^3x32 12-shift solve "
+                      f"({el:.1f} s), scaled to the oracle's full solve of {iters_full} iterations"}
+
+
+def oracle_full_iters():
+    p = os.path.join(ROOT, "tests", "golden", "mms_16x16x16x32.json")
+    try:
+        with open(p) as f:
+            return int(json.load(f)["iters"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    iters_full = oracle_full_iters()
+    if iters_full is None:
+        return {"impl": "reference", "unavailable": "oracle iteration count for the workload not recorded"}
+    import oracle
+    import synth
+    U = synth.random_su3_field(DIMS, ROUGHNESS, GAUGE_SEED)
+    b = synth.gaussian_rhs(DIMS, RHS_SEED)[0]
+    sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
+    act = oracle.action(DIMS, KAPPA, MU_BAR, EPS_BAR)
+    sample = 2
+    for _ in range(args.warmup):
+        oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=sample)
+    el = time.perf_counter() - t
+    per_iter = el / (args.steps * sample)
+    value = NSHIFT / (per_iter * iters_full)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * iters_full * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "16^3x32", "nshift": NSHIFT, "nrhs": 1, "rho": RHO},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle.nthreads(), "kind": "oracle",
+                             "sample": f"each step: {sample} MMS-CG iterations of the full workload, scaled to "
+                                       f"the oracle's {iters_full}-iteration solve"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tmnd", choices=["tmnd", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    out = run_tmnd(args)
+    ws, rank, _ = _dist()
+    if rank == 0 and out is not None:
+        if ws == 1 and not args.no_cpu_baseline:
+            itf = oracle_full_iters() or out["iters"]
+            out["cpu_baseline"] = cpu_baseline(itf)
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

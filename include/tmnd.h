@@ -1,0 +1,169 @@
+/*
+ * tmnd.h — C ABI of libtmnd.so: GB300 (sm_103a) kernels for the shifted
+ * systems (Qhat^2 + sigma_i) x_i = b of the even-odd reduced, non-degenerate
+ * twisted-mass Wilson operator (arXiv:1805.09584).
+ *
+ * Operator (Sec. 2, Eqs. "non-degenerate" and "Wilson" with c_sw = 0), in the
+ * hopping-parameter normalisation (2 kappa times the paper's form, with
+ * m + 4 = 1/(2 kappa)):
+ *     D   = 1 - kappa H + 2 i kappa mu_bar (gamma_5 (x) tau_3) - 2 kappa eps_bar (1 (x) tau_1)
+ *     H psi(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu)
+ *     Mhat = A - kappa^2 H_oe A^-1 H_eo          (even-odd Schur complement on odd sites, Sec. 2)
+ *     A    = 1 + 2 i kappa mu_bar gamma_5 tau_3 - 2 kappa eps_bar tau_1
+ *     Qhat = (gamma_5 (x) tau_1) Mhat,  Qhat^2 = Mhat^+ Mhat     (Eq. "g5tau1-hermiticity")
+ * Gamma matrices: chiral basis, gamma_5 = diag(1,1,-1,-1) (Sec. 2);
+ * gamma_0 = [[0,-1],[-1,0]], gamma_k = [[0,-i sigma_k],[i sigma_k,0]] in 2x2 blocks.
+ * Lattice: dims = {T, X, Y, Z}, all even, mu = 0 is time; periodic in space,
+ * antiperiodic in time when `antiperiodic_t` is set.  Site parity is
+ * (t+x+y+z) & 1; the reduced system lives on the odd sites.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are caller-owned (e.g. torch tensors' data_ptr()).  The
+ *     library owns only the gauge handle, its packed links and a grow-only
+ *     workspace inside the handle.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     stream-ordered and asynchronous unless stated otherwise.
+ *   - Errors are returned as tmnd_status, never by aborting; a message is
+ *     available from tmnd_last_error() (thread-local).  Invalid input is
+ *     rejected with TMND_ERR_ARG before anything is launched.
+ *   - A gauge handle may be used by one host thread at a time.
+ *
+ * Layouts
+ *   canonical links (host) : complex128 [4][T][X][Y][Z][3][3], row-major, mu slowest.
+ *   canonical spinor       : complex128 [nrhs][V/2][2 flavour][4 spin][3 colour]
+ *                            on odd sites; odd half-index = lex >> 1 with
+ *                            lex = ((t*X + x)*Y + y)*Z + z.
+ *   internal spinor (TMND_F64): per right-hand side, 24 planes of V/2
+ *                            complex128 values, plane c = flavour*12 + spin*3 + colour,
+ *                            i.e. element (c, h) at offset (c * V/2 + h) complex
+ *                            numbers; right-hand sides follow one another.
+ *                            tmnd_spinor_bytes() gives the size of one.
+ */
+#ifndef TMND_H
+#define TMND_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TMND_OK = 0,
+    TMND_ERR_ARG = 1,      /* invalid argument (odd dims, sigma <= 0, bad pointer alignment, ...) */
+    TMND_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+    TMND_ERR_OOM = 3,      /* device allocation failed */
+    TMND_ERR_NOCONV = 4,   /* solver reached maxiter before every required shift converged */
+    TMND_ERR_NAN = 5,      /* NaN/Inf met in a reduction */
+    TMND_ERR_TIMEOUT = 6,  /* a bounded wait gave up */
+    TMND_ERR_NOTSU3 = 7    /* a link failed the SU(3) check at gauge creation */
+} tmnd_status;
+
+typedef enum {
+    TMND_F64 = 0           /* FP64 storage and arithmetic */
+} tmnd_prec;
+
+typedef enum {
+    TMND_OP_MHAT = 0,      /* out = Mhat in                            (Sec. 2 even-odd reduction) */
+    TMND_OP_MHAT_DAG = 1,  /* out = Mhat^+ in                          */
+    TMND_OP_QHAT2 = 2,     /* out = (Mhat^+ Mhat + sigma) in           (Eq. "shifted_linear") */
+    TMND_OP_QHAT = 3       /* out = (gamma_5 (x) tau_1) Mhat in         (Eq. "g5tau1-hermiticity") */
+} tmnd_op;
+
+typedef struct {
+    int dims[4];           /* {T, X, Y, Z}: each even and >= 2; V/2 < 2^31 */
+    double kappa;          /* hopping parameter, m + 4 = 1/(2 kappa) */
+    double mu_bar;         /* twisted mass mu_bar of Eq. "non-degenerate" */
+    double eps_bar;        /* mass splitting eps_bar of Eq. "non-degenerate" */
+    int antiperiodic_t;    /* 1: antiperiodic time boundary */
+} tmnd_action;
+
+typedef struct tmnd_gauge tmnd_gauge;
+
+/* Create a gauge handle on the current CUDA device.  Copies `host_links`
+ * (canonical layout, host memory, read only during the call) to the device
+ * and packs it per parity and direction.  Every link is checked on the host
+ * to be SU(3) (|U U^+ - 1| and |det U - 1| below 1e-10); a failing link gives
+ * TMND_ERR_NOTSU3.  Synchronous.  (Sec. 2: U_mu(x) in SU(3).) */
+tmnd_status tmnd_gauge_create(const double *host_links, const tmnd_action *act, int prec,
+                              tmnd_gauge **out);
+
+/* Release the handle and all device memory it owns.  Synchronises the device. */
+void tmnd_gauge_destroy(tmnd_gauge *g);
+
+/* Bytes of one internal spinor (one right-hand side) for this handle. */
+size_t tmnd_spinor_bytes(const tmnd_gauge *g);
+
+/* canonical (device) -> internal (device), nrhs right-hand sides.  The two
+ * buffers must not overlap.  Layouts as above. */
+tmnd_status tmnd_spinor_pack(const tmnd_gauge *g, void *dev_internal, const void *dev_canonical,
+                             int nrhs, void *stream);
+
+/* internal (device) -> canonical (device). */
+tmnd_status tmnd_spinor_unpack(const tmnd_gauge *g, void *dev_canonical, const void *dev_internal,
+                               int nrhs, void *stream);
+
+/* out = op(in) for nrhs internal spinors (see tmnd_op).  `sigma` is used by
+ * TMND_OP_QHAT2 only.  `out` and `in` must not overlap.  Uses the handle's
+ * workspace (one even-site and one odd-site spinor), growing it on first use.
+ * (Sec. 2 even-odd Schur complement; Eq. "g5tau1-hermiticity".) */
+tmnd_status tm_nd_apply(tmnd_gauge *g, void *out, const void *in, int op, double sigma,
+                        int nrhs, void *stream);
+
+#define TMND_MAX_SHIFTS 32
+
+typedef struct {
+    double rho;            /* stop shift i when its residual |r_i| <= rho |b| (Sec. 3.1 criterion) */
+    int maxiter;           /* iteration cap; TMND_ERR_NOCONV if reached */
+    int nsolve;            /* the first nsolve shifts must converge; the base system is
+                              sigma[nsolve-1]; shifts after it are guess shifts (Sec. 4.2.2)
+                              iterated along, never required to converge.  0 = all. */
+    int check_every;       /* iterations between host convergence checks (0 = 32) */
+    int profile;           /* 1: time the stencil and update kernels of every iteration with
+                              CUDA events (filled into hop_ms / update_ms) */
+} tmnd_solve_params;
+
+typedef struct {
+    int iters;                             /* Krylov iterations of the base system */
+    int conv_iter[TMND_MAX_SHIFTS];        /* iteration after which shift i froze, -1 if never */
+    double true_res[TMND_MAX_SHIFTS];      /* |b - (Qhat^2 + sigma_i) x_i| / |b|, FP64, recomputed
+                                              with the operator after the solve (max over RHS) */
+    double zeta[TMND_MAX_SHIFTS];          /* final zeta_i of the recursion (last RHS) */
+    double hop_ms;                         /* profile: device time of the 4 stencil launches per
+                                              iteration, summed over iterations and RHS */
+    double update_ms;                      /* profile: device time of the scalar + multi-shift
+                                              update launches, summed likewise */
+    long long launches;                    /* kernels this call launched (early-exit ones included) */
+} tmnd_solve_info;
+
+/* Multi-mass-shift CG (Sec. 1 "standard" solver; Sec. 4.2.2) for
+ * (Qhat^2 + sigma_i) x_i = b, i < nshift, for each of nrhs right-hand sides.
+ *   b      : device, nrhs internal spinors (read only)
+ *   sigma  : host, nshift values, strictly descending, > 0 (descending order of Sec. 4.2.1)
+ *   x      : host array of nshift device pointers; x[i] holds nrhs internal
+ *            spinors and receives the solutions (overwritten, no initial guess)
+ *   info   : may be NULL
+ * Returns after the solve has finished (synchronous on `stream`).  Uses the
+ * handle's workspace (4 + nshift spinors per right-hand side). */
+tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, const double *sigma, int nshift,
+                         void *const *x, const tmnd_solve_params *params, tmnd_solve_info *info,
+                         void *stream);
+
+/* Lagrange-interpolated initial guess (Sec. 4.2.1; App. B):
+ *   out = sum_{j<k} l_j(target) xs[j],   l_j(m) = prod_{i != j} (m - m_i)/(m_j - m_i)
+ * with the weights computed on the host in FP64 over `nodes` (host, k distinct
+ * shifts, 1 <= k <= 8) and the combination done on the device.
+ *   xs  : host array of k device pointers, each nrhs internal spinors
+ *   out : device, nrhs internal spinors (may not alias any xs[j])
+ *   lebesgue_out : host, may be NULL; receives gamma_k(target) = sum |l_j|. */
+tmnd_status lagrange_guess(const tmnd_gauge *g, const double *nodes, const void *const *xs, int k,
+                           double target, void *out, int nrhs, double *lebesgue_out, void *stream);
+
+/* Message for the last error on this host thread ("" if none). */
+const char *tmnd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMND_H */

@@ -1,0 +1,212 @@
+"""GB300 (sm_103a) kernels for the shifted systems of the non-degenerate
+twisted-mass operator (arXiv:1805.09584): the even-odd Schur stencil, the
+multi-mass-shift CG and Lagrange-interpolated guesses.
+
+This module is the thin Python binding of `libtmnd.so` (C ABI in
+`include/tmnd.h`): argument marshalling only, every step runs in the CUDA
+library.  PyTorch tensors (or raw integer device addresses) provide device
+memory; streams are passed as `cudaStream_t` handles.  There is no CPU
+fallback: if the library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtmnd.so")
+MAX_SHIFTS = 32
+
+TMND_F64 = 0
+OP_MHAT, OP_MHAT_DAG, OP_QHAT2, OP_QHAT = 0, 1, 2, 3
+
+STATUS = {0: "TMND_OK", 1: "TMND_ERR_ARG", 2: "TMND_ERR_CUDA", 3: "TMND_ERR_OOM", 4: "TMND_ERR_NOCONV",
+          5: "TMND_ERR_NAN", 6: "TMND_ERR_TIMEOUT", 7: "TMND_ERR_NOTSU3"}
+
+# every entry point declared in include/tmnd.h
+EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd_spinor_pack",
+           "tmnd_spinor_unpack", "tm_nd_apply", "mms_cg_solve", "lagrange_guess", "tmnd_last_error")
+
+
+class TmndError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Action(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("kappa", ctypes.c_double), ("mu_bar", ctypes.c_double),
+                ("eps_bar", ctypes.c_double), ("antiperiodic_t", ctypes.c_int)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("maxiter", ctypes.c_int), ("nsolve", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("conv_iter", ctypes.c_int * MAX_SHIFTS),
+                ("true_res", ctypes.c_double * MAX_SHIFTS), ("zeta", ctypes.c_double * MAX_SHIFTS),
+                ("hop_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("launches", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtmnd.so (built in-tree by `__graft_entry__.build()`); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                              "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.tmnd_gauge_create.argtypes = [vp, ctypes.POINTER(Action), i, ctypes.POINTER(vp)]
+        L.tmnd_gauge_destroy.argtypes = [vp]
+        L.tmnd_gauge_destroy.restype = None
+        L.tmnd_spinor_bytes.argtypes = [vp]
+        L.tmnd_spinor_bytes.restype = ctypes.c_size_t
+        L.tmnd_spinor_pack.argtypes = [vp, vp, vp, i, vp]
+        L.tmnd_spinor_unpack.argtypes = [vp, vp, vp, i, vp]
+        L.tm_nd_apply.argtypes = [vp, vp, vp, i, d, i, vp]
+        L.mms_cg_solve.argtypes = [vp, vp, i, ctypes.POINTER(d), i, ctypes.POINTER(vp),
+                                   ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp]
+        L.lagrange_guess.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(vp), i, d, vp, i,
+                                     ctypes.POINTER(d), vp]
+        L.tmnd_last_error.restype = ctypes.c_char_p
+        for name in ("tmnd_gauge_create", "tmnd_spinor_pack", "tmnd_spinor_unpack", "tm_nd_apply",
+                     "mms_cg_solve", "lagrange_guess"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise TmndError(status, lib().tmnd_last_error().decode(errors="replace"))
+
+
+def _ptr(t) -> int:
+    """Device address of a tensor (anything with data_ptr()) or a raw integer."""
+    if t is None:
+        return 0
+    return int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def make_action(dims, kappa, mu_bar, eps_bar, antiperiodic_t=True) -> Action:
+    a = Action()
+    for k in range(4):
+        a.dims[k] = int(dims[k])
+    a.kappa, a.mu_bar, a.eps_bar = float(kappa), float(mu_bar), float(eps_bar)
+    a.antiperiodic_t = int(bool(antiperiodic_t))
+    return a
+
+
+# ------------------------------------------------------------ C-ABI mirror
+def tmnd_gauge_create(host_links: np.ndarray, act: Action, prec: int = TMND_F64) -> ctypes.c_void_p:
+    links = np.ascontiguousarray(host_links, dtype=np.complex128)
+    h = ctypes.c_void_p()
+    _check(lib().tmnd_gauge_create(links.ctypes.data, ctypes.byref(act), int(prec), ctypes.byref(h)))
+    return h
+
+
+def tmnd_gauge_destroy(h) -> None:
+    lib().tmnd_gauge_destroy(h)
+
+
+def tmnd_spinor_bytes(h) -> int:
+    return int(lib().tmnd_spinor_bytes(h))
+
+
+def tmnd_spinor_pack(h, dev_internal, dev_canonical, nrhs: int = 1, stream=None) -> None:
+    _check(lib().tmnd_spinor_pack(h, _ptr(dev_internal), _ptr(dev_canonical), int(nrhs), _stream(stream)))
+
+
+def tmnd_spinor_unpack(h, dev_canonical, dev_internal, nrhs: int = 1, stream=None) -> None:
+    _check(lib().tmnd_spinor_unpack(h, _ptr(dev_canonical), _ptr(dev_internal), int(nrhs), _stream(stream)))
+
+
+def tm_nd_apply(h, out, inp, op: int, sigma: float = 0.0, nrhs: int = 1, stream=None) -> None:
+    _check(lib().tm_nd_apply(h, _ptr(out), _ptr(inp), int(op), float(sigma), int(nrhs), _stream(stream)))
+
+
+def mms_cg_solve(h, b, nrhs: int, sigma, x, rho: float = 1e-10, maxiter: int = 100000, nsolve: int = 0,
+                 check_every: int = 0, profile: bool = False, stream=None) -> dict:
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    ns = len(sig)
+    xs = (ctypes.c_void_p * ns)(*[_ptr(v) for v in x])
+    p = SolveParams(float(rho), int(maxiter), int(nsolve), int(check_every), int(bool(profile)))
+    info = SolveInfo()
+    st = lib().mms_cg_solve(h, _ptr(b), int(nrhs), sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns, xs,
+                            ctypes.byref(p), ctypes.byref(info), _stream(stream))
+    out = {"status": st, "iters": info.iters, "conv_iter": list(info.conv_iter[:ns]),
+           "true_res": list(info.true_res[:ns]), "zeta": list(info.zeta[:ns]),
+           "hop_ms": info.hop_ms, "update_ms": info.update_ms, "launches": info.launches}
+    _check(st)
+    return out
+
+
+def lagrange_guess(h, nodes, xs, target: float, out, nrhs: int = 1, stream=None) -> float:
+    nd = np.ascontiguousarray(nodes, dtype=np.float64)
+    k = len(nd)
+    arr = (ctypes.c_void_p * k)(*[_ptr(v) for v in xs])
+    leb = ctypes.c_double()
+    _check(lib().lagrange_guess(h, nd.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), arr, k, float(target),
+                                _ptr(out), int(nrhs), ctypes.byref(leb), _stream(stream)))
+    return leb.value
+
+
+# ------------------------------------------------------------ conveniences
+class Gauge:
+    """Owns a tmnd_gauge handle (created from canonical host links)."""
+
+    def __init__(self, host_links, dims, kappa, mu_bar, eps_bar, antiperiodic_t=True, prec=TMND_F64):
+        self.dims = tuple(int(d) for d in dims)
+        self.vh = int(np.prod(self.dims)) // 2
+        self.act = make_action(dims, kappa, mu_bar, eps_bar, antiperiodic_t)
+        self.handle = tmnd_gauge_create(host_links, self.act, prec)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            tmnd_gauge_destroy(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spinor(self, nrhs: int = 1, device="cuda"):
+        """A new internal-layout spinor buffer (torch complex128, nrhs * 24 * V/2)."""
+        import torch
+        return torch.empty(nrhs * 24 * self.vh, dtype=torch.complex128, device=device)
+
+    def pack(self, canonical, nrhs: int = 1, stream=None):
+        out = self.spinor(nrhs, canonical.device)
+        tmnd_spinor_pack(self.handle, out, canonical, nrhs, stream)
+        return out
+
+    def unpack(self, internal, nrhs: int = 1, stream=None):
+        import torch
+        out = torch.empty((nrhs, self.vh, 2, 4, 3), dtype=torch.complex128, device=internal.device)
+        tmnd_spinor_unpack(self.handle, out, internal, nrhs, stream)
+        return out

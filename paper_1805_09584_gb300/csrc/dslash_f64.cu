@@ -1,0 +1,301 @@
+// FP64 hopping kernels for the even-odd reduced ND twisted-mass operator.
+//
+//   even kernel:  t_e = kappa^2 A^-1 H_eo psi_o
+//   odd  kernel:  y_o = A psi_o - H_oe t_e                 => y = Mhat psi  (Sec. 2 even-odd reduction)
+//   dagger:       Mhat^+ = gamma_5 Mhat(-mu_bar) gamma_5     (A and gamma_5 commute; H is gamma_5-hermitian)
+//                 even: kappa^2 A(-mu)^-1 H_eo gamma_5 psi_o
+//                 odd : A(-mu) psi_o - gamma_5 H_oe t_e
+//
+// H psi(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu)
+// (Sec. 2, Eq. "Wilson" in the hopping normalisation).  In the chiral basis
+// gamma_mu = [[0, B_mu],[B_mu^+, 0]] with B_0 = -1, B_k = -i sigma_k, so
+//   (1 - gamma_mu) psi = (chi, -B^+ chi),  chi = psi_up - B psi_lo
+//   (1 + gamma_mu) psi = (chi,  B^+ chi),  chi = psi_up + B psi_lo
+// and only the two-spin chi is multiplied by the link (spin projection).
+//
+// One thread owns one output site and both flavours: the flavours share the
+// eight links (the doublet is two right-hand sides of the same hop).  On
+// GB300 the FP64 path is bound by the FP64 pipe, not by HBM, so the kernel
+// minimises FP64 instructions: links are kept uncompressed (no
+// reconstruction arithmetic), boundary signs and gamma_5 are applied as
+// sign-bit flips on the integer pipe, multiplications by +-i are swaps, and
+// kappa^2 is folded into the A^-1 coefficients.
+#include "tmnd_internal.cuh"
+
+namespace {
+
+// (B_mu v) for the lower two spins, v[2][3]
+template <int MU>
+__device__ __forceinline__ double2 Bmul(const double2 v[2][3], int s, int c) {
+    if (MU == 0) return cneg(v[s][c]);
+    if (MU == 1) return cmulmi(v[1 - s][c]);                 // -i sigma_1
+    if (MU == 2) return s == 0 ? cneg(v[1][c]) : v[0][c];    // -i sigma_2 = [[0,-1],[1,0]]
+    return s == 0 ? cmulmi(v[0][c]) : cmuli(v[1][c]);        // -i sigma_3 = diag(-i, i)
+}
+
+// (B_mu^+ v)
+template <int MU>
+__device__ __forceinline__ double2 Bdag(const double2 v[2][3], int s, int c) {
+    if (MU == 0) return cneg(v[s][c]);
+    if (MU == 1) return cmuli(v[1 - s][c]);                  // i sigma_1
+    if (MU == 2) return s == 0 ? v[1][c] : cneg(v[0][c]);    // i sigma_2 = [[0,1],[-1,0]]
+    return s == 0 ? cmuli(v[0][c]) : cmulmi(v[1][c]);        // i sigma_3 = diag(i, -i)
+}
+
+// Accumulate the hop from neighbour hn in direction MU, DIR (+1 forward
+// with U_mu(x), -1 backward with U_mu(x-mu)^+) into acc[flavour][spin][colour].
+// G5IN: the input field is gamma_5 psi (lower spins negated).
+template <int MU, int DIR, bool G5IN>
+__device__ __forceinline__ void hop_dir(const double2 *__restrict__ in, int Vh, int hn,
+                                        const double2 *__restrict__ U, int hl,
+                                        unsigned long long smask, double2 acc[2][4][3]) {
+    double2 u[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) u[i][j] = __ldg(&U[(i * 3 + j) * Vh + hl]);
+    // sign of the B psi_lo term in chi: forward -, backward +; gamma_5 on input flips it
+    constexpr bool plus = (DIR < 0) != G5IN;
+#pragma unroll
+    for (int f = 0; f < 2; f++) {
+        double2 up[2][3], lo[2][3];
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                up[s][c] = __ldg(&in[(f * 12 + s * 3 + c) * Vh + hn]);
+                lo[s][c] = __ldg(&in[(f * 12 + (s + 2) * 3 + c) * Vh + hn]);
+            }
+        double2 chi[2][3];
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                double2 b = Bmul<MU>(lo, s, c);
+                chi[s][c] = cflip(plus ? cadd(up[s][c], b) : csub(up[s][c], b), smask);
+            }
+        double2 v[2][3];
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                if (DIR > 0) {
+                    double2 t = cmul(u[i][0], chi[s][0]);
+                    t = cfma(u[i][1], chi[s][1], t);
+                    v[s][i] = cfma(u[i][2], chi[s][2], t);
+                } else {
+                    double2 t = cmul_conj(u[0][i], chi[s][0]);
+                    t = cfma_conj(u[1][i], chi[s][1], t);
+                    v[s][i] = cfma_conj(u[2][i], chi[s][2], t);
+                }
+            }
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                acc[f][s][c] = cadd(acc[f][s][c], v[s][c]);
+                double2 b = Bdag<MU>(v, s, c);
+                acc[f][s + 2][c] = (DIR > 0) ? csub(acc[f][s + 2][c], b) : cadd(acc[f][s + 2][c], b);
+            }
+    }
+}
+
+// H applied at output site of parity P, half-index h; in = field on parity 1-P.
+template <int P, bool G5IN>
+__device__ __forceinline__ void hop_all(const Geom &g, const double2 *__restrict__ links,
+                                        const double2 *__restrict__ in, int h, double2 acc[2][4][3]) {
+    const int Vh = g.Vh;
+    int zh = h % g.Zh;
+    int r = h / g.Zh;
+    int y = r % g.Y;
+    r /= g.Y;
+    int x = r % g.X;
+    int t = r / g.X;
+    int z = 2 * zh + ((P + t + x + y) & 1);
+#pragma unroll
+    for (int f = 0; f < 2; f++)
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc[f][s][c] = make_double2(0.0, 0.0);
+
+    const double2 *Lp = links + (size_t)P * 4 * 9 * Vh;         // links based at parity P sites
+    const double2 *Lq = links + (size_t)(1 - P) * 4 * 9 * Vh;   // links based at parity 1-P sites
+    const unsigned long long NEG = 0x8000000000000000ull;
+    auto idx = [&](int tt, int xx, int yy, int zz) { return ((tt * g.X + xx) * g.Y + yy) * g.Zh + (zz >> 1); };
+
+    // mu = 0 (time), with the antiperiodic sign on boundary-crossing hops
+    {
+        int tf = (t + 1 == g.T) ? 0 : t + 1;
+        int tb = (t == 0) ? g.T - 1 : t - 1;
+        unsigned long long mf = (g.apbc && t + 1 == g.T) ? NEG : 0ull;
+        unsigned long long mb = (g.apbc && t == 0) ? NEG : 0ull;
+        int hf = idx(tf, x, y, z), hb = idx(tb, x, y, z);
+        hop_dir<0, +1, G5IN>(in, Vh, hf, Lp + 0 * 9 * (size_t)Vh, h, mf, acc);
+        hop_dir<0, -1, G5IN>(in, Vh, hb, Lq + 0 * 9 * (size_t)Vh, hb, mb, acc);
+    }
+    {
+        int xf = (x + 1 == g.X) ? 0 : x + 1;
+        int xb = (x == 0) ? g.X - 1 : x - 1;
+        int hf = idx(t, xf, y, z), hb = idx(t, xb, y, z);
+        hop_dir<1, +1, G5IN>(in, Vh, hf, Lp + 1 * 9 * (size_t)Vh, h, 0ull, acc);
+        hop_dir<1, -1, G5IN>(in, Vh, hb, Lq + 1 * 9 * (size_t)Vh, hb, 0ull, acc);
+    }
+    {
+        int yf = (y + 1 == g.Y) ? 0 : y + 1;
+        int yb = (y == 0) ? g.Y - 1 : y - 1;
+        int hf = idx(t, x, yf, z), hb = idx(t, x, yb, z);
+        hop_dir<2, +1, G5IN>(in, Vh, hf, Lp + 2 * 9 * (size_t)Vh, h, 0ull, acc);
+        hop_dir<2, -1, G5IN>(in, Vh, hb, Lq + 2 * 9 * (size_t)Vh, hb, 0ull, acc);
+    }
+    {
+        int zf = (z + 1 == g.Z) ? 0 : z + 1;
+        int zb = (z == 0) ? g.Z - 1 : z - 1;
+        int hf = idx(t, x, y, zf), hb = idx(t, x, y, zb);
+        hop_dir<3, +1, G5IN>(in, Vh, hf, Lp + 3 * 9 * (size_t)Vh, h, 0ull, acc);
+        hop_dir<3, -1, G5IN>(in, Vh, hb, Lq + 3 * 9 * (size_t)Vh, hb, 0ull, acc);
+    }
+}
+
+// even sites: t_e = kappa^2 A^-1 H psi  (DAG: kappa^2 A(-mu)^-1 H gamma_5 psi)
+template <bool DAG>
+__global__ void __launch_bounds__(HOP_THREADS) k_hop_even(Geom g, SiteTerm st, const double2 *__restrict__ links,
+                                                         const double2 *__restrict__ psi, double2 *__restrict__ out,
+                                                         const int *__restrict__ done) {
+    if (done && *done) return;
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= g.Vh) return;
+    double2 acc[2][4][3];
+    hop_all<0, DAG>(g, links, psi, h, acc);
+    const double a = st.kappa2 * st.inv_det;
+    const double e = a * st.kpp;
+    const int Vh = g.Vh;
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        // A^-1 = [[1 - i kp g, kpp],[kpp, 1 + i kp g]] / det, g = gamma_5 eigenvalue
+        const double b = a * (DAG ? -st.kp : st.kp) * (s < 2 ? 1.0 : -1.0);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            double2 p0 = acc[0][s][c], p1 = acc[1][s][c];
+            double2 o0, o1;
+            o0.x = fma(a, p0.x, fma(b, p0.y, e * p1.x));
+            o0.y = fma(a, p0.y, fma(-b, p0.x, e * p1.y));
+            o1.x = fma(a, p1.x, fma(-b, p1.y, e * p0.x));
+            o1.y = fma(a, p1.y, fma(b, p1.x, e * p0.y));
+            out[(0 * 12 + s * 3 + c) * Vh + h] = o0;
+            out[(1 * 12 + s * 3 + c) * Vh + h] = o1;
+        }
+    }
+}
+
+// odd sites: y = A psi - H t  (DAG: A(-mu) psi - gamma_5 H t), then the epilogue.
+template <bool DAG, int EPI>
+__global__ void __launch_bounds__(HOP_THREADS) k_hop_odd(Geom g, SiteTerm st, const double2 *__restrict__ links,
+                                                        const double2 *__restrict__ psi, const double2 *__restrict__ te,
+                                                        double2 *__restrict__ out, HopEpiArgs ea) {
+    __shared__ double red[40];
+    if (ea.done && *ea.done) return;
+    const int Vh = g.Vh;
+    double alpha = 0.0;
+    if (EPI == EPI_MMS_R) {
+        // (p, w) = |Mhat p|^2 + sigma |p|^2 from the previous kernel's partials
+        double yy = block_reduce_partials(ea.part_in, ea.npart_in, red);
+        double pp = block_reduce_partials(ea.part_in + ea.npart_in, ea.npart_in, red);
+        alpha = *ea.rr / (yy + ea.sigma * pp);
+    }
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = h < Vh;
+    double n1 = 0.0, n2 = 0.0;
+    if (valid) {
+        double2 acc[2][4][3];
+        hop_all<1, false>(g, links, te, h, acc);
+        const double kp = DAG ? -st.kp : st.kp;
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            const double b = kp * (s < 2 ? 1.0 : -1.0);
+            // DAG: gamma_5 on the hop term flips the sign of the lower spins
+            const bool hopneg = DAG && s >= 2;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                double2 p0 = __ldg(&psi[(0 * 12 + s * 3 + c) * Vh + h]);
+                double2 p1 = __ldg(&psi[(1 * 12 + s * 3 + c) * Vh + h]);
+                double2 h0 = acc[0][s][c], h1 = acc[1][s][c];
+                if (hopneg) { h0 = cneg(h0); h1 = cneg(h1); }
+                // A = [[1 + i kp g, -kpp],[-kpp, 1 - i kp g]]
+                double2 y0, y1;
+                y0.x = fma(-b, p0.y, fma(-st.kpp, p1.x, p0.x - h0.x));
+                y0.y = fma(b, p0.x, fma(-st.kpp, p1.y, p0.y - h0.y));
+                y1.x = fma(b, p1.y, fma(-st.kpp, p0.x, p1.x - h1.x));
+                y1.y = fma(-b, p1.x, fma(-st.kpp, p0.y, p1.y - h1.y));
+                const int i0 = (0 * 12 + s * 3 + c) * Vh + h, i1 = (1 * 12 + s * 3 + c) * Vh + h;
+                if (EPI == EPI_STORE || EPI == EPI_STORE_NORMS) {
+                    out[i0] = y0;
+                    out[i1] = y1;
+                    if (EPI == EPI_STORE_NORMS) {
+                        n1 = fma(y0.x, y0.x, fma(y0.y, y0.y, fma(y1.x, y1.x, fma(y1.y, y1.y, n1))));
+                        n2 = fma(p0.x, p0.x, fma(p0.y, p0.y, fma(p1.x, p1.x, fma(p1.y, p1.y, n2))));
+                    }
+                } else if (EPI == EPI_SHIFT) {
+                    double2 a0 = __ldg(&ea.aux[i0]), a1 = __ldg(&ea.aux[i1]);
+                    out[i0] = make_double2(fma(ea.sigma, a0.x, y0.x), fma(ea.sigma, a0.y, y0.y));
+                    out[i1] = make_double2(fma(ea.sigma, a1.x, y1.x), fma(ea.sigma, a1.y, y1.y));
+                } else {  // EPI_MMS_R
+                    double2 a0 = __ldg(&ea.aux[i0]), a1 = __ldg(&ea.aux[i1]);
+                    double2 w0 = make_double2(fma(ea.sigma, a0.x, y0.x), fma(ea.sigma, a0.y, y0.y));
+                    double2 w1 = make_double2(fma(ea.sigma, a1.x, y1.x), fma(ea.sigma, a1.y, y1.y));
+                    double2 r0 = ea.r[i0], r1 = ea.r[i1];
+                    r0.x = fma(-alpha, w0.x, r0.x); r0.y = fma(-alpha, w0.y, r0.y);
+                    r1.x = fma(-alpha, w1.x, r1.x); r1.y = fma(-alpha, w1.y, r1.y);
+                    ea.r[i0] = r0;
+                    ea.r[i1] = r1;
+                    n1 = fma(r0.x, r0.x, fma(r0.y, r0.y, fma(r1.x, r1.x, fma(r1.y, r1.y, n1))));
+                }
+            }
+        }
+    }
+    if (EPI == EPI_STORE_NORMS) {
+        double s1 = block_sum(n1, red);
+        double s2 = block_sum(n2, red);
+        if (threadIdx.x == 0) {
+            ea.part_out[blockIdx.x] = s1;
+            ea.part_out[gridDim.x + blockIdx.x] = s2;
+        }
+    } else if (EPI == EPI_MMS_R) {
+        double s1 = block_sum(n1, red);
+        if (threadIdx.x == 0) ea.part_out[blockIdx.x] = s1;
+    }
+}
+
+}  // namespace
+
+void launch_hop_even_f64(const Geom &g, const SiteTerm &st, const double2 *links, const double2 *psi_o,
+                         double2 *t_e, bool dag, const int *done, cudaStream_t s) {
+    dim3 grid(hop_blocks(g)), block(HOP_THREADS);
+    if (dag)
+        k_hop_even<true><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, done);
+    else
+        k_hop_even<false><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, done);
+}
+
+void launch_hop_odd_f64(const Geom &g, const SiteTerm &st, const double2 *links, const double2 *psi_o,
+                        const double2 *t_e, double2 *y_o, bool dag, HopEpi epi, const HopEpiArgs &ea,
+                        cudaStream_t s) {
+    dim3 grid(hop_blocks(g)), block(HOP_THREADS);
+#define TMND_ODD(D, E) k_hop_odd<D, E><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, y_o, ea)
+    if (!dag) {
+        switch (epi) {
+            case EPI_STORE: TMND_ODD(false, EPI_STORE); break;
+            case EPI_STORE_NORMS: TMND_ODD(false, EPI_STORE_NORMS); break;
+            case EPI_SHIFT: TMND_ODD(false, EPI_SHIFT); break;
+            case EPI_MMS_R: TMND_ODD(false, EPI_MMS_R); break;
+        }
+    } else {
+        switch (epi) {
+            case EPI_STORE: TMND_ODD(true, EPI_STORE); break;
+            case EPI_STORE_NORMS: TMND_ODD(true, EPI_STORE_NORMS); break;
+            case EPI_SHIFT: TMND_ODD(true, EPI_SHIFT); break;
+            case EPI_MMS_R: TMND_ODD(true, EPI_MMS_R); break;
+        }
+    }
+#undef TMND_ODD
+}

@@ -1,0 +1,159 @@
+// Internal definitions shared by the libtmnd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "tmnd.h"
+
+// ------------------------------------------------------------------ errors
+void tmnd_set_error(const char *fmt, ...);
+
+#define TMND_CUDA_TRY(call)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            tmnd_set_error("%s:%d: %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return (e_ == cudaErrorMemoryAllocation) ? TMND_ERR_OOM : TMND_ERR_CUDA;     \
+        }                                                                                \
+    } while (0)
+
+#define TMND_ARG_CHECK(cond, ...)                  \
+    do {                                           \
+        if (!(cond)) {                             \
+            tmnd_set_error(__VA_ARGS__);           \
+            return TMND_ERR_ARG;                   \
+        }                                          \
+    } while (0)
+
+// ---------------------------------------------------------------- geometry
+// Lattice geometry for the even-odd layout.  Half-index h of site (t,x,y,z)
+// is lex >> 1 with lex = ((t*X + x)*Y + y)*Z + z; Zh = Z/2.
+struct Geom {
+    int T, X, Y, Z, Zh;
+    int Vh;        // V/2
+    int apbc;      // antiperiodic time boundary
+};
+
+// Parameters of the site-diagonal term A = 1 + i kp g5 tau3 - kpp tau1 (hopping form):
+// kp = 2 kappa mu_bar, kpp = 2 kappa eps_bar; A^-1 = [[1 - i kp g, kpp],[kpp, 1 + i kp g]] / det,
+// det = 1 + kp^2 - kpp^2 for gamma_5 eigenvalue g.
+struct SiteTerm {
+    double kappa2;  // kappa^2, folded into A^-1 in the even-site kernel
+    double kp;      // 2 kappa mu_bar
+    double kpp;     // 2 kappa eps_bar
+    double inv_det; // 1 / (1 + kp^2 - kpp^2)
+};
+
+// Gauge handle.
+struct tmnd_gauge {
+    tmnd_action act;
+    int prec;
+    int device;
+    Geom geom;
+    SiteTerm st;
+    double2 *links;        // [2 parity][4 mu][9][Vh] complex, U_mu(x) stored at the parity/half-index of x
+    void *work;            // grow-only workspace
+    size_t work_bytes;
+    double2 *partials;     // reduction partials (grow-only, separate from work)
+    size_t partials_bytes;
+};
+
+tmnd_status tmnd_ensure_workspace(tmnd_gauge *g, size_t bytes);
+tmnd_status tmnd_ensure_partials(tmnd_gauge *g, size_t bytes);
+
+// Number of complex numbers per site of a doublet spinor.
+constexpr int NCOMP = 24;
+
+// --------------------------------------------------------- device helpers
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// i * a
+__device__ __forceinline__ double2 cmuli(double2 a) { return make_double2(-a.y, a.x); }
+// -i * a
+__device__ __forceinline__ double2 cmulmi(double2 a) { return make_double2(a.y, -a.x); }
+__device__ __forceinline__ double2 cneg(double2 a) { return make_double2(-a.x, -a.y); }
+// acc + a*b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// a*b
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc + conj(a)*b
+__device__ __forceinline__ double2 cfma_conj(double2 a, double2 b, double2 acc) {
+    return make_double2(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+// conj(a)*b
+__device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+// Flip the sign of a double without touching the FP64 pipe (integer XOR of the sign bit).
+__device__ __forceinline__ double dflip(double v, unsigned long long mask) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)mask);
+}
+__device__ __forceinline__ double2 cflip(double2 a, unsigned long long mask) {
+    return make_double2(dflip(a.x, mask), dflip(a.y, mask));
+}
+
+// Block-wide sum of one double (blockDim.x a multiple of 32, <= 1024); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *smem /* >= 32 */) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) smem[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        int nw = blockDim.x >> 5;
+        for (int i = 0; i < nw; i++) s += smem[i];
+    }
+    return s;
+}
+
+// Deterministic sum of n partials, computed by a whole block (fixed order,
+// same result in every block); result returned to all threads.
+__device__ __forceinline__ double block_reduce_partials(const double *p, int n, double *smem) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += p[i];
+    double s = block_sum(v, smem);
+    __syncthreads();
+    if (threadIdx.x == 0) smem[32] = s;
+    __syncthreads();
+    double r = smem[32];
+    __syncthreads();
+    return r;
+}
+
+// --------------------------------------------------------- launch helpers
+// Hop kernels (tm_nd_apply and the solver share these launchers).
+enum HopEpi {
+    EPI_STORE = 0,        // out = y
+    EPI_STORE_NORMS = 1,  // out = y; partials |y|^2, |in|^2
+    EPI_SHIFT = 2,        // out = y + sigma * aux
+    EPI_MMS_R = 3         // w = y + sigma * aux; r -= alpha w; partial |r|^2  (alpha from partials)
+};
+
+constexpr int HOP_THREADS = 128;
+
+struct HopEpiArgs {
+    double sigma;
+    const double2 *aux;     // EPI_SHIFT / EPI_MMS_R: the vector multiplied by sigma
+    double2 *r;             // EPI_MMS_R: residual updated in place
+    double *part_out;       // partial sums written per block (EPI_STORE_NORMS: 2 per block; EPI_MMS_R: 1)
+    const double *part_in;  // EPI_MMS_R: partials of |y|^2, |p|^2 from the previous kernel
+    int npart_in;           // number of blocks that wrote part_in
+    const double *rr;       // EPI_MMS_R: (r,r) before the update (device scalar)
+    const int *done;        // if non-null and *done != 0 the kernel returns immediately
+};
+
+// even-site kernel: t_e = kappa^2 A^-1 H_eo psi_o   (dag: kappa^2 A(-mu)^-1 H_eo gamma_5 psi_o)
+void launch_hop_even_f64(const Geom &g, const SiteTerm &st, const double2 *links, const double2 *psi_o,
+                         double2 *t_e, bool dag, const int *done, cudaStream_t s);
+// odd-site kernel: y_o = A psi_o - H_oe t_e   (dag: A(-mu) psi_o - gamma_5 H_oe t_e), with epilogue
+void launch_hop_odd_f64(const Geom &g, const SiteTerm &st, const double2 *links, const double2 *psi_o,
+                        const double2 *t_e, double2 *y_o, bool dag, HopEpi epi, const HopEpiArgs &ea,
+                        cudaStream_t s);
+inline int hop_blocks(const Geom &g) { return (g.Vh + HOP_THREADS - 1) / HOP_THREADS; }
