@@ -247,6 +247,7 @@ extern "C" tmnd_status tm_nd_apply(tmnd_gauge *g, void *out, const void *in, int
     TMND_ARG_CHECK(((uintptr_t)out & 15) == 0 && ((uintptr_t)in & 15) == 0,
                    "tm_nd_apply: pointers must be 16-byte aligned");
     TMND_ARG_CHECK(isfinite(sigma), "tm_nd_apply: sigma must be finite");
+    cudaGetLastError();  // clear a stale, non-sticky error left by earlier unrelated calls
     const size_t sp = tmnd_spinor_bytes(g);
     tmnd_status st = tmnd_ensure_workspace(g, 2 * sp);
     if (st != TMND_OK) return st;

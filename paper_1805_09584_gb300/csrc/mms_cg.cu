@@ -277,7 +277,7 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
         cudaGraph_t graph = nullptr;
         TMND_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         for (int k = 0; k < check_every; k++) {
-            if (profile) cudaEventRecord(ev(inst, k, 0), s);
+            if (profile) cudaEventRecordWithFlags(ev(inst, k, 0), s, cudaEventRecordExternal);
             HopEpiArgs e1 = {};
             e1.part_out = part_norm;
             e1.done = &st->done;
@@ -294,10 +294,10 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
             e2.rr = &st->rr;
             e2.done = &st->done;
             launch_hop_odd_f64(g->geom, g->st, g->links, y, te, nullptr, true, EPI_MMS_R, e2, s);
-            if (profile) cudaEventRecord(ev(inst, k, 1), s);
+            if (profile) cudaEventRecordWithFlags(ev(inst, k, 1), s, cudaEventRecordExternal);
             k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c);
             k_update<<<nb_str, UPD_THREADS, 0, s>>>(n, cf, r, p, ptrs, nshift);
-            if (profile) cudaEventRecord(ev(inst, k, 2), s);
+            if (profile) cudaEventRecordWithFlags(ev(inst, k, 2), s, cudaEventRecordExternal);
         }
         cudaError_t ce = cudaStreamEndCapture(s, &graph);
         if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec[inst], graph, 0);
@@ -322,8 +322,11 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
         int inst = (int)(j % ninst);
         for (int k = 0; k < check_every; k++) {
             float a = 0.f, b2 = 0.f;
-            cudaEventElapsedTime(&a, ev(inst, k, 0), ev(inst, k, 1));
-            cudaEventElapsedTime(&b2, ev(inst, k, 1), ev(inst, k, 2));
+            if (cudaEventElapsedTime(&a, ev(inst, k, 0), ev(inst, k, 1)) != cudaSuccess ||
+                cudaEventElapsedTime(&b2, ev(inst, k, 1), ev(inst, k, 2)) != cudaSuccess) {
+                cudaGetLastError();
+                a = b2 = nanf("");
+            }
             hop_t.push_back(a);
             upd_t.push_back(b2);
         }
@@ -414,6 +417,7 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
                                     void *const *x, const tmnd_solve_params *params, tmnd_solve_info *info,
                                     void *stream) {
     TMND_ARG_CHECK(g && b && sigma && x && params, "mms_cg_solve: NULL argument");
+    cudaGetLastError();  // clear a stale, non-sticky error left by earlier unrelated calls
     TMND_ARG_CHECK(nshift >= 1 && nshift <= TMND_MAX_SHIFTS, "mms_cg_solve: nshift = %d not in [1, %d]", nshift,
                    TMND_MAX_SHIFTS);
     TMND_ARG_CHECK(nrhs >= 1, "mms_cg_solve: nrhs = %d", nrhs);
@@ -445,9 +449,9 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     cudaStream_t s;
     TMND_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaEvent_t e0;
-    cudaEventCreateWithFlags(&e0, cudaEventDisableTiming);
-    cudaEventRecord(e0, user);
-    cudaStreamWaitEvent(s, e0, 0);
+    TMND_CUDA_TRY(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+    TMND_CUDA_TRY(cudaEventRecord(e0, user));
+    TMND_CUDA_TRY(cudaStreamWaitEvent(s, e0, 0));
     tmnd_status res = TMND_OK;
     for (int k = 0; k < nrhs && res == TMND_OK; k++) {
         tmnd_status rk = mms_one_rhs(g, (const double2 *)b + (size_t)k * (sp / sizeof(double2)),

@@ -7,6 +7,9 @@ allowed as a factor 1.2), and differs from the oracle's own MMS-CG solution by
 at most 2 rho |b| / sigma_i (lambda_min(Qhat^2 + sigma) >= sigma).
 Element-wise agreement is NOT expected: two correct solutions may differ by
 ~rho/sigma relative."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -17,10 +20,11 @@ from gpu_common import EPS, KAPPA, MU, rel_err, require_gpu, torch
 pytestmark = pytest.mark.gpu
 
 
-def _solve(tm, g, b, sig, rho=1e-10, nsolve=0, nrhs=1, check_every=0):
+def _solve(tm, g, b, sig, rho=1e-10, nsolve=0, nrhs=1, check_every=0, profile=False):
     bi = g.pack(torch.from_numpy(b).cuda(), nrhs=nrhs)
     xs = [g.spinor(nrhs) for _ in sig]
-    info = tm.mms_cg_solve(g.handle, bi, nrhs, sig, xs, rho=rho, nsolve=nsolve, check_every=check_every)
+    info = tm.mms_cg_solve(g.handle, bi, nrhs, sig, xs, rho=rho, nsolve=nsolve, check_every=check_every,
+                           profile=profile)
     return info, [g.unpack(x, nrhs).cpu().numpy() for x in xs]
 
 
@@ -34,8 +38,11 @@ def test_mms_config1_matches_oracle(check_every):
     act = oracle.action(dims, KAPPA, MU, EPS)
     sig = synth.shift_set(10, 1e-4, 1.0)
     g = tm.Gauge(U, dims, KAPPA, MU, EPS)
-    info, xs = _solve(tm, g, b, sig, check_every=check_every)
+    info, xs = _solve(tm, g, b, sig, check_every=check_every, profile=check_every > 0)
     ref = oracle.mms_cg(act, U, b, sig, rho=1e-10)
+    if check_every > 0:  # profiled: per-iteration event timings are real numbers
+        assert np.isfinite(info["hop_ms"]) and info["hop_ms"] > 0
+        assert np.isfinite(info["update_ms"]) and info["update_ms"] > 0
     nb = np.linalg.norm(b)
     # same algorithm in FP64: iteration counts agree up to rounding-order effects
     assert abs(info["iters"] - ref["iters"]) <= 2
@@ -126,8 +133,12 @@ def test_mms_bench_workload_certified_by_oracle():
     act = oracle.action(dims, KAPPA, MU, EPS)
     sig = synth.shift_set(12, 1e-5, 2.0)
     g = tm.Gauge(U, dims, KAPPA, MU, EPS)
-    info, xs = _solve(tm, g, b, sig)
+    info, xs = _solve(tm, g, b, sig, profile=True)
     for i, s in enumerate(sig):
         tr = oracle.true_residual(act, U, b, xs[i][0], s)
         assert tr <= 1.2e-10, (i, tr, info)
+    # the oracle's own solve of this workload (stored by tests/golden/make_golden.py)
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "mms_16x16x16x32.json")))
+    assert abs(info["iters"] - gold["iters"]) <= 2
+    assert all(abs(a - b2) <= 2 for a, b2 in zip(info["conv_iter"], gold["conv_iter"]))
     g.close()
