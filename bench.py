@@ -140,7 +140,7 @@ def run_tmnd(args):
     e0.record(stream)
     for _ in range(args.steps):
         flush.fill_(1.0)
-        infos.append(step(profile=True))
+        infos.append(step())
     e1.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
@@ -186,14 +186,25 @@ def run_tmnd(args):
     h2d = b_host.nbytes
     d2h = NSHIFT * b_host.nbytes
 
-    # ---- roofline of the dominant kernel (the FP64 stencil launches), live events
-    hop_ms = sum(i["hop_ms"] for i in infos)
-    n_hop_launch = 4 * sum(i["iters"] for i in infos)
+    # ---- roofline of the dominant kernel (the FP64 stencil launches): one more
+    # solve, identical to the timed ones, with CUDA events recorded around the
+    # stencil and update launches of every iteration (event nodes in the graph;
+    # kept out of the timed region so that they do not slow the headline number)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    pinfo = step(profile=True)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = p0.elapsed_time(p1)
+    hop_ms = pinfo["hop_ms"]
+    n_hop_launch = 4 * pinfo["iters"]
     hop_avg_s = hop_ms / 1e3 / n_hop_launch
     flop_per_launch = HOP_FLOP_PER_SITE * g.vh
     achieved_tflops = flop_per_launch / hop_avg_s / 1e12
     fp64_peak = FP64_PEAK_TFLOPS
-    upd_ms = sum(i["update_ms"] for i in infos)
+    upd_ms = pinfo["update_ms"]
     launches = sum(i["launches"] for i in infos)
 
     out = None
@@ -213,10 +224,12 @@ def run_tmnd(args):
                          "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": achieved_tflops / fp64_peak, "traffic": None,
                          "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                         "hop_share_of_step": hop_ms / ms,
+                         "hop_share_of_step": hop_ms / prof_ms,
+                         "measured": "CUDA events around every iteration's 4 stencil launches of a profiled "
+                                     "solve run right after the timed steps",
                          "hop_achieved_gbs": HOP_BYTES_PER_SITE * g.vh / hop_avg_s / 1e9,
                          "hbm_peak_gbs": _peaks().get("hbm_gbs")},
-            "update_share_of_step": upd_ms / ms,
+            "update_share_of_step": upd_ms / prof_ms,
             "gpu_launches": launches,
             "clocks": clocks,
         }
