@@ -110,6 +110,38 @@ tmnd_status tmnd_spinor_unpack(const tmnd_gauge *g, void *dev_canonical, const v
 tmnd_status tm_nd_apply(tmnd_gauge *g, void *out, const void *in, int op, double sigma,
                         int nrhs, void *stream);
 
+/* No-allocation variant of tm_nd_apply.  The paper has no counterpart: this
+ * is a library convenience.
+ *
+ * Same operation, arguments, layouts and stream semantics as tm_nd_apply, but
+ * the two intermediate spinors (one even-site, one odd-site) live in one fixed
+ * array of device memory declared inside the library instead of the handle's
+ * workspace, so the call itself never allocates or frees device memory (no
+ * cudaMalloc, no cudaFree, no allocating library routine).  It is meant for
+ * callers that cannot allocate device memory at call time: programs whose
+ * device memory is entirely owned by another allocator (a framework's caching
+ * allocator, a fixed arena) with no room left for a library's own cudaMalloc,
+ * and latency-critical loops that cannot accept the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree.  (tm_nd_apply grows its workspace
+ * with cudaMalloc the first time a handle needs it.)
+ *
+ *   - Limit: V/2 <= TMND_NOALLOC_MAX_VH odd sites (e.g. 16^4, 8^3x64);
+ *     larger lattices are rejected with TMND_ERR_ARG.  The array takes
+ *     2 x 24 x TMND_NOALLOC_MAX_VH complex128 = 24 MiB on every GPU that loads
+ *     the library, until the process exits.
+ *   - The current device must be the handle's device.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - Every call on a device (any handle, stream or host thread) uses the same
+ *     array.  Calls whose executions overlap on the GPU race on it and give
+ *     wrong results: order them (one stream, or events between streams).
+ *   - The array keeps the last call's contents; everything a call reads from
+ *     it is written earlier in the same call, so no clearing is needed. */
+#define TMND_NOALLOC_MAX_VH 32768
+tmnd_status tm_nd_apply_noalloc(const tmnd_gauge *g, void *out, const void *in, int op, double sigma,
+                                int nrhs, void *stream);
+
 #define TMND_MAX_SHIFTS 32
 
 typedef struct {

@@ -27,7 +27,9 @@ STATUS = {0: "TMND_OK", 1: "TMND_ERR_ARG", 2: "TMND_ERR_CUDA", 3: "TMND_ERR_OOM"
 
 # every entry point declared in include/tmnd.h
 EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd_spinor_pack",
-           "tmnd_spinor_unpack", "tm_nd_apply", "mms_cg_solve", "lagrange_guess", "tmnd_last_error")
+           "tmnd_spinor_unpack", "tm_nd_apply", "tm_nd_apply_noalloc", "mms_cg_solve", "lagrange_guess",
+           "tmnd_last_error")
+NOALLOC_MAX_VH = 32768
 
 
 class TmndError(RuntimeError):
@@ -72,13 +74,14 @@ def lib() -> ctypes.CDLL:
         L.tmnd_spinor_pack.argtypes = [vp, vp, vp, i, vp]
         L.tmnd_spinor_unpack.argtypes = [vp, vp, vp, i, vp]
         L.tm_nd_apply.argtypes = [vp, vp, vp, i, d, i, vp]
+        L.tm_nd_apply_noalloc.argtypes = [vp, vp, vp, i, d, i, vp]
         L.mms_cg_solve.argtypes = [vp, vp, i, ctypes.POINTER(d), i, ctypes.POINTER(vp),
                                    ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp]
         L.lagrange_guess.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(vp), i, d, vp, i,
                                      ctypes.POINTER(d), vp]
         L.tmnd_last_error.restype = ctypes.c_char_p
         for name in ("tmnd_gauge_create", "tmnd_spinor_pack", "tmnd_spinor_unpack", "tm_nd_apply",
-                     "mms_cg_solve", "lagrange_guess"):
+                     "tm_nd_apply_noalloc", "mms_cg_solve", "lagrange_guess"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -140,6 +143,13 @@ def tmnd_spinor_unpack(h, dev_canonical, dev_internal, nrhs: int = 1, stream=Non
 
 def tm_nd_apply(h, out, inp, op: int, sigma: float = 0.0, nrhs: int = 1, stream=None) -> None:
     _check(lib().tm_nd_apply(h, _ptr(out), _ptr(inp), int(op), float(sigma), int(nrhs), _stream(stream)))
+
+
+def tm_nd_apply_noalloc(h, out, inp, op: int, sigma: float = 0.0, nrhs: int = 1, stream=None) -> None:
+    """tm_nd_apply with its temporaries in the library's fixed device array: never
+    allocates (for callers whose device memory is owned by another allocator or
+    that cannot take cudaMalloc's synchronisation); V/2 <= NOALLOC_MAX_VH."""
+    _check(lib().tm_nd_apply_noalloc(h, _ptr(out), _ptr(inp), int(op), float(sigma), int(nrhs), _stream(stream)))
 
 
 def mms_cg_solve(h, b, nrhs: int, sigma, x, rho: float = 1e-10, maxiter: int = 100000, nsolve: int = 0,
