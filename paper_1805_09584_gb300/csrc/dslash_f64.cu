@@ -45,7 +45,7 @@ __device__ __forceinline__ double2 Bdag(const double2 v[2][3], int s, int c) {
 // Accumulate the hop from neighbour hn in direction MU, DIR (+1 forward
 // with U_mu(x), -1 backward with U_mu(x-mu)^+) into acc[flavour][spin][colour].
 // G5IN: the input field is gamma_5 psi (lower spins negated).
-template <int MU, int DIR, bool G5IN>
+template <int MU, int DIR, bool G5IN, bool FIRST = false>
 __device__ __forceinline__ void hop_dir(const double2 *__restrict__ in, int Vh, int hn,
                                         const double2 *__restrict__ U, int hl,
                                         unsigned long long smask, double2 acc[2][4][3]) {
@@ -93,9 +93,14 @@ __device__ __forceinline__ void hop_dir(const double2 *__restrict__ in, int Vh, 
         for (int s = 0; s < 2; s++)
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                acc[f][s][c] = cadd(acc[f][s][c], v[s][c]);
                 double2 b = Bdag<MU>(v, s, c);
-                acc[f][s + 2][c] = (DIR > 0) ? csub(acc[f][s + 2][c], b) : cadd(acc[f][s + 2][c], b);
+                if (FIRST) {  // the first direction initialises the accumulator
+                    acc[f][s][c] = v[s][c];
+                    acc[f][s + 2][c] = (DIR > 0) ? cneg(b) : b;
+                } else {
+                    acc[f][s][c] = cadd(acc[f][s][c], v[s][c]);
+                    acc[f][s + 2][c] = (DIR > 0) ? csub(acc[f][s + 2][c], b) : cadd(acc[f][s + 2][c], b);
+                }
             }
     }
 }
@@ -112,13 +117,6 @@ __device__ __forceinline__ void hop_all(const Geom &g, const double2 *__restrict
     int x = r % g.X;
     int t = r / g.X;
     int z = 2 * zh + ((P + t + x + y) & 1);
-#pragma unroll
-    for (int f = 0; f < 2; f++)
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) acc[f][s][c] = make_double2(0.0, 0.0);
-
     const double2 *Lp = links + (size_t)P * 4 * 9 * Vh;         // links based at parity P sites
     const double2 *Lq = links + (size_t)(1 - P) * 4 * 9 * Vh;   // links based at parity 1-P sites
     const unsigned long long NEG = 0x8000000000000000ull;
@@ -131,7 +129,7 @@ __device__ __forceinline__ void hop_all(const Geom &g, const double2 *__restrict
         unsigned long long mf = (g.apbc && t + 1 == g.T) ? NEG : 0ull;
         unsigned long long mb = (g.apbc && t == 0) ? NEG : 0ull;
         int hf = idx(tf, x, y, z), hb = idx(tb, x, y, z);
-        hop_dir<0, +1, G5IN>(in, Vh, hf, Lp + 0 * 9 * (size_t)Vh, h, mf, acc);
+        hop_dir<0, +1, G5IN, true>(in, Vh, hf, Lp + 0 * 9 * (size_t)Vh, h, mf, acc);
         hop_dir<0, -1, G5IN>(in, Vh, hb, Lq + 0 * 9 * (size_t)Vh, hb, mb, acc);
     }
     {
@@ -161,10 +159,10 @@ __device__ __forceinline__ void hop_all(const Geom &g, const double2 *__restrict
 template <bool DAG>
 __global__ void __launch_bounds__(HOP_THREADS) k_hop_even(Geom g, SiteTerm st, const double2 *__restrict__ links,
                                                          const double2 *__restrict__ psi, double2 *__restrict__ out,
-                                                         const int *__restrict__ done) {
+                                                         const int *__restrict__ done, int chunk) {
     if (done && *done) return;
-    int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= g.Vh) return;
+    const int h_end = min(g.Vh, (blockIdx.x + 1) * chunk);
+    for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) {
     double2 acc[2][4][3];
     hop_all<0, DAG>(g, links, psi, h, acc);
     const double a = st.kappa2 * st.inv_det;
@@ -186,13 +184,14 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop_even(Geom g, SiteTerm st, c
             out[(1 * 12 + s * 3 + c) * Vh + h] = o1;
         }
     }
+    }
 }
 
 // odd sites: y = A psi - H t  (DAG: A(-mu) psi - gamma_5 H t), then the epilogue.
 template <bool DAG, int EPI>
 __global__ void __launch_bounds__(HOP_THREADS) k_hop_odd(Geom g, SiteTerm st, const double2 *__restrict__ links,
                                                         const double2 *__restrict__ psi, const double2 *__restrict__ te,
-                                                        double2 *__restrict__ out, HopEpiArgs ea) {
+                                                        double2 *__restrict__ out, HopEpiArgs ea, int chunk) {
     __shared__ double red[40];
     if (ea.done && *ea.done) return;
     const int Vh = g.Vh;
@@ -203,10 +202,9 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop_odd(Geom g, SiteTerm st, co
         double pp = block_reduce_partials(ea.part_in + ea.npart_in, ea.npart_in, red);
         alpha = *ea.rr / (yy + ea.sigma * pp);
     }
-    int h = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = h < Vh;
     double n1 = 0.0, n2 = 0.0;
-    if (valid) {
+    const int h_end = min(Vh, (int)(blockIdx.x + 1) * chunk);
+    for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) {
         double2 acc[2][4][3];
         hop_all<1, false>(g, links, te, h, acc);
         const double kp = DAG ? -st.kp : st.kp;
@@ -268,20 +266,50 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop_odd(Geom g, SiteTerm st, co
 
 }  // namespace
 
+// Persistent, balanced grid: every SM gets the same number of resident
+// blocks and every block a contiguous chunk of about the same number of
+// sites, so the FP64 pipe of every SM finishes at the same time (a plain
+// one-site-per-thread grid leaves a 1.7-wave tail at 16^3x32).
+int hop_blocks(const Geom &g) {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int sms = 0, per_sm = 0, per_sm2 = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hop_odd<true, EPI_MMS_R>, HOP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_hop_even<true>, HOP_THREADS, 0);
+        per_sm = per_sm < per_sm2 ? per_sm : per_sm2;
+        if (sms <= 0) sms = 152;
+        if (per_sm <= 0) per_sm = 1;
+        cached[dev] = sms * per_sm;
+    }
+    int want = (g.Vh + HOP_THREADS - 1) / HOP_THREADS;
+    return want < cached[dev] ? want : cached[dev];
+}
+
+static int hop_chunk(const Geom &g) {
+    int nb = hop_blocks(g);
+    return (g.Vh + nb - 1) / nb;
+}
+
 void launch_hop_even_f64(const Geom &g, const SiteTerm &st, const double2 *links, const double2 *psi_o,
                          double2 *t_e, bool dag, const int *done, cudaStream_t s) {
     dim3 grid(hop_blocks(g)), block(HOP_THREADS);
+    const int chunk = hop_chunk(g);
     if (dag)
-        k_hop_even<true><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, done);
+        k_hop_even<true><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, done, chunk);
     else
-        k_hop_even<false><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, done);
+        k_hop_even<false><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, done, chunk);
 }
 
 void launch_hop_odd_f64(const Geom &g, const SiteTerm &st, const double2 *links, const double2 *psi_o,
                         const double2 *t_e, double2 *y_o, bool dag, HopEpi epi, const HopEpiArgs &ea,
                         cudaStream_t s) {
     dim3 grid(hop_blocks(g)), block(HOP_THREADS);
-#define TMND_ODD(D, E) k_hop_odd<D, E><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, y_o, ea)
+    const int chunk = hop_chunk(g);
+#define TMND_ODD(D, E) k_hop_odd<D, E><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, y_o, ea, chunk)
     if (!dag) {
         switch (epi) {
             case EPI_STORE: TMND_ODD(false, EPI_STORE); break;

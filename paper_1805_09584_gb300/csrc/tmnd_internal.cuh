@@ -156,4 +156,5 @@ void launch_hop_even_f64(const Geom &g, const SiteTerm &st, const double2 *links
 void launch_hop_odd_f64(const Geom &g, const SiteTerm &st, const double2 *links, const double2 *psi_o,
                         const double2 *t_e, double2 *y_o, bool dag, HopEpi epi, const HopEpiArgs &ea,
                         cudaStream_t s);
-inline int hop_blocks(const Geom &g) { return (g.Vh + HOP_THREADS - 1) / HOP_THREADS; }
+// Number of blocks (= reduction partials) of every hop launch for this geometry.
+int hop_blocks(const Geom &g);
