@@ -60,14 +60,22 @@ typedef enum {
 } tmnd_status;
 
 typedef enum {
-    TMND_F64 = 0           /* FP64 storage and arithmetic */
+    TMND_F64 = 0,          /* FP64 storage and arithmetic: 24 complex128 planes per RHS */
+    TMND_F32 = 1,          /* FP32 storage: 24 complex64 planes per RHS */
+    TMND_S16 = 2           /* 16-bit fixed-point storage with FP32 arithmetic: 6 planes of
+                              16-byte words over V/2 sites (word = one complex component,
+                              real part in the low 16 bits, imaginary in the high 16 bits,
+                              component c = flavour*12 + spin*3 + colour, plane c/4), then
+                              V/2 floats: the per-site scale max|v|/32767 */
 } tmnd_prec;
 
 typedef enum {
     TMND_OP_MHAT = 0,      /* out = Mhat in                            (Sec. 2 even-odd reduction) */
     TMND_OP_MHAT_DAG = 1,  /* out = Mhat^+ in                          */
     TMND_OP_QHAT2 = 2,     /* out = (Mhat^+ Mhat + sigma) in           (Eq. "shifted_linear") */
-    TMND_OP_QHAT = 3       /* out = (gamma_5 (x) tau_1) Mhat in         (Eq. "g5tau1-hermiticity") */
+    TMND_OP_QHAT = 3,      /* out = (gamma_5 (x) tau_1) Mhat in         (Eq. "g5tau1-hermiticity") */
+    TMND_OP_S16 = 16       /* flag OR-ed into the op: apply the sloppy operator (FP32 arithmetic,
+                              16-bit links and intermediates) to TMND_S16 spinors */
 } tmnd_op;
 
 typedef struct {
@@ -82,7 +90,10 @@ typedef struct tmnd_gauge tmnd_gauge;
 
 /* Create a gauge handle on the current CUDA device.  Copies `host_links`
  * (canonical layout, host memory, read only during the call) to the device
- * and packs it per parity and direction.  Every link is checked on the host
+ * and packs it per parity and direction, in FP64 (18 reals per link) and in
+ * 16-bit fixed point (rows 0 and 1, scale 32767; row 2 rebuilt in the
+ * kernels) for the sloppy operator.  `prec` is TMND_F64 or TMND_S16 (both
+ * copies are made either way).  Every link is checked on the host
  * to be SU(3) (|U U^+ - 1| and |det U - 1| below 1e-10); a failing link gives
  * TMND_ERR_NOTSU3.  Synchronous.  (Sec. 2: U_mu(x) in SU(3).) */
 tmnd_status tmnd_gauge_create(const double *host_links, const tmnd_action *act, int prec,
@@ -91,8 +102,18 @@ tmnd_status tmnd_gauge_create(const double *host_links, const tmnd_action *act, 
 /* Release the handle and all device memory it owns.  Synchronises the device. */
 void tmnd_gauge_destroy(tmnd_gauge *g);
 
-/* Bytes of one internal spinor (one right-hand side) for this handle. */
+/* Bytes of one internal FP64 spinor (one right-hand side) for this handle. */
 size_t tmnd_spinor_bytes(const tmnd_gauge *g);
+
+/* Bytes of one internal spinor of precision `prec` (tmnd_prec). */
+size_t tmnd_spinor_bytes_prec(const tmnd_gauge *g, int prec);
+
+/* Convert nrhs internal spinors between precisions (F64 <-> S16, F32 -> S16,
+ * F64 <-> F32; same precision copies).  Quantisation to S16 rounds every
+ * component to the nearest multiple of (site max)/32767.  Buffers must not
+ * overlap; device pointers, 16-byte aligned. */
+tmnd_status tmnd_spinor_convert(const tmnd_gauge *g, void *dst, int dst_prec, const void *src, int src_prec,
+                                int nrhs, void *stream);
 
 /* canonical (device) -> internal (device), nrhs right-hand sides.  The two
  * buffers must not overlap.  Layouts as above. */
@@ -104,7 +125,9 @@ tmnd_status tmnd_spinor_unpack(const tmnd_gauge *g, void *dev_canonical, const v
                                int nrhs, void *stream);
 
 /* out = op(in) for nrhs internal spinors (see tmnd_op).  `sigma` is used by
- * TMND_OP_QHAT2 only.  `out` and `in` must not overlap.  Uses the handle's
+ * TMND_OP_QHAT2 only.  With TMND_OP_S16 in `op`, in and out are TMND_S16
+ * spinors and the operator is the sloppy one (FP32 arithmetic on 16-bit links,
+ * intermediates rounded to 16 bits per site).  `out` and `in` must not overlap.  Uses the handle's
  * workspace (one even-site and one odd-site spinor), growing it on first use.
  * (Sec. 2 even-odd Schur complement; Eq. "g5tau1-hermiticity".) */
 tmnd_status tm_nd_apply(tmnd_gauge *g, void *out, const void *in, int op, double sigma,

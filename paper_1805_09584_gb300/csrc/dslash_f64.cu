@@ -241,7 +241,8 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop_odd(Geom g, SiteTerm st, co
                     double2 a0 = __ldg(&ea.aux[i0]), a1 = __ldg(&ea.aux[i1]);
                     double2 w0 = make_double2(fma(ea.sigma, a0.x, y0.x), fma(ea.sigma, a0.y, y0.y));
                     double2 w1 = make_double2(fma(ea.sigma, a1.x, y1.x), fma(ea.sigma, a1.y, y1.y));
-                    double2 r0 = ea.r[i0], r1 = ea.r[i1];
+                    const double2 *rin = ea.r_in ? ea.r_in : ea.r;
+                    double2 r0 = rin[i0], r1 = rin[i1];
                     r0.x = fma(-alpha, w0.x, r0.x); r0.y = fma(-alpha, w0.y, r0.y);
                     r1.x = fma(-alpha, w1.x, r1.x); r1.y = fma(-alpha, w1.y, r1.y);
                     ea.r[i0] = r0;

@@ -87,7 +87,7 @@ extern "C" tmnd_status tmnd_gauge_create(const double *host_links, const tmnd_ac
     TMND_ARG_CHECK(out != nullptr, "tmnd_gauge_create: out is NULL");
     *out = nullptr;
     TMND_ARG_CHECK(host_links != nullptr && act != nullptr, "tmnd_gauge_create: NULL argument");
-    TMND_ARG_CHECK(prec == TMND_F64, "tmnd_gauge_create: unsupported precision %d", prec);
+    TMND_ARG_CHECK(prec == TMND_F64 || prec == TMND_S16, "tmnd_gauge_create: unsupported precision %d", prec);
     for (int d = 0; d < 4; d++)
         TMND_ARG_CHECK(act->dims[d] >= 2 && act->dims[d] % 2 == 0,
                        "tmnd_gauge_create: dims[%d] = %d must be even and >= 2", d, act->dims[d]);
@@ -122,15 +122,21 @@ extern "C" tmnd_status tmnd_gauge_create(const double *host_links, const tmnd_ac
     g->st.kp = kp;
     g->st.kpp = kpp;
     g->st.inv_det = 1.0 / det;
+    g->stf.kappa2 = (float)g->st.kappa2;
+    g->stf.kp = (float)kp;
+    g->stf.kpp = (float)kpp;
+    g->stf.inv_det = (float)g->st.inv_det;
 
     size_t nb = sizeof(double2) * 4 * V * 9;
     double2 *canon = nullptr;
     cudaError_t e = cudaMalloc(&g->links, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&g->links_s16, sizeof(int2) * 3 * 4 * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&canon, nb);
     if (e == cudaSuccess) e = cudaMemcpy(canon, host_links, nb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         long n = 4 * V * 9;
         k_pack_links<<<(unsigned)((n + 255) / 256), 256>>>(g->geom, canon, g->links);
+        launch_pack_links_s16(g->geom, canon, g->links_s16, 0);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -138,6 +144,7 @@ extern "C" tmnd_status tmnd_gauge_create(const double *host_links, const tmnd_ac
     if (e != cudaSuccess) {
         tmnd_set_error("tmnd_gauge_create: %s", cudaGetErrorString(e));
         if (g->links) cudaFree(g->links);
+        if (g->links_s16) cudaFree(g->links_s16);
         delete g;
         return e == cudaErrorMemoryAllocation ? TMND_ERR_OOM : TMND_ERR_CUDA;
     }
@@ -149,6 +156,7 @@ extern "C" void tmnd_gauge_destroy(tmnd_gauge *g) {
     if (!g) return;
     cudaDeviceSynchronize();
     if (g->links) cudaFree(g->links);
+    if (g->links_s16) cudaFree(g->links_s16);
     if (g->work) cudaFree(g->work);
     if (g->partials) cudaFree(g->partials);
     delete g;
@@ -238,9 +246,57 @@ static void apply_mhat(const tmnd_gauge *g, const double2 *in, double2 *out, dou
     launch_hop_odd_f64(g->geom, g->st, g->links, in, te, out, dag, epi, ea, s);
 }
 
+// Sloppy operator on TMND_S16 spinors.
+static tmnd_status apply_s16(tmnd_gauge *g, void *out, const void *in, int op, double sigma, int nrhs,
+                             cudaStream_t s) {
+    const int Vh = g->geom.Vh;
+    const size_t sb = spinor_bytes_prec(Vh, TMND_S16);
+    tmnd_status st = tmnd_ensure_workspace(g, 2 * sb);
+    if (st != TMND_OK) return st;
+    S16Out te = s16_out(g->work, Vh);
+    S16Out yo = s16_out((char *)g->work + sb, Vh);
+    S16In te_in{te.q, te.nrm}, yo_in{yo.q, yo.nrm};
+    S16EpiArgs ea = {};
+    for (int k = 0; k < nrhs; k++) {
+        S16In ik = s16_in((const char *)in + k * sb, Vh);
+        S16Out ok = s16_out((char *)out + k * sb, Vh);
+        switch (op) {
+            case TMND_OP_MHAT:
+            case TMND_OP_MHAT_DAG: {
+                const bool dag = op == TMND_OP_MHAT_DAG;
+                launch_hop_even_s16(g->geom, g->stf, g->links_s16, ik, te, dag, nullptr, s);
+                launch_hop_odd_s16(g->geom, g->stf, g->links_s16, ik, te_in, ok, dag, EPI_STORE, ea, s);
+                break;
+            }
+            case TMND_OP_QHAT2: {
+                launch_hop_even_s16(g->geom, g->stf, g->links_s16, ik, te, false, nullptr, s);
+                launch_hop_odd_s16(g->geom, g->stf, g->links_s16, ik, te_in, yo, false, EPI_STORE, ea, s);
+                S16EpiArgs e2 = {};
+                e2.sigma = sigma;
+                e2.aux = ik;
+                launch_hop_even_s16(g->geom, g->stf, g->links_s16, yo_in, te, true, nullptr, s);
+                launch_hop_odd_s16(g->geom, g->stf, g->links_s16, yo_in, te_in, ok, true, EPI_SHIFT, e2, s);
+                break;
+            }
+            default:
+                tmnd_set_error("tm_nd_apply: op %d not available for TMND_S16 spinors", op);
+                return TMND_ERR_ARG;
+        }
+    }
+    TMND_CUDA_TRY(cudaGetLastError());
+    return TMND_OK;
+}
+
 extern "C" tmnd_status tm_nd_apply(tmnd_gauge *g, void *out, const void *in, int op, double sigma, int nrhs,
                                    void *stream) {
     TMND_ARG_CHECK(g && out && in, "tm_nd_apply: NULL argument");
+    if (op & TMND_OP_S16) {
+        TMND_ARG_CHECK(nrhs >= 1 && out != in && ((uintptr_t)out & 15) == 0 && ((uintptr_t)in & 15) == 0 &&
+                           isfinite(sigma),
+                       "tm_nd_apply: bad arguments");
+        cudaGetLastError();
+        return apply_s16(g, out, in, op & ~TMND_OP_S16, sigma, nrhs, (cudaStream_t)stream);
+    }
     TMND_ARG_CHECK(op >= TMND_OP_MHAT && op <= TMND_OP_QHAT, "tm_nd_apply: unknown op %d", op);
     TMND_ARG_CHECK(nrhs >= 1, "tm_nd_apply: nrhs = %d", nrhs);
     TMND_ARG_CHECK(out != in, "tm_nd_apply: out and in must not alias");

@@ -11,18 +11,31 @@
 //   p_i = zeta_i' r + beta_i p_i;  p = r + beta p
 // and shift i freezes once |zeta_i| |r| <= rho |b| (its residual is zeta_i r).
 //
-// Per iteration the device runs five kernels and never waits for the host:
+// Per iteration the device runs six kernels and never waits for the host:
 //   1 even hop   t = kappa^2 A^-1 H p
 //   2 odd hop    y = Mhat p, with block partials |y|^2, |p|^2
 //                ((p, w) = |Mhat p|^2 + sigma_0 |p|^2, so w is never formed)
 //   3 even hop   t = kappa^2 A(-mu)^-1 H gamma_5 y
-//   4 odd hop    w = Mhat^+ y + sigma_0 p is applied directly: r -= alpha w, block partials |r|^2
+//   4 odd hop    w = Mhat^+ y + sigma_0 p is applied directly: r' = r - alpha w
+//                into the next slot of a ring of WIN residuals, block partials |r'|^2
 //   5 scalars    one thread: deterministic sums of the partials, alpha, beta,
-//                zeta_i', alpha_i, beta_i, freezing, done flag (single state in device memory)
-//   6 update     x_i += alpha_i p_i; p_i = zeta_i' r + beta_i p_i (active shifts); p = r + beta p
-// A block of `check_every` iterations is captured once into a CUDA graph and
-// replayed; every kernel returns at once when the done flag is set, and the
-// host reads the flag between replays (double-buffered, so the GPU never idles).
+//                zeta_i', alpha_i, beta_i, freezing, done flag, and the window
+//                coefficients below (single state in device memory)
+//   6 p update   p = r' + beta p
+// Windowed shift update: the shifted vectors are touched once per WIN
+// iterations.  Within a window starting at iteration k0,
+//   p_i^(k0+j) = P_j p_i^(k0) + sum_{l<j} Q_{j,l} r^(k0+l+1)
+//   x_i^(k0+j) = x_i^(k0) + a_j p_i^(k0) + sum_l e_{j,l} r^(k0+l+1)
+// with P, Q, a, e updated by the scalar kernel from alpha_i, beta_i, zeta_i'
+// (P_{j+1} = beta_i P_j, Q_{j+1,l} = beta_i Q_{j,l}, Q_{j+1,j} = zeta_i',
+//  a += alpha_i P_j, e_l += alpha_i Q_{j,l}), so that one pass at the end of
+// the window applies WIN iterations of the recursion to x_i and p_i (exact
+// algebra: the same recursion, regrouped).  This cuts the shifted vectors'
+// HBM traffic and arithmetic by ~WIN/2.
+// A block of `check_every` iterations (a multiple of WIN) is captured once
+// into a CUDA graph and replayed; every kernel returns at once when the done
+// flag is set, and the host reads the flag between replays (double-buffered,
+// so the GPU never idles).
 #include <math.h>
 #include <string.h>
 
@@ -47,11 +60,14 @@ struct MMSState {
     int status;         // TMND_OK / TMND_ERR_NAN
 };
 
+constexpr int WIN = 8;  // iterations per windowed shift update
+
 struct MMSCoef {
     int skip;           // the solve was already done before this iteration
     double beta;
-    double alpha_i[NS], beta_i[NS], zeta_i[NS];
-    int active[NS];     // shifts updated in this iteration
+    // window coefficients per shift (see the header comment)
+    double P[NS], Q[NS][WIN], a[NS], e[NS][WIN];
+    int touched[NS];    // shift was active during this window
 };
 
 struct MMSConst {
@@ -105,8 +121,9 @@ __global__ void k_init_state(MMSState *st, const double *__restrict__ part, int 
 }
 
 // Scalar step of the recursion (one block; thread 0 does the arithmetic).
+// j = position of this iteration inside its window.
 __global__ void k_scalars(MMSState *st, MMSCoef *cf, const double *__restrict__ part_norm, int nb_hop,
-                          const double *__restrict__ part_rr, MMSConst c) {
+                          const double *__restrict__ part_rr, MMSConst c, int j) {
     __shared__ double red[40];
     const int was_done = st->done;
     double yy = 0, pp = 0, rr_new = 0;
@@ -116,6 +133,14 @@ __global__ void k_scalars(MMSState *st, MMSCoef *cf, const double *__restrict__ 
         rr_new = block_reduce_partials(part_rr, nb_hop, red);
     }
     if (threadIdx.x != 0) return;
+    if (j == 0) {  // a new window starts: x_i and p_i are up to date
+        for (int s = 0; s < c.nshift; s++) {
+            cf->P[s] = 1.0;
+            cf->a[s] = 0.0;
+            cf->touched[s] = 0;
+            for (int l = 0; l < WIN; l++) cf->Q[s][l] = cf->e[s][l] = 0.0;
+        }
+    }
     if (was_done) {
         cf->skip = 1;
         return;
@@ -132,15 +157,21 @@ __global__ void k_scalars(MMSState *st, MMSCoef *cf, const double *__restrict__ 
     cf->beta = beta;
     const int it = st->iter + 1;
     for (int s = 0; s < c.nshift; s++) {
-        cf->active[s] = st->active[s];
         if (!st->active[s]) continue;
         const double z = st->zeta[s], zo = st->zeta_old[s];
         const double zn = z * zo * st->alpha_old /
                           (alpha * st->beta_old * (zo - z) + zo * st->alpha_old * (1.0 + alpha * c.delta[s]));
         const double ratio = zn / z;
-        cf->alpha_i[s] = alpha * ratio;
-        cf->beta_i[s] = beta * ratio * ratio;
-        cf->zeta_i[s] = zn;
+        const double al = alpha * ratio;        // alpha_i
+        const double be = beta * ratio * ratio; // beta_i
+        // x_i += alpha_i p_i, with p_i = P p_i(k0) + sum_{l<j} Q_l r_l
+        cf->a[s] += al * cf->P[s];
+        for (int l = 0; l < j; l++) cf->e[s][l] += al * cf->Q[s][l];
+        // p_i <- zeta_i' r' + beta_i p_i, r' in slot j
+        cf->P[s] *= be;
+        for (int l = 0; l < j; l++) cf->Q[s][l] *= be;
+        cf->Q[s][j] = zn;
+        cf->touched[s] = 1;
         st->zeta_old[s] = z;
         st->zeta[s] = zn;
         if (s < c.nsolve && zn * zn * rr_new <= c.rho2 * st->bb) {
@@ -155,45 +186,71 @@ __global__ void k_scalars(MMSState *st, MMSCoef *cf, const double *__restrict__ 
     if (!st->active[c.nsolve - 1] || it >= c.maxiter) st->done = 1;
 }
 
-// Fused multi-shift update: the dominant HBM stream of the iteration at many shifts.
-__global__ void __launch_bounds__(UPD_THREADS) k_update(long n, const MMSCoef *__restrict__ cf, const double2 *__restrict__ r,
-                                                        double2 *__restrict__ p, ShiftPtrs sp, int nshift) {
-    __shared__ double s_a[NS], s_b[NS], s_z[NS];
+// p = r' + beta p (base search direction, every iteration)
+__global__ void k_pupdate(long n, const MMSCoef *__restrict__ cf, const double2 *__restrict__ r,
+                          double2 *__restrict__ p) {
+    if (cf->skip) return;
+    const double beta = cf->beta;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double2 rv = r[i], pv = p[i];
+        p[i] = make_double2(fma(beta, pv.x, rv.x), fma(beta, pv.y, rv.y));
+    }
+}
+
+// Windowed multi-shift update (end of each window): for every shift active
+// in the window, x_i += a p_i + sum_l e_l r_l and p_i = P p_i + sum_l Q_l r_l
+// over the WIN residuals of the window.  The dominant HBM stream of the
+// iteration at many shifts, now once per WIN iterations.
+struct RingPtrs {
+    const double2 *r[WIN];
+};
+
+__global__ void __launch_bounds__(UPD_THREADS) k_window(long n, const MMSCoef *__restrict__ cf, RingPtrs ring,
+                                                        ShiftPtrs sp, int nshift) {
+    __shared__ double s_P[NS], s_a[NS], s_Q[NS][WIN], s_e[NS][WIN];
     __shared__ int s_idx[NS];
     __shared__ int s_n;
-    __shared__ double s_beta;
-    if (cf->skip) return;
     if (threadIdx.x == 0) {
         int m = 0;
         for (int s = 0; s < nshift; s++)
-            if (cf->active[s]) {
+            if (cf->touched[s]) {
                 s_idx[m] = s;
-                s_a[m] = cf->alpha_i[s];
-                s_b[m] = cf->beta_i[s];
-                s_z[m] = cf->zeta_i[s];
+                s_P[m] = cf->P[s];
+                s_a[m] = cf->a[s];
+                for (int l = 0; l < WIN; l++) {
+                    s_Q[m][l] = cf->Q[s][l];
+                    s_e[m][l] = cf->e[s][l];
+                }
                 m++;
             }
         s_n = m;
-        s_beta = cf->beta;
     }
     __syncthreads();
     const int m = s_n;
-    const double beta = s_beta;
+    if (m == 0) return;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const double2 rv = r[i];
-        const double2 pv = p[i];
+        double2 rv[WIN];
+#pragma unroll
+        for (int l = 0; l < WIN; l++) rv[l] = ring.r[l][i];
         for (int k = 0; k < m; k++) {
             const int s = s_idx[k];
             double2 *xs = sp.x[s];
             double2 *ps = sp.p[s];
             const double2 pi = ps[i];
             double2 xv = xs[i];
+            double2 pn = make_double2(s_P[k] * pi.x, s_P[k] * pi.y);
             xv.x = fma(s_a[k], pi.x, xv.x);
             xv.y = fma(s_a[k], pi.y, xv.y);
+#pragma unroll
+            for (int l = 0; l < WIN; l++) {
+                xv.x = fma(s_e[k][l], rv[l].x, xv.x);
+                xv.y = fma(s_e[k][l], rv[l].y, xv.y);
+                pn.x = fma(s_Q[k][l], rv[l].x, pn.x);
+                pn.y = fma(s_Q[k][l], rv[l].y, pn.y);
+            }
             xs[i] = xv;
-            ps[i] = make_double2(fma(s_z[k], rv.x, s_b[k] * pi.x), fma(s_z[k], rv.y, s_b[k] * pi.y));
+            ps[i] = pn;
         }
-        p[i] = make_double2(fma(beta, pv.x, rv.x), fma(beta, pv.y, rv.y));
     }
 }
 
@@ -223,21 +280,27 @@ int stream_blocks(long n) {
 
 }  // namespace
 
-// One right-hand side.  work holds r, p, y, te, p_i[nshift] (spinor-sized each).
+// One right-hand side.  work holds the WIN residual slots, p, y, te, p_i[nshift]
+// (spinor-sized each).  Residual r^(k0+j+1) of window position j goes to slot
+// j; position 0 reads slot WIN-1 (the last residual of the previous window,
+// or b at the start).
 static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *x, const double *sigma, int nshift,
                                int nsolve, double rho, int maxiter, int check_every, int profile,
                                tmnd_solve_info *info, cudaStream_t s, int rhs_index) {
     const size_t sp = tmnd_spinor_bytes(g);
     const long n = (long)(sp / sizeof(double2));
     char *w = (char *)g->work;
-    double2 *r = (double2 *)(w + 0 * sp);
-    double2 *p = (double2 *)(w + 1 * sp);
-    double2 *y = (double2 *)(w + 2 * sp);
-    double2 *te = (double2 *)(w + 3 * sp);
+    double2 *slot[WIN];
+    RingPtrs ring;
+    for (int l = 0; l < WIN; l++) ring.r[l] = slot[l] = (double2 *)(w + l * sp);
+    double2 *r = slot[WIN - 1];
+    double2 *p = (double2 *)(w + (WIN + 0) * sp);
+    double2 *y = (double2 *)(w + (WIN + 1) * sp);
+    double2 *te = (double2 *)(w + (WIN + 2) * sp);
     ShiftPtrs ptrs = {};
     for (int i = 0; i < nshift; i++) {
         ptrs.x[i] = x[i] + (size_t)rhs_index * n;
-        ptrs.p[i] = (double2 *)(w + (4 + i) * sp);
+        ptrs.p[i] = (double2 *)(w + (WIN + 3 + i) * sp);
     }
     // small device area after the partials
     const int nb_hop = hop_blocks(g->geom);
@@ -277,6 +340,7 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
         cudaGraph_t graph = nullptr;
         TMND_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         for (int k = 0; k < check_every; k++) {
+            const int j = k % WIN;  // position inside the window
             if (profile) cudaEventRecordWithFlags(ev(inst, k, 0), s, cudaEventRecordExternal);
             HopEpiArgs e1 = {};
             e1.part_out = part_norm;
@@ -287,7 +351,8 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
             HopEpiArgs e2 = {};
             e2.sigma = c.sigma0;
             e2.aux = p;
-            e2.r = r;
+            e2.r_in = slot[(j + WIN - 1) % WIN];
+            e2.r = slot[j];
             e2.part_out = part_rr;
             e2.part_in = part_norm;
             e2.npart_in = nb_hop;
@@ -295,8 +360,9 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
             e2.done = &st->done;
             launch_hop_odd_f64(g->geom, g->st, g->links, y, te, nullptr, true, EPI_MMS_R, e2, s);
             if (profile) cudaEventRecordWithFlags(ev(inst, k, 1), s, cudaEventRecordExternal);
-            k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c);
-            k_update<<<nb_str, UPD_THREADS, 0, s>>>(n, cf, r, p, ptrs, nshift);
+            k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c, j);
+            k_pupdate<<<nb_str, UPD_THREADS, 0, s>>>(n, cf, slot[j], p);
+            if (j == WIN - 1) k_window<<<nb_str, UPD_THREADS, 0, s>>>(n, cf, ring, ptrs, nshift);
             if (profile) cudaEventRecordWithFlags(ev(inst, k, 2), s, cudaEventRecordExternal);
         }
         cudaError_t ce = cudaStreamEndCapture(s, &graph);
@@ -357,7 +423,7 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
         tmnd_set_error("mms_cg_solve: %s", cudaGetErrorString(err));
         return TMND_ERR_CUDA;
     }
-    if (info) info->launches += 2 + nlaunch * (long long)check_every * 6 + 5LL * nshift;
+    if (info) info->launches += 2 + nlaunch * ((long long)check_every * 6 + check_every / WIN) + 5LL * nshift;
 
     MMSState hs;
     TMND_CUDA_TRY(cudaMemcpy(&hs, st, sizeof hs, cudaMemcpyDeviceToHost));
@@ -431,11 +497,12 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     TMND_ARG_CHECK(nsolve <= nshift, "mms_cg_solve: nsolve = %d > nshift", nsolve);
     TMND_ARG_CHECK(params->rho > 0 && params->rho < 1, "mms_cg_solve: rho = %g not in (0, 1)", params->rho);
     TMND_ARG_CHECK(params->maxiter >= 1, "mms_cg_solve: maxiter = %d", params->maxiter);
-    const int check_every = params->check_every > 0 ? params->check_every : 32;
+    int check_every = params->check_every > 0 ? params->check_every : 32;
     TMND_ARG_CHECK(check_every <= 4096, "mms_cg_solve: check_every too large");
+    check_every = (check_every + WIN - 1) / WIN * WIN;  // whole windows per graph replay
 
     const size_t sp = tmnd_spinor_bytes(g);
-    tmnd_status st = tmnd_ensure_workspace(g, (4 + (size_t)nshift) * sp);
+    tmnd_status st = tmnd_ensure_workspace(g, (WIN + 3 + (size_t)nshift) * sp);
     if (st != TMND_OK) return st;
     const long n = (long)(sp / sizeof(double2));
     size_t pbytes = sizeof(double) * (3 * (size_t)hop_blocks(g->geom) + stream_blocks(n)) + 256 + 2 * 4096 +

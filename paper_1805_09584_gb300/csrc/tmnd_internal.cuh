@@ -46,6 +46,11 @@ struct SiteTerm {
     double inv_det; // 1 / (1 + kp^2 - kpp^2)
 };
 
+// Site term in FP32 for the sloppy kernels.
+struct SiteTermF {
+    float kappa2, kp, kpp, inv_det;
+};
+
 // Gauge handle.
 struct tmnd_gauge {
     tmnd_action act;
@@ -54,6 +59,8 @@ struct tmnd_gauge {
     Geom geom;
     SiteTerm st;
     double2 *links;        // [2 parity][4 mu][9][Vh] complex, U_mu(x) stored at the parity/half-index of x
+    int2 *links_s16;       // [2 parity][4 mu][3][Vh]: rows 0, 1 as int16 pairs (scale 32767)
+    SiteTermF stf;         // FP32 copy of st for the sloppy kernels
     void *work;            // grow-only workspace
     size_t work_bytes;
     double2 *partials;     // reduction partials (grow-only, separate from work)
@@ -141,7 +148,8 @@ constexpr int HOP_THREADS = 128;
 struct HopEpiArgs {
     double sigma;
     const double2 *aux;     // EPI_SHIFT / EPI_MMS_R: the vector multiplied by sigma
-    double2 *r;             // EPI_MMS_R: residual updated in place
+    double2 *r;             // EPI_MMS_R: updated residual (written)
+    const double2 *r_in;    // EPI_MMS_R: residual before the update (NULL: update r in place)
     double *part_out;       // partial sums written per block (EPI_STORE_NORMS: 2 per block; EPI_MMS_R: 1)
     const double *part_in;  // EPI_MMS_R: partials of |y|^2, |p|^2 from the previous kernel
     int npart_in;           // number of blocks that wrote part_in
@@ -158,3 +166,45 @@ void launch_hop_odd_f64(const Geom &g, const SiteTerm &st, const double2 *links,
                         cudaStream_t s);
 // Number of blocks (= reduction partials) of every hop launch for this geometry.
 int hop_blocks(const Geom &g);
+
+// ------------------------------------------------- sloppy (16-bit) path
+
+// 16-bit spinor of one right-hand side: 6 int4 planes over V/2 sites, then V/2 floats (scale).
+struct S16In {
+    const int4 *q;
+    const float *nrm;
+};
+struct S16Out {
+    int4 *q;
+    float *nrm;
+};
+constexpr size_t S16_BYTES_PER_SITE = 6 * 16 + 4;
+__host__ __device__ inline S16In s16_in(const void *base, int Vh) {
+    return S16In{(const int4 *)base, (const float *)((const char *)base + 96 * (size_t)Vh)};
+}
+__host__ __device__ inline S16Out s16_out(void *base, int Vh) {
+    return S16Out{(int4 *)base, (float *)((char *)base + 96 * (size_t)Vh)};
+}
+
+struct S16EpiArgs {
+    double sigma;
+    S16In aux;              // EPI_SHIFT / EPI_MMS_R: vector multiplied by sigma
+    float2 *r;              // EPI_MMS_R: updated residual (FP32 planes, written)
+    const float2 *r_in;     // EPI_MMS_R: residual before the update
+    double *part_out;
+    const double *part_in;
+    int npart_in;
+    const double *rr;
+    const int *done;
+};
+
+int hop_blocks_s16(const Geom &g);
+void launch_hop_even_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In in, S16Out out, bool dag,
+                         const int *done, cudaStream_t s);
+void launch_hop_odd_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In psi, S16In te, S16Out out,
+                        bool dag, HopEpi epi, const S16EpiArgs &ea, cudaStream_t s);
+
+void launch_pack_links_s16(const Geom &g, const double2 *canon, int2 *out, cudaStream_t s);
+size_t spinor_bytes_prec(int Vh, int prec);
+tmnd_status convert_spinor(int Vh, void *dst, int dst_prec, const void *src, int src_prec, int nrhs,
+                           cudaStream_t s);
