@@ -176,6 +176,14 @@ typedef struct {
     int check_every;       /* iterations between host convergence checks (0 = 32) */
     int profile;           /* 1: time the stencil and update kernels of every iteration with
                               CUDA events (filled into hop_ms / update_ms) */
+    int prec;              /* TMND_F64 (0): plain FP64 multi-shift CG.
+                              TMND_S16: mixed precision.  A sloppy multi-shift CG (FP32
+                              arithmetic, 16-bit stencil vectors and links, FP32 residual,
+                              FP64 dot-product accumulation) down to rho_inner, then FP64
+                              defect correction per shift: FP64 true residual, sloppy CG on
+                              the defect to rho_inner, FP64 update, until every required
+                              shift's FP64 true residual is <= rho. */
+    double rho_inner;      /* TMND_S16: relative tolerance of each sloppy solve (0 = 1e-5) */
 } tmnd_solve_params;
 
 typedef struct {
@@ -189,6 +197,10 @@ typedef struct {
     double update_ms;                      /* profile: device time of the scalar + multi-shift
                                               update launches, summed likewise */
     long long launches;                    /* kernels this call launched (early-exit ones included) */
+    int refine_rounds;                     /* TMND_S16: defect-correction rounds (max over RHS) */
+    int refine_iters;                      /* TMND_S16: sloppy CG iterations of the corrections (sum) */
+    int fp64_applies;                      /* FP64 applications of Qhat^2 + sigma (certification and
+                                              defect correction, summed over RHS) */
 } tmnd_solve_info;
 
 /* Multi-mass-shift CG (Sec. 1 "standard" solver; Sec. 4.2.2) for

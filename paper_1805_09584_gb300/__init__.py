@@ -19,14 +19,16 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtmnd.so")
 MAX_SHIFTS = 32
 
-TMND_F64 = 0
+TMND_F64, TMND_F32, TMND_S16 = 0, 1, 2
 OP_MHAT, OP_MHAT_DAG, OP_QHAT2, OP_QHAT = 0, 1, 2, 3
+OP_S16 = 16  # flag: sloppy operator on TMND_S16 spinors
 
 STATUS = {0: "TMND_OK", 1: "TMND_ERR_ARG", 2: "TMND_ERR_CUDA", 3: "TMND_ERR_OOM", 4: "TMND_ERR_NOCONV",
           5: "TMND_ERR_NAN", 6: "TMND_ERR_TIMEOUT", 7: "TMND_ERR_NOTSU3"}
 
 # every entry point declared in include/tmnd.h
-EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd_spinor_pack",
+EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd_spinor_bytes_prec",
+           "tmnd_spinor_convert", "tmnd_spinor_pack",
            "tmnd_spinor_unpack", "tm_nd_apply", "tm_nd_apply_noalloc", "mms_cg_solve", "lagrange_guess",
            "tmnd_last_error")
 NOALLOC_MAX_VH = 32768
@@ -45,13 +47,15 @@ class Action(ctypes.Structure):
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("maxiter", ctypes.c_int), ("nsolve", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("profile", ctypes.c_int), ("prec", ctypes.c_int),
+                ("rho_inner", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("conv_iter", ctypes.c_int * MAX_SHIFTS),
                 ("true_res", ctypes.c_double * MAX_SHIFTS), ("zeta", ctypes.c_double * MAX_SHIFTS),
-                ("hop_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("launches", ctypes.c_longlong)]
+                ("hop_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("launches", ctypes.c_longlong),
+                ("refine_rounds", ctypes.c_int), ("refine_iters", ctypes.c_int), ("fp64_applies", ctypes.c_int)]
 
 
 _lib = None
@@ -71,6 +75,10 @@ def lib() -> ctypes.CDLL:
         L.tmnd_gauge_destroy.restype = None
         L.tmnd_spinor_bytes.argtypes = [vp]
         L.tmnd_spinor_bytes.restype = ctypes.c_size_t
+        L.tmnd_spinor_bytes_prec.argtypes = [vp, i]
+        L.tmnd_spinor_bytes_prec.restype = ctypes.c_size_t
+        L.tmnd_spinor_convert.argtypes = [vp, vp, i, vp, i, i, vp]
+        L.tmnd_spinor_convert.restype = ctypes.c_int
         L.tmnd_spinor_pack.argtypes = [vp, vp, vp, i, vp]
         L.tmnd_spinor_unpack.argtypes = [vp, vp, vp, i, vp]
         L.tm_nd_apply.argtypes = [vp, vp, vp, i, d, i, vp]
@@ -133,6 +141,15 @@ def tmnd_spinor_bytes(h) -> int:
     return int(lib().tmnd_spinor_bytes(h))
 
 
+def tmnd_spinor_bytes_prec(h, prec: int) -> int:
+    return int(lib().tmnd_spinor_bytes_prec(h, int(prec)))
+
+
+def tmnd_spinor_convert(h, dst, dst_prec: int, src, src_prec: int, nrhs: int = 1, stream=None) -> None:
+    _check(lib().tmnd_spinor_convert(h, _ptr(dst), int(dst_prec), _ptr(src), int(src_prec), int(nrhs),
+                                     _stream(stream)))
+
+
 def tmnd_spinor_pack(h, dev_internal, dev_canonical, nrhs: int = 1, stream=None) -> None:
     _check(lib().tmnd_spinor_pack(h, _ptr(dev_internal), _ptr(dev_canonical), int(nrhs), _stream(stream)))
 
@@ -153,17 +170,21 @@ def tm_nd_apply_noalloc(h, out, inp, op: int, sigma: float = 0.0, nrhs: int = 1,
 
 
 def mms_cg_solve(h, b, nrhs: int, sigma, x, rho: float = 1e-10, maxiter: int = 100000, nsolve: int = 0,
-                 check_every: int = 0, profile: bool = False, stream=None) -> dict:
+                 check_every: int = 0, profile: bool = False, prec: int = TMND_F64, rho_inner: float = 0.0,
+                 stream=None) -> dict:
     sig = np.ascontiguousarray(sigma, dtype=np.float64)
     ns = len(sig)
     xs = (ctypes.c_void_p * ns)(*[_ptr(v) for v in x])
-    p = SolveParams(float(rho), int(maxiter), int(nsolve), int(check_every), int(bool(profile)))
+    p = SolveParams(float(rho), int(maxiter), int(nsolve), int(check_every), int(bool(profile)), int(prec),
+                    float(rho_inner))
     info = SolveInfo()
     st = lib().mms_cg_solve(h, _ptr(b), int(nrhs), sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns, xs,
                             ctypes.byref(p), ctypes.byref(info), _stream(stream))
     out = {"status": st, "iters": info.iters, "conv_iter": list(info.conv_iter[:ns]),
            "true_res": list(info.true_res[:ns]), "zeta": list(info.zeta[:ns]),
-           "hop_ms": info.hop_ms, "update_ms": info.update_ms, "launches": info.launches}
+           "hop_ms": info.hop_ms, "update_ms": info.update_ms, "launches": info.launches,
+           "refine_rounds": info.refine_rounds, "refine_iters": info.refine_iters,
+           "fp64_applies": info.fp64_applies}
     _check(st)
     return out
 
@@ -205,10 +226,21 @@ class Gauge:
         except Exception:
             pass
 
-    def spinor(self, nrhs: int = 1, device="cuda"):
-        """A new internal-layout spinor buffer (torch complex128, nrhs * 24 * V/2)."""
+    def spinor(self, nrhs: int = 1, device="cuda", prec: int = TMND_F64):
+        """A new internal-layout spinor buffer: complex128 (TMND_F64), complex64
+        (TMND_F32) or raw 16-byte words (TMND_S16), nrhs right-hand sides."""
         import torch
-        return torch.empty(nrhs * 24 * self.vh, dtype=torch.complex128, device=device)
+        if prec == TMND_F64:
+            return torch.empty(nrhs * 24 * self.vh, dtype=torch.complex128, device=device)
+        if prec == TMND_F32:
+            return torch.empty(nrhs * 24 * self.vh, dtype=torch.complex64, device=device)
+        nbytes = tmnd_spinor_bytes_prec(self.handle, prec) * nrhs
+        return torch.empty(nbytes // 4, dtype=torch.int32, device=device)
+
+    def convert(self, src, src_prec: int, dst_prec: int, nrhs: int = 1, stream=None):
+        out = self.spinor(nrhs, src.device, dst_prec)
+        tmnd_spinor_convert(self.handle, out, dst_prec, src, src_prec, nrhs, stream)
+        return out
 
     def pack(self, canonical, nrhs: int = 1, stream=None):
         out = self.spinor(nrhs, canonical.device)

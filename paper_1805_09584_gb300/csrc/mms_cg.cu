@@ -77,10 +77,12 @@ struct MMSConst {
     double rho2;        // rho^2
 };
 
-struct ShiftPtrs {
-    double2 *x[NS];
-    double2 *p[NS];
+template <typename T>
+struct ShiftPtrsT {
+    T *x[NS];
+    T *p[NS];
 };
+using ShiftPtrs = ShiftPtrsT<double2>;
 
 __global__ void k_init(long n, const double2 *__restrict__ b, double2 *__restrict__ r, double2 *__restrict__ p,
                        ShiftPtrs sp, int nshift, double *__restrict__ part) {
@@ -201,12 +203,16 @@ __global__ void k_pupdate(long n, const MMSCoef *__restrict__ cf, const double2 
 // in the window, x_i += a p_i + sum_l e_l r_l and p_i = P p_i + sum_l Q_l r_l
 // over the WIN residuals of the window.  The dominant HBM stream of the
 // iteration at many shifts, now once per WIN iterations.
-struct RingPtrs {
-    const double2 *r[WIN];
+template <typename T>
+struct RingPtrsT {
+    const T *r[WIN];
 };
+using RingPtrs = RingPtrsT<double2>;
 
-__global__ void __launch_bounds__(UPD_THREADS) k_window(long n, const MMSCoef *__restrict__ cf, RingPtrs ring,
-                                                        ShiftPtrs sp, int nshift) {
+// T = double2 (FP64 path) or float2 (sloppy path; coefficients rounded to FP32)
+template <typename T>
+__global__ void __launch_bounds__(UPD_THREADS) k_window(long n, const MMSCoef *__restrict__ cf, RingPtrsT<T> ring,
+                                                        ShiftPtrsT<T> sp, int nshift) {
     __shared__ double s_P[NS], s_a[NS], s_Q[NS][WIN], s_e[NS][WIN];
     __shared__ int s_idx[NS];
     __shared__ int s_n;
@@ -228,25 +234,28 @@ __global__ void __launch_bounds__(UPD_THREADS) k_window(long n, const MMSCoef *_
     __syncthreads();
     const int m = s_n;
     if (m == 0) return;
+    using R = decltype(T::x);
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        double2 rv[WIN];
+        T rv[WIN];
 #pragma unroll
         for (int l = 0; l < WIN; l++) rv[l] = ring.r[l][i];
         for (int k = 0; k < m; k++) {
             const int s = s_idx[k];
-            double2 *xs = sp.x[s];
-            double2 *ps = sp.p[s];
-            const double2 pi = ps[i];
-            double2 xv = xs[i];
-            double2 pn = make_double2(s_P[k] * pi.x, s_P[k] * pi.y);
-            xv.x = fma(s_a[k], pi.x, xv.x);
-            xv.y = fma(s_a[k], pi.y, xv.y);
+            T *xs = sp.x[s];
+            T *ps = sp.p[s];
+            const T pi = ps[i];
+            T xv = xs[i];
+            T pn;
+            pn.x = (R)s_P[k] * pi.x;
+            pn.y = (R)s_P[k] * pi.y;
+            xv.x = fma((R)s_a[k], pi.x, xv.x);
+            xv.y = fma((R)s_a[k], pi.y, xv.y);
 #pragma unroll
             for (int l = 0; l < WIN; l++) {
-                xv.x = fma(s_e[k][l], rv[l].x, xv.x);
-                xv.y = fma(s_e[k][l], rv[l].y, xv.y);
-                pn.x = fma(s_Q[k][l], rv[l].x, pn.x);
-                pn.y = fma(s_Q[k][l], rv[l].y, pn.y);
+                xv.x = fma((R)s_e[k][l], rv[l].x, xv.x);
+                xv.y = fma((R)s_e[k][l], rv[l].y, xv.y);
+                pn.x = fma((R)s_Q[k][l], rv[l].x, pn.x);
+                pn.y = fma((R)s_Q[k][l], rv[l].y, pn.y);
             }
             xs[i] = xv;
             ps[i] = pn;
@@ -268,6 +277,88 @@ __global__ void k_diff_norm(long n, const double2 *__restrict__ b, const double2
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+
+// ------------------------------------------------------------ sloppy path
+// One site per thread: r = b, p = quantise(b), p_i = b, x_i = 0, partial |b|^2.
+__global__ void k_init_s(int Vh, const float2 *__restrict__ b, float2 *__restrict__ r, S16Out p,
+                         ShiftPtrsT<float2> sp, int nshift, double *__restrict__ part) {
+    __shared__ double red[40];
+    double acc = 0.0;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        float v[24][2];
+        float a = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 24; c++) {
+            const float2 bv = b[(size_t)c * Vh + h];
+            v[c][0] = bv.x;
+            v[c][1] = bv.y;
+            r[(size_t)c * Vh + h] = bv;
+            a = fmaf(bv.x, bv.x, fmaf(bv.y, bv.y, a));
+            for (int s = 0; s < nshift; s++) {
+                sp.p[s][(size_t)c * Vh + h] = bv;
+                sp.x[s][(size_t)c * Vh + h] = make_float2(0.f, 0.f);
+            }
+        }
+        s16_store_site(p, Vh, h, v);
+        acc += a;
+    }
+    double t = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// p = r' + beta p, p stored in 16 bits (in place, one site per thread)
+__global__ void k_pupdate_s(int Vh, const MMSCoef *__restrict__ cf, const float2 *__restrict__ r, S16Out p) {
+    if (cf->skip) return;
+    const float beta = (float)cf->beta;
+    const S16In pin{p.q, p.nrm};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        float v[24][2];
+        s16_load_site(pin, Vh, h, v);
+#pragma unroll
+        for (int c = 0; c < 24; c++) {
+            const float2 rv = r[(size_t)c * Vh + h];
+            v[c][0] = fmaf(beta, v[c][0], rv.x);
+            v[c][1] = fmaf(beta, v[c][1], rv.y);
+        }
+        s16_store_site(p, Vh, h, v);
+    }
+}
+
+// x += (double) e  (FP64 accumulation of a sloppy correction)
+__global__ void k_add_f32_to_f64(long n, const float2 *__restrict__ e, double2 *__restrict__ x) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float2 d = e[i];
+        double2 v = x[i];
+        v.x += (double)d.x;
+        v.y += (double)d.y;
+        x[i] = v;
+    }
+}
+
+// r = b - y in FP64 and block partials |r|^2 (true residual of the refinement)
+__global__ void k_resid(long n, const double2 *__restrict__ b, const double2 *__restrict__ y,
+                        double2 *__restrict__ r, double *__restrict__ part) {
+    __shared__ double red[40];
+    double acc = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double2 u = b[i], v = y[i];
+        const double2 d = make_double2(u.x - v.x, u.y - v.y);
+        r[i] = d;
+        acc = fma(d.x, d.x, fma(d.y, d.y, acc));
+    }
+    double t = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+int site_blocks(int Vh) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+    long want = (Vh + 127) / 128, cap = (long)sms * 8;
+    return (int)(want < cap ? want : cap);
+}
+
 int stream_blocks(long n) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -276,6 +367,102 @@ int stream_blocks(long n) {
     long want = (n + UPD_THREADS - 1) / UPD_THREADS;
     long cap = (long)sms * 8;   // 8 resident 256-thread blocks per SM
     return (int)(want < cap ? want : cap);
+}
+
+
+// Capture `check_every` iterations of `body` into a CUDA graph and replay it
+// until the device-side done flag is set (or the iteration budget is spent).
+// The host reads the flag of replay j-1 while replay j runs.  With profiling,
+// body calls mark(0/1/2) to place event-record nodes; two graph instances
+// alternate so that one instance's events are read while the other runs.
+struct LoopOut {
+    long nlaunch = 0;
+    std::vector<float> hop_t, upd_t;  // per iteration (profiling only)
+};
+
+template <typename Body>
+tmnd_status run_graph_loop(cudaStream_t s, const int *done_dev, int maxiter, int check_every, int profile, Body body,
+                           LoopOut &out) {
+    const int ninst = profile ? 2 : 1;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> evs;  // [inst][k][3]
+    if (profile) {
+        evs.resize((size_t)ninst * check_every * 3);
+        for (auto &e : evs) cudaEventCreate(&e);
+    }
+    auto ev = [&](int inst, int k, int j) { return evs[((size_t)inst * check_every + k) * 3 + j]; };
+    auto cleanup = [&]() {
+        for (int inst = 0; inst < ninst; inst++)
+            if (exec[inst]) cudaGraphExecDestroy(exec[inst]);
+        for (auto &e : evs) cudaEventDestroy(e);
+    };
+    for (int inst = 0; inst < ninst; inst++) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            for (int k = 0; k < check_every; k++) {
+                auto mark = [&](int which) {
+                    if (profile) cudaEventRecordWithFlags(ev(inst, k, which), s, cudaEventRecordExternal);
+                };
+                body(k, mark);
+            }
+            ce = cudaStreamEndCapture(s, &graph);
+        }
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec[inst], graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            cleanup();
+            tmnd_set_error("mms_cg_solve: graph capture failed: %s", cudaGetErrorString(ce));
+            return TMND_ERR_CUDA;
+        }
+    }
+    int *flags = nullptr;  // pinned [2]
+    cudaEvent_t fev[2];
+    cudaError_t err = cudaHostAlloc((void **)&flags, 2 * sizeof(int), cudaHostAllocDefault);
+    if (err != cudaSuccess) {
+        cleanup();
+        tmnd_set_error("mms_cg_solve: cudaHostAlloc: %s", cudaGetErrorString(err));
+        return TMND_ERR_CUDA;
+    }
+    cudaEventCreateWithFlags(&fev[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&fev[1], cudaEventDisableTiming);
+    auto harvest = [&](long j) {  // read the events of replay j (complete)
+        int inst = (int)(j % ninst);
+        for (int k = 0; k < check_every; k++) {
+            float a = 0.f, b2 = 0.f;
+            if (cudaEventElapsedTime(&a, ev(inst, k, 0), ev(inst, k, 1)) != cudaSuccess ||
+                cudaEventElapsedTime(&b2, ev(inst, k, 1), ev(inst, k, 2)) != cudaSuccess) {
+                cudaGetLastError();
+                a = b2 = nanf("");
+            }
+            out.hop_t.push_back(a);
+            out.upd_t.push_back(b2);
+        }
+    };
+    const long max_launch = (long)maxiter / check_every + 3;
+    for (long j = 0; j < max_launch && err == cudaSuccess; j++) {
+        err = cudaGraphLaunch(exec[j % ninst], s);
+        if (err != cudaSuccess) break;
+        out.nlaunch++;
+        cudaMemcpyAsync(&flags[j & 1], done_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(fev[j & 1], s);
+        if (j > 0) {
+            err = cudaEventSynchronize(fev[(j - 1) & 1]);
+            if (err == cudaSuccess && profile) harvest(j - 1);
+            if (err == cudaSuccess && flags[(j - 1) & 1]) break;
+        }
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err == cudaSuccess && profile && out.nlaunch > 0) harvest(out.nlaunch - 1);
+    cudaEventDestroy(fev[0]);
+    cudaEventDestroy(fev[1]);
+    cudaFreeHost(flags);
+    cleanup();
+    if (err != cudaSuccess) {
+        tmnd_set_error("mms_cg_solve: %s", cudaGetErrorString(err));
+        return TMND_ERR_CUDA;
+    }
+    return TMND_OK;
 }
 
 }  // namespace
@@ -325,105 +512,41 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
     k_init_state<<<1, 256, 0, s>>>(st, part_str, nb_str, c);
     TMND_CUDA_TRY(cudaGetLastError());
 
-    // Capture one block of `check_every` iterations into a graph.  With
-    // profiling, two instances alternate so that the events of one replay are
-    // read on the host while the other replay runs.
-    const int ninst = profile ? 2 : 1;
-    cudaGraphExec_t exec[2] = {nullptr, nullptr};
-    std::vector<cudaEvent_t> evs;  // [inst][k][3]
-    if (profile) {
-        evs.resize((size_t)ninst * check_every * 3);
-        for (auto &e : evs) cudaEventCreate(&e);
-    }
-    auto ev = [&](int inst, int k, int j) { return evs[((size_t)inst * check_every + k) * 3 + j]; };
-    for (int inst = 0; inst < ninst; inst++) {
-        cudaGraph_t graph = nullptr;
-        TMND_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < check_every; k++) {
-            const int j = k % WIN;  // position inside the window
-            if (profile) cudaEventRecordWithFlags(ev(inst, k, 0), s, cudaEventRecordExternal);
-            HopEpiArgs e1 = {};
-            e1.part_out = part_norm;
-            e1.done = &st->done;
-            launch_hop_even_f64(g->geom, g->st, g->links, p, te, false, &st->done, s);
-            launch_hop_odd_f64(g->geom, g->st, g->links, p, te, y, false, EPI_STORE_NORMS, e1, s);
-            launch_hop_even_f64(g->geom, g->st, g->links, y, te, true, &st->done, s);
-            HopEpiArgs e2 = {};
-            e2.sigma = c.sigma0;
-            e2.aux = p;
-            e2.r_in = slot[(j + WIN - 1) % WIN];
-            e2.r = slot[j];
-            e2.part_out = part_rr;
-            e2.part_in = part_norm;
-            e2.npart_in = nb_hop;
-            e2.rr = &st->rr;
-            e2.done = &st->done;
-            launch_hop_odd_f64(g->geom, g->st, g->links, y, te, nullptr, true, EPI_MMS_R, e2, s);
-            if (profile) cudaEventRecordWithFlags(ev(inst, k, 1), s, cudaEventRecordExternal);
-            k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c, j);
-            k_pupdate<<<nb_str, UPD_THREADS, 0, s>>>(n, cf, slot[j], p);
-            if (j == WIN - 1) k_window<<<nb_str, UPD_THREADS, 0, s>>>(n, cf, ring, ptrs, nshift);
-            if (profile) cudaEventRecordWithFlags(ev(inst, k, 2), s, cudaEventRecordExternal);
-        }
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec[inst], graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) {
-            for (auto &e : evs) cudaEventDestroy(e);
-            if (exec[0]) cudaGraphExecDestroy(exec[0]);
-            tmnd_set_error("mms_cg_solve: graph capture failed: %s", cudaGetErrorString(ce));
-            return TMND_ERR_CUDA;
-        }
-    }
-
-    // Replay with a double-buffered convergence check: replay j runs while
-    // the host waits for replay j-1 and reads its done flag.
-    int *flags = nullptr;  // pinned [2]
-    cudaEvent_t fev[2];
-    TMND_CUDA_TRY(cudaHostAlloc((void **)&flags, 2 * sizeof(int), cudaHostAllocDefault));
-    cudaEventCreateWithFlags(&fev[0], cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&fev[1], cudaEventDisableTiming);
-    std::vector<float> hop_t, upd_t;  // per global iteration
-    auto harvest = [&](long j) {       // read the events of replay j (complete)
-        int inst = (int)(j % ninst);
-        for (int k = 0; k < check_every; k++) {
-            float a = 0.f, b2 = 0.f;
-            if (cudaEventElapsedTime(&a, ev(inst, k, 0), ev(inst, k, 1)) != cudaSuccess ||
-                cudaEventElapsedTime(&b2, ev(inst, k, 1), ev(inst, k, 2)) != cudaSuccess) {
-                cudaGetLastError();
-                a = b2 = nanf("");
-            }
-            hop_t.push_back(a);
-            upd_t.push_back(b2);
-        }
+    auto body = [&](int k, auto mark) {
+        const int j = k % WIN;  // position inside the window
+        mark(0);
+        HopEpiArgs e1 = {};
+        e1.part_out = part_norm;
+        e1.done = &st->done;
+        launch_hop_even_f64(g->geom, g->st, g->links, p, te, false, &st->done, s);
+        launch_hop_odd_f64(g->geom, g->st, g->links, p, te, y, false, EPI_STORE_NORMS, e1, s);
+        launch_hop_even_f64(g->geom, g->st, g->links, y, te, true, &st->done, s);
+        HopEpiArgs e2 = {};
+        e2.sigma = c.sigma0;
+        e2.aux = p;
+        e2.r_in = slot[(j + WIN - 1) % WIN];
+        e2.r = slot[j];
+        e2.part_out = part_rr;
+        e2.part_in = part_norm;
+        e2.npart_in = nb_hop;
+        e2.rr = &st->rr;
+        e2.done = &st->done;
+        launch_hop_odd_f64(g->geom, g->st, g->links, y, te, nullptr, true, EPI_MMS_R, e2, s);
+        mark(1);
+        k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c, j);
+        k_pupdate<<<nb_str, UPD_THREADS, 0, s>>>(n, cf, slot[j], p);
+        if (j == WIN - 1) k_window<double2><<<nb_str, UPD_THREADS, 0, s>>>(n, cf, ring, ptrs, nshift);
+        mark(2);
     };
-    const long max_launch = (long)maxiter / check_every + 3;
-    long nlaunch = 0;
-    cudaError_t err = cudaSuccess;
-    for (long j = 0; j < max_launch && err == cudaSuccess; j++) {
-        err = cudaGraphLaunch(exec[j % ninst], s);
-        if (err != cudaSuccess) break;
-        nlaunch++;
-        cudaMemcpyAsync(&flags[j & 1], &st->done, sizeof(int), cudaMemcpyDeviceToHost, s);
-        cudaEventRecord(fev[j & 1], s);
-        if (j > 0) {
-            err = cudaEventSynchronize(fev[(j - 1) & 1]);
-            if (err == cudaSuccess && profile) harvest(j - 1);
-            if (err == cudaSuccess && flags[(j - 1) & 1]) break;
-        }
+    LoopOut lo;
+    tmnd_status ls = run_graph_loop(s, &st->done, maxiter, check_every, profile, body, lo);
+    if (ls != TMND_OK) return ls;
+    const long nlaunch = lo.nlaunch;
+    std::vector<float> &hop_t = lo.hop_t, &upd_t = lo.upd_t;
+    if (info) {
+        info->launches += 2 + nlaunch * ((long long)check_every * 6 + check_every / WIN) + 5LL * nshift;
+        info->fp64_applies += nshift;
     }
-    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-    if (err == cudaSuccess && profile && nlaunch > 0) harvest(nlaunch - 1);
-    cudaEventDestroy(fev[0]);
-    cudaEventDestroy(fev[1]);
-    cudaFreeHost(flags);
-    for (int inst = 0; inst < ninst; inst++) cudaGraphExecDestroy(exec[inst]);
-    for (auto &e : evs) cudaEventDestroy(e);
-    if (err != cudaSuccess) {
-        tmnd_set_error("mms_cg_solve: %s", cudaGetErrorString(err));
-        return TMND_ERR_CUDA;
-    }
-    if (info) info->launches += 2 + nlaunch * ((long long)check_every * 6 + check_every / WIN) + 5LL * nshift;
 
     MMSState hs;
     TMND_CUDA_TRY(cudaMemcpy(&hs, st, sizeof hs, cudaMemcpyDeviceToHost));
@@ -479,6 +602,257 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
     return TMND_OK;
 }
 
+
+// ---------------------------------------------------------- mixed precision
+// Workspace of the mixed solve (one right-hand side at a time).
+struct MixedWork {
+    double2 *r64, *y64, *te64;          // FP64: defect, (Qhat^2+sigma) x, even temporary
+    float2 *ring[WIN];                  // FP32 residual slots of the sloppy MMS-CG
+    float2 *b32;                        // FP32 right-hand side of the sloppy solve
+    float2 *p32[NS], *x32[NS];          // FP32 shifted directions and sloppy solutions
+    void *p16, *y16, *te16;             // 16-bit stencil vectors
+};
+
+static size_t mixed_work_bytes(int Vh, int nshift) {
+    const size_t s64 = spinor_bytes_prec(Vh, TMND_F64), s32 = spinor_bytes_prec(Vh, TMND_F32),
+                 s16 = spinor_bytes_prec(Vh, TMND_S16);
+    return 3 * s64 + (WIN + 1 + 2 * (size_t)nshift) * s32 + 3 * s16;
+}
+
+static MixedWork mixed_work(void *base, int Vh, int nshift) {
+    const size_t s64 = spinor_bytes_prec(Vh, TMND_F64), s32 = spinor_bytes_prec(Vh, TMND_F32),
+                 s16 = spinor_bytes_prec(Vh, TMND_S16);
+    char *w = (char *)base;
+    MixedWork m;
+    m.r64 = (double2 *)w; w += s64;
+    m.y64 = (double2 *)w; w += s64;
+    m.te64 = (double2 *)w; w += s64;
+    for (int l = 0; l < WIN; l++) { m.ring[l] = (float2 *)w; w += s32; }
+    m.b32 = (float2 *)w; w += s32;
+    for (int i = 0; i < nshift; i++) { m.p32[i] = (float2 *)w; w += s32; }
+    for (int i = 0; i < nshift; i++) { m.x32[i] = (float2 *)w; w += s32; }
+    m.p16 = w; w += s16;
+    m.y16 = w; w += s16;
+    m.te16 = w;
+    return m;
+}
+
+// Sloppy multi-shift CG on m.b32 for shifts sigma[0..nshift), solutions into
+// m.x32[0..nshift).  Same recursion and kernel sequence as the FP64 solver,
+// with the stencil in FP32/16-bit (dslash_s16.cu).
+static tmnd_status mms_sloppy(tmnd_gauge *g, MixedWork &m, const double *sigma, int nshift, int nsolve, double rho,
+                              int maxiter, int check_every, int profile, cudaStream_t s, MMSState &hs, LoopOut &lo) {
+    const int Vh = g->geom.Vh;
+    const long n = 24L * Vh;
+    const int nb_hop = hop_blocks_s16(g->geom);
+    const int nb_str = stream_blocks(n);
+    const int nb_site = site_blocks(Vh);
+    double *part_norm = (double *)g->partials;
+    double *part_rr = part_norm + 2 * nb_hop;
+    double *part_str = part_rr + nb_hop;
+    char *tail = (char *)(part_str + (nb_str > nb_site ? nb_str : nb_site));
+    tail = (char *)(((uintptr_t)tail + 255) & ~(uintptr_t)255);
+    MMSState *st = (MMSState *)tail;
+    MMSCoef *cf = (MMSCoef *)(tail + ((sizeof(MMSState) + 255) & ~(size_t)255));
+
+    MMSConst c = {};
+    c.nshift = nshift;
+    c.nsolve = nsolve;
+    c.maxiter = maxiter;
+    c.sigma0 = sigma[nsolve - 1];
+    for (int i = 0; i < nshift; i++) c.delta[i] = sigma[i] - c.sigma0;
+    c.rho2 = rho * rho;
+    ShiftPtrsT<float2> ptrs = {};
+    for (int i = 0; i < nshift; i++) {
+        ptrs.x[i] = m.x32[i];
+        ptrs.p[i] = m.p32[i];
+    }
+    RingPtrsT<float2> ring;
+    for (int l = 0; l < WIN; l++) ring.r[l] = m.ring[l];
+    const S16Out p16 = s16_out(m.p16, Vh), y16 = s16_out(m.y16, Vh), te16 = s16_out(m.te16, Vh);
+    const S16In p16i{p16.q, p16.nrm}, y16i{y16.q, y16.nrm}, te16i{te16.q, te16.nrm};
+
+    k_init_s<<<nb_site, 128, 0, s>>>(Vh, m.b32, m.ring[WIN - 1], p16, ptrs, nshift, part_str);
+    k_init_state<<<1, 256, 0, s>>>(st, part_str, nb_site, c);
+    TMND_CUDA_TRY(cudaGetLastError());
+
+    auto body = [&](int k, auto mark) {
+        const int j = k % WIN;
+        mark(0);
+        S16EpiArgs e1 = {};
+        e1.part_out = part_norm;
+        e1.done = &st->done;
+        launch_hop_even_s16(g->geom, g->stf, g->links_s16, p16i, te16, false, &st->done, s);
+        launch_hop_odd_s16(g->geom, g->stf, g->links_s16, p16i, te16i, y16, false, EPI_STORE_NORMS, e1, s);
+        launch_hop_even_s16(g->geom, g->stf, g->links_s16, y16i, te16, true, &st->done, s);
+        S16EpiArgs e2 = {};
+        e2.sigma = c.sigma0;
+        e2.aux = p16i;
+        e2.r_in = m.ring[(j + WIN - 1) % WIN];
+        e2.r = m.ring[j];
+        e2.part_out = part_rr;
+        e2.part_in = part_norm;
+        e2.npart_in = nb_hop;
+        e2.rr = &st->rr;
+        e2.done = &st->done;
+        launch_hop_odd_s16(g->geom, g->stf, g->links_s16, y16i, te16i, S16Out{}, true, EPI_MMS_R, e2, s);
+        mark(1);
+        k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c, j);
+        k_pupdate_s<<<nb_site, 128, 0, s>>>(Vh, cf, m.ring[j], p16);
+        if (j == WIN - 1) k_window<float2><<<nb_str, UPD_THREADS, 0, s>>>(n, cf, ring, ptrs, nshift);
+        mark(2);
+    };
+    tmnd_status ls = run_graph_loop(s, &st->done, maxiter, check_every, profile, body, lo);
+    if (ls != TMND_OK) return ls;
+    TMND_CUDA_TRY(cudaMemcpy(&hs, st, sizeof hs, cudaMemcpyDeviceToHost));
+    if (hs.status == TMND_ERR_NAN) {
+        tmnd_set_error("mms_cg_solve: NaN/Inf in a sloppy reduction at iteration %d", hs.iter);
+        return TMND_ERR_NAN;
+    }
+    return TMND_OK;
+}
+
+// (Qhat^2 + sigma) x - b in FP64 into m.r64 (as b - (...)), returns |r|^2 on the host.
+static tmnd_status fp64_defect(tmnd_gauge *g, MixedWork &m, const double2 *b, const double2 *x, double sigma,
+                               cudaStream_t s, double *rr) {
+    const long n = 24L * g->geom.Vh;
+    const int nb = stream_blocks(n);
+    double *part = (double *)g->partials;
+    HopEpiArgs ea = {};
+    launch_hop_even_f64(g->geom, g->st, g->links, x, m.te64, false, nullptr, s);
+    launch_hop_odd_f64(g->geom, g->st, g->links, x, m.te64, m.r64, false, EPI_STORE, ea, s);
+    HopEpiArgs e2 = {};
+    e2.sigma = sigma;
+    e2.aux = x;
+    launch_hop_even_f64(g->geom, g->st, g->links, m.r64, m.te64, true, nullptr, s);
+    launch_hop_odd_f64(g->geom, g->st, g->links, m.r64, m.te64, m.y64, true, EPI_SHIFT, e2, s);
+    k_resid<<<nb, UPD_THREADS, 0, s>>>(n, b, m.y64, m.r64, part);
+    std::vector<double> h(nb);
+    TMND_CUDA_TRY(cudaMemcpyAsync(h.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    TMND_CUDA_TRY(cudaStreamSynchronize(s));
+    double acc = 0;
+    for (int k = 0; k < nb; k++) acc += h[k];
+    *rr = acc;
+    return TMND_OK;
+}
+
+static tmnd_status mixed_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *x, const double *sigma,
+                                 int nshift, int nsolve, double rho, double rho_inner, int maxiter, int check_every,
+                                 int profile, tmnd_solve_info *info, cudaStream_t s, int rhs_index) {
+    const int Vh = g->geom.Vh;
+    const long n = 24L * Vh;
+    MixedWork m = mixed_work(g->work, Vh, nshift);
+    double2 *xk[NS];
+    for (int i = 0; i < nshift; i++) xk[i] = x[i] + (size_t)rhs_index * n;
+    tmnd_status st;
+    // |b|^2 in FP64
+    double bb = 0;
+    {
+        const int nb = stream_blocks(n);
+        double *part = (double *)g->partials;
+        TMND_CUDA_TRY(cudaMemsetAsync(m.y64, 0, sizeof(double2) * n, s));
+        k_diff_norm<<<nb, UPD_THREADS, 0, s>>>(n, b, m.y64, part);
+        std::vector<double> h(nb);
+        TMND_CUDA_TRY(cudaMemcpyAsync(h.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+        TMND_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int k = 0; k < nb; k++) bb += h[k];
+    }
+    if (bb == 0.0) {
+        for (int i = 0; i < nshift; i++) TMND_CUDA_TRY(cudaMemsetAsync(xk[i], 0, sizeof(double2) * n, s));
+        return TMND_OK;
+    }
+    // 1. sloppy multi-shift CG on b
+    st = convert_spinor(Vh, m.b32, TMND_F32, b, TMND_F64, 1, s);
+    if (st != TMND_OK) return st;
+    MMSState hs;
+    LoopOut lo;
+    st = mms_sloppy(g, m, sigma, nshift, nsolve, rho_inner, maxiter, check_every, profile, s, hs, lo);
+    if (st != TMND_OK) return st;
+    for (int i = 0; i < nshift; i++) {
+        st = convert_spinor(Vh, xk[i], TMND_F64, m.x32[i], TMND_F32, 1, s);
+        if (st != TMND_OK) return st;
+    }
+    int fp64 = 0, rounds = 0, riters = 0;
+    long long launches = 2 + lo.nlaunch * ((long long)check_every * 6 + check_every / WIN) + 2 + nshift;
+    double hop_ms = 0, upd_ms = 0;
+    auto add_prof = [&](const LoopOut &l, int iters) {
+        for (int k = 0; k < iters && k < (int)l.hop_t.size(); k++) {
+            hop_ms += l.hop_t[k];
+            upd_ms += l.upd_t[k];
+        }
+    };
+    add_prof(lo, hs.iter);
+    if (info) {
+        if (rhs_index == 0 || hs.iter > info->iters) info->iters = hs.iter;
+        for (int i = 0; i < nshift; i++) {
+            info->conv_iter[i] = hs.conv_iter[i];
+            info->zeta[i] = hs.zeta[i];
+        }
+    }
+    // 2. FP64 defect correction, shift by shift, for the shifts that must converge
+    std::vector<double> res(nshift, 0.0);
+    std::vector<int> todo;
+    for (int i = 0; i < nsolve; i++) todo.push_back(i);
+    const int max_rounds = 8;
+    for (int round = 0; !todo.empty(); round++) {
+        std::vector<int> next;
+        for (int i : todo) {
+            double rr = 0;
+            st = fp64_defect(g, m, b, xk[i], sigma[i], s, &rr);
+            if (st != TMND_OK) return st;
+            fp64++;
+            launches += 5;
+            res[i] = sqrt(rr / bb);
+            if (!isfinite(res[i])) {
+                tmnd_set_error("mms_cg_solve: NaN/Inf in the FP64 defect of shift %d", i);
+                return TMND_ERR_NAN;
+            }
+            if (res[i] <= rho) continue;
+            if (round >= max_rounds) {
+                next.push_back(i);
+                continue;
+            }
+            // sloppy CG on the defect: (Qhat^2 + sigma_i) e = r, to the tolerance the target needs
+            st = convert_spinor(Vh, m.b32, TMND_F32, m.r64, TMND_F64, 1, s);
+            if (st != TMND_OK) return st;
+            const double need = 0.3 * rho / res[i];
+            const double tol = need > rho_inner ? need : rho_inner;
+            MMSState hc;
+            LoopOut lc;
+            st = mms_sloppy(g, m, &sigma[i], 1, 1, tol, maxiter, check_every, profile, s, hc, lc);
+            if (st != TMND_OK) return st;
+            add_prof(lc, hc.iter);
+            riters += hc.iter;
+            launches += 2 + lc.nlaunch * ((long long)check_every * 6 + check_every / WIN) + 1;
+            k_add_f32_to_f64<<<stream_blocks(n), UPD_THREADS, 0, s>>>(n, m.x32[0], xk[i]);
+            TMND_CUDA_TRY(cudaGetLastError());
+            next.push_back(i);
+        }
+        if (round >= max_rounds) {
+            todo = next;
+            break;
+        }
+        todo = next;
+        if (!todo.empty()) rounds = round + 1;
+    }
+    if (info) {
+        for (int i = 0; i < nshift; i++)
+            if (rhs_index == 0 || res[i] > info->true_res[i]) info->true_res[i] = res[i];
+        info->fp64_applies += fp64;
+        info->refine_iters += riters;
+        if (rounds > info->refine_rounds) info->refine_rounds = rounds;
+        info->launches += launches;
+        info->hop_ms += hop_ms;
+        info->update_ms += upd_ms;
+    }
+    if (!todo.empty()) {
+        tmnd_set_error("mms_cg_solve: shift %d not converged after %d defect-correction rounds (residual %g)",
+                       todo[0], max_rounds, res[todo[0]]);
+        return TMND_ERR_NOCONV;
+    }
+    return TMND_OK;
+}
+
 extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, const double *sigma, int nshift,
                                     void *const *x, const tmnd_solve_params *params, tmnd_solve_info *info,
                                     void *stream) {
@@ -501,12 +875,18 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     TMND_ARG_CHECK(check_every <= 4096, "mms_cg_solve: check_every too large");
     check_every = (check_every + WIN - 1) / WIN * WIN;  // whole windows per graph replay
 
+    const int mixed = params->prec == TMND_S16;
+    TMND_ARG_CHECK(params->prec == TMND_F64 || mixed, "mms_cg_solve: prec %d not supported", params->prec);
+    const double rho_inner = params->rho_inner > 0 ? params->rho_inner : 1e-5;
+    TMND_ARG_CHECK(rho_inner < 1, "mms_cg_solve: rho_inner = %g not in (0, 1)", rho_inner);
     const size_t sp = tmnd_spinor_bytes(g);
-    tmnd_status st = tmnd_ensure_workspace(g, (WIN + 3 + (size_t)nshift) * sp);
+    tmnd_status st = tmnd_ensure_workspace(
+        g, mixed ? mixed_work_bytes(g->geom.Vh, nshift) : (WIN + 3 + (size_t)nshift) * sp);
     if (st != TMND_OK) return st;
     const long n = (long)(sp / sizeof(double2));
-    size_t pbytes = sizeof(double) * (3 * (size_t)hop_blocks(g->geom) + stream_blocks(n)) + 256 + 2 * 4096 +
-                    sizeof(MMSState) + sizeof(MMSCoef);
+    const int nbh = hop_blocks(g->geom) > hop_blocks_s16(g->geom) ? hop_blocks(g->geom) : hop_blocks_s16(g->geom);
+    const int nbs = stream_blocks(n) > site_blocks(g->geom.Vh) ? stream_blocks(n) : site_blocks(g->geom.Vh);
+    size_t pbytes = sizeof(double) * (3 * (size_t)nbh + nbs) + 256 + 2 * 4096 + sizeof(MMSState) + sizeof(MMSCoef);
     st = tmnd_ensure_partials(g, pbytes);
     if (st != TMND_OK) return st;
     if (info) memset(info, 0, sizeof *info);
@@ -521,9 +901,12 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     TMND_CUDA_TRY(cudaStreamWaitEvent(s, e0, 0));
     tmnd_status res = TMND_OK;
     for (int k = 0; k < nrhs && res == TMND_OK; k++) {
-        tmnd_status rk = mms_one_rhs(g, (const double2 *)b + (size_t)k * (sp / sizeof(double2)),
-                                     (double2 *const *)x, sigma, nshift, nsolve, params->rho, params->maxiter,
-                                     check_every, params->profile ? 1 : 0, info, s, k);
+        const double2 *bk = (const double2 *)b + (size_t)k * (sp / sizeof(double2));
+        tmnd_status rk =
+            mixed ? mixed_one_rhs(g, bk, (double2 *const *)x, sigma, nshift, nsolve, params->rho, rho_inner,
+                                  params->maxiter, check_every, params->profile ? 1 : 0, info, s, k)
+                  : mms_one_rhs(g, bk, (double2 *const *)x, sigma, nshift, nsolve, params->rho, params->maxiter,
+                                check_every, params->profile ? 1 : 0, info, s, k);
         if (rk != TMND_OK) res = rk;
     }
     cudaEventRecord(e0, s);

@@ -208,3 +208,40 @@ void launch_pack_links_s16(const Geom &g, const double2 *canon, int2 *out, cudaS
 size_t spinor_bytes_prec(int Vh, int prec);
 tmnd_status convert_spinor(int Vh, void *dst, int dst_prec, const void *src, int src_prec, int nrhs,
                            cudaStream_t s);
+
+// Site-level 16-bit (de)quantisation shared by the sloppy solver kernels.
+// v[c][0/1] = real/imaginary part of component c = flavour*12 + spin*3 + colour.
+__device__ __forceinline__ float s16_i2f(int n) { return __int_as_float(n + 0x4B400000) - 12582912.0f; }
+
+__device__ __forceinline__ void s16_load_site(S16In in, int Vh, int h, float v[24][2]) {
+    const float sc = in.nrm[h];
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        const int4 w = in.q[(size_t)j * Vh + h];
+        const int ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            v[4 * j + k][0] = s16_i2f((ws[k] << 16) >> 16) * sc;
+            v[4 * j + k][1] = s16_i2f(ws[k] >> 16) * sc;
+        }
+    }
+}
+
+__device__ __forceinline__ void s16_store_site(S16Out out, int Vh, int h, const float v[24][2]) {
+    float m = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 24; c++) m = fmaxf(m, fmaxf(fabsf(v[c][0]), fabsf(v[c][1])));
+    const float sc = m > 0.0f ? 32767.0f / m : 0.0f;
+    out.nrm[h] = m * (1.0f / 32767.0f);
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        int w[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int re = __float_as_int(fmaf(v[4 * j + k][0], sc, 12582912.0f));
+            const int im = __float_as_int(fmaf(v[4 * j + k][1], sc, 12582912.0f));
+            w[k] = __byte_perm(re, im, 0x5410);
+        }
+        out.q[(size_t)j * Vh + h] = make_int4(w[0], w[1], w[2], w[3]);
+    }
+}

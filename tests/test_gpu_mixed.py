@@ -1,0 +1,71 @@
+"""Mixed-precision multi-shift solve (sloppy FP32/16-bit MMS-CG + FP64 defect
+correction) against the FP64 oracle.  The certification is the oracle's own
+true residual |b - (Qhat^2 + sigma_i) x_i| / |b| <= 1e-10 for every required
+shift (the library stops each shift on its FP64 true residual, so no drift
+allowance is needed beyond FP64 summation-order effects: factor 1.01)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import EPS, KAPPA, MU, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed(tm, g, b, sig, nrhs=1, nsolve=0, rho=1e-10, rho_inner=0.0):
+    bi = g.pack(torch.from_numpy(b).cuda(), nrhs=nrhs)
+    xs = [g.spinor(nrhs) for _ in sig]
+    info = tm.mms_cg_solve(g.handle, bi, nrhs, sig, xs, rho=rho, nsolve=nsolve, prec=tm.TMND_S16,
+                           rho_inner=rho_inner)
+    return info, [g.unpack(x, nrhs).cpu().numpy() for x in xs]
+
+
+def test_mixed_config1_certified():
+    tm = require_gpu()
+    dims = (4, 4, 4, 4)
+    U = synth.random_su3_field(dims, 0.3, 1001)
+    b = synth.gaussian_rhs(dims, 2001)[0]
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    sig = synth.shift_set(10, 1e-4, 1.0)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    info, xs = _mixed(tm, g, b, sig)
+    for i, s in enumerate(sig):
+        tr = oracle.true_residual(act, U, b, xs[i][0], s)
+        assert tr <= 1.01e-10, (i, tr, info)
+        assert abs(info["true_res"][i] - tr) <= 1e-3 * tr + 1e-16
+    assert info["fp64_applies"] >= len(sig)
+    g.close()
+
+
+def test_mixed_multi_rhs_ragged_and_guess_shifts():
+    tm = require_gpu()
+    dims = (8, 6, 6, 6)
+    U = synth.random_su3_field(dims, 0.5, 77)
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    b = synth.gaussian_rhs(dims, 99, nrhs=2)
+    sig = synth.shift_set(8, 1e-3, 2.0)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    info, xs = _mixed(tm, g, b, sig, nrhs=2, nsolve=6)
+    for k in range(2):
+        for i in range(6):
+            assert oracle.true_residual(act, U, b[k], xs[i][k], sig[i]) <= 1.01e-10
+        for i in (6, 7):  # guess shifts: sloppy iterates, better than the zero vector
+            assert oracle.true_residual(act, U, b[k], xs[i][k], sig[i]) < 1.0
+    g.close()
+
+
+def test_mixed_bench_lattice_certified():
+    """16^3x32, roughness 0.5, 12 shifts in 1e-5..2: every shift certified."""
+    tm = require_gpu()
+    dims = (32, 16, 16, 16)
+    U = synth.random_su3_field(dims, 0.5, 1002)
+    b = synth.gaussian_rhs(dims, 2032)[0]
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    sig = synth.shift_set(12, 1e-5, 2.0)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    info, xs = _mixed(tm, g, b, sig)
+    for i, s in enumerate(sig):
+        tr = oracle.true_residual(act, U, b, xs[i][0], s)
+        assert tr <= 1.01e-10, (i, tr, info)
+    g.close()
