@@ -197,3 +197,93 @@ def lagrange_guess(nodes, xs, target) -> np.ndarray:
     for wi, xi in zip(w, xs):
         out = out + wi * np.asarray(xi, np.complex128)
     return out
+
+
+# ---------------------------------------------------------------- multigrid
+# Aggregation-based two-level construction of Sec. 3 (DD-alphaAMG): blocks of
+# the fine lattice, a prolongator P built from test vectors that is
+# Gamma_5-compatible (each block's vectors split by chirality, Sec. 3:
+# Gamma_5 P = P Gamma_5,c) and orthonormal (P^+ P = 1), the coarse operator
+# D_c = P^+ D P (Sec. 3), its doublet form (Sec. 3.2, Eq. "non-degenerate_coarse")
+# and the error propagation of the two-level method (Eq. "error_propagation").
+#
+# Layouts (single flavour, full lattice): fine vectors complex [V][4 spin][3 colour]
+# in lexicographic site order; coarse vectors complex [nblock][2 chirality][Nv],
+# blocks in lexicographic order of their block coordinates (t slowest).
+# Chirality 0 = spins 0, 1 (gamma_5 = +1), chirality 1 = spins 2, 3.
+
+def mg_block_of_site(dims, bdims) -> np.ndarray:
+    """Block index of every lexicographic site (blocks of size bdims)."""
+    T, X, Y, Z = dims
+    bt, bx, by, bz = bdims
+    nb = (T // bt, X // bx, Y // by, Z // bz)
+    t, x, y, z = np.meshgrid(np.arange(T), np.arange(X), np.arange(Y), np.arange(Z), indexing="ij")
+    b = (((t // bt) * nb[1] + x // bx) * nb[2] + y // by) * nb[3] + z // bz
+    return b.ravel()
+
+
+def mg_prolongator(dims, bdims, vecs) -> np.ndarray:
+    """Dense P [V*12, nblock*2*Nv]: for each block and chirality, the test
+    vectors restricted there and orthonormalised by modified Gram-Schmidt in
+    the order given (Sec. 3: aggregation over O(20) test vectors, Gamma_5
+    compatible).  vecs: complex [Nv][V][4][3]."""
+    vecs = np.asarray(vecs, np.complex128)
+    nv = vecs.shape[0]
+    V = int(np.prod(dims))
+    blk = mg_block_of_site(dims, bdims)
+    nblock = int(blk.max()) + 1
+    P = np.zeros((V * 12, nblock * 2 * nv), np.complex128)
+    for b in range(nblock):
+        sites = np.nonzero(blk == b)[0]
+        for chi in range(2):
+            rows = (sites[:, None] * 12 + (chi * 6 + np.arange(6))[None, :]).ravel()
+            cols = []
+            for k in range(nv):
+                v = vecs[k].reshape(V * 12)[rows].copy()
+                for u in cols:
+                    v = v - np.vdot(u, v) * u
+                v = v / np.linalg.norm(v)
+                cols.append(v)
+            for k, v in enumerate(cols):
+                P[rows, b * 2 * nv + chi * nv + k] = v
+    return P
+
+
+def wilson_apply(act: Action, links, psi_single) -> np.ndarray:
+    """Single-flavour D_W (hopping form, Eq. "Wilson" with c_sw = 0) through
+    the doublet oracle with mu_bar = eps_bar = 0 and the second flavour zero."""
+    a0 = action(act.dims, act.kappa, 0.0, 0.0, apbc=act.apbc, paper_norm=act.paper_norm)
+    V = int(np.prod(act.dims))
+    psi = np.zeros((V, 2, 4, 3), np.complex128)
+    psi[:, 0] = np.asarray(psi_single).reshape(V, 4, 3)
+    return dnd(a0, links, psi)[:, 0]
+
+
+def mg_coarse_wilson(act: Action, links, P) -> np.ndarray:
+    """D_W,c = P^+ D_W P (Sec. 3), column by column."""
+    V = int(np.prod(act.dims))
+    DP = np.empty_like(P)
+    for j in range(P.shape[1]):
+        DP[:, j] = wilson_apply(act, links, P[:, j].reshape(V, 4, 3)).ravel()
+    return P.conj().T @ DP
+
+
+def mg_coarse_nd(Dcw, nblock, nv, mu_c, eps_c) -> np.ndarray:
+    """Doublet coarse operator (Sec. 3.2, Eq. "non-degenerate_coarse"):
+    D_ND,c = D_W,c (x) 1_2 + i mu_c (Gamma_5,c (x) tau_3) - eps_c (1 (x) tau_1),
+    in the coarse layout [block][flavour][chirality][Nv].  In the hopping
+    normalisation mu_c = 2 kappa mu_bar, eps_c = 2 kappa eps_bar."""
+    n = nblock * 2 * nv
+    out = np.zeros((2 * n, 2 * n), np.complex128)
+    g5c = np.tile(np.repeat([1.0, -1.0], nv), nblock)
+
+    def idx(f):  # coarse ND index of (block, flavour f, chirality, k)
+        b = np.repeat(np.arange(nblock), 2 * nv)
+        r = np.tile(np.arange(2 * nv), nblock)
+        return b * 4 * nv + f * 2 * nv + r
+    i0, i1 = idx(0), idx(1)
+    out[np.ix_(i0, i0)] = Dcw + np.diag(1j * mu_c * g5c)
+    out[np.ix_(i1, i1)] = Dcw - np.diag(1j * mu_c * g5c)
+    out[i0, i1] = -eps_c
+    out[i1, i0] = -eps_c
+    return out
