@@ -226,6 +226,108 @@ tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, const double *s
 tmnd_status lagrange_guess(const tmnd_gauge *g, const double *nodes, const void *const *xs, int k,
                            double target, void *out, int nrhs, double *lebesgue_out, void *stream);
 
+/* ---------------------------------------------------------------- multigrid
+ * Aggregation-based two-level multigrid (Sec. 3, DD-alphaAMG; Sec. 3.2 for the
+ * doublet), FP32.  Layouts:
+ *   fine MG vector   : full lattice, complex64 [parity][ncomp][V/2] per RHS
+ *                      (ncomp = 12 for one flavour, 24 for the doublet; component
+ *                      = flavour*12 + spin*3 + colour; parity 0 = even first)
+ *   coarse vector    : complex64 [nrhs][nblock][2 flavour][2 chirality][nvec],
+ *                      blocks in lexicographic order of their block coordinates
+ *   prolongator P    : complex64 [nblock][2 chirality][nvec][block site][6], block site
+ *                      s = ((it*bx + ix)*by + iy)*bz + iz, 6 = (spin within chirality)*3 + colour
+ *   coarse operator  : complex64 [nblock][9][2 nvec][2 nvec], direction 0 = self,
+ *                      1 + 2 mu + (0: neighbour block in +mu, 1: in -mu) */
+typedef struct tmnd_mg tmnd_mg;
+
+typedef struct {
+    int block[4];              /* aggregate size {bt, bx, by, bz}; each divides dims */
+    int nvec;                  /* test vectors per chirality, 1..32 (N_v of Sec. 3) */
+    double coarse_mu_factor;   /* d of Sec. 3: coarse twisted mass d*mu_bar (<= 0: 1) */
+} tmnd_mg_params;
+
+/* Build the hierarchy from `nvec` caller-provided test vectors (device, FP32
+ * single-flavour fine MG vectors, one after another): orthonormalise them per
+ * aggregate and chirality by Gram-Schmidt into a Gamma_5-compatible P (Sec. 3),
+ * and assemble D_W,c = P^+ D_W P (Sec. 3) and G_odd = P^+ gamma_5 Pi_odd P (the
+ * odd-site shift of the case-C systems).  Synchronous. */
+tmnd_status tmnd_mg_create(tmnd_gauge *g, const tmnd_mg_params *p, const void *test_vectors, tmnd_mg **out);
+void tmnd_mg_destroy(tmnd_mg *mg);
+
+/* Bytes of one coarse doublet vector (one RHS). */
+size_t tmnd_mg_coarse_bytes(const tmnd_mg *mg);
+
+/* out_c = P_ND^+ in (restriction of nrhs fine doublet MG vectors), P_ND = P (x) 1_2 (Sec. 3.2). */
+tmnd_status tmnd_mg_restrict(const tmnd_mg *mg, void *out_c, const void *in_fine, int nrhs, void *stream);
+
+/* out = P_ND in_c (prolongation of nrhs coarse vectors). */
+tmnd_status tmnd_mg_prolong(const tmnd_mg *mg, void *out_fine, const void *in_c, int nrhs, void *stream);
+
+/* out_c = D'_c in_c for nrhs coarse doublet vectors, with the coarse doublet operator
+ * (Sec. 3.2, Eq. "non-degenerate_coarse", hopping normalisation)
+ *   D'_c = D_W,c (x) 1 + i 2 kappa d mu_bar (Gamma_5,c (x) tau_3) - 2 kappa eps_bar (1 (x) tau_1)
+ *          + i odd_shift_s (tau_1 (x) G_odd)
+ * (the last term is the coarse image of + i s gamma_5 tau_1 on odd sites, the shift
+ * of the case-C systems).  9-point stencil over blocks; nrhs * 4 nvec <= 1024. */
+tmnd_status mg_coarse_apply(const tmnd_mg *mg, void *out_c, const void *in_c, int nrhs, double odd_shift_s,
+                            void *stream);
+
+/* out = D' in on the full lattice (fine doublet MG vectors, FP32), with
+ *   D' = D_ND + i s (gamma_5 (x) tau_1) Pi_odd
+ * (Eq. "non-degenerate" in the hopping normalisation; the odd-site term makes
+ * the odd Schur complement Mhat + i s gamma_5 tau_1, the operator of the case-C
+ * systems (Qhat + i s) y = b, Sec. 3.1 Eq. "lindif"). */
+tmnd_status tmnd_dnd_full_apply(tmnd_gauge *g, void *out, const void *in, double s, void *stream);
+
+/* Solve D' x = b (fine doublet MG vectors, FP32; x holds the initial guess and
+ * receives the solution) by flexible GCR(restart) preconditioned with one
+ * two-level V-cycle per iteration (Sec. 3, Eq. "error_propagation"): `nu`
+ * minimal-residual pre- and post-smoothing steps and a coarse GCR on
+ * mg_coarse_apply.  Stops at |b - D'x| <= tol |b| or after maxiter outer
+ * iterations; iters / res (relative residual, FP32 operator) may be NULL.
+ * Synchronous; allocates its scratch for the call. */
+tmnd_status tmnd_mg_solve(tmnd_mg *mg, void *x, const void *b, double s, double tol, int maxiter, int restart,
+                          int nu, int *iters, double *res, void *stream);
+
+/* Relax nvec single-flavour fine MG vectors (device, in place) towards the
+ * near-null space of D_TM(mu_bar): `iters` steps x <- x - w D x with
+ * w = <Dx, x>/<Dx, Dx> (minimal residual on D x = 0), then normalise.  The
+ * relaxed vectors are the test vectors of tmnd_mg_create (Sec. 3 setup). */
+tmnd_status tmnd_mg_smooth_vectors(tmnd_gauge *g, void *vecs, int nvec, int iters, void *stream);
+
+typedef struct {
+    double rho;            /* target relative residual of every shift (FP64 true residual) */
+    int maxiter;           /* iteration cap of the multi-shift and defect-correction solves */
+    int prec;              /* TMND_F64 or TMND_S16 for the multi-shift part (see tmnd_solve_params) */
+    double rho_inner;      /* sloppy tolerance (0 = 1e-5) */
+    int n_guess;           /* shifts after the n_mms largest iterated along in the multi-shift
+                              CG as guesses (Sec. 4.2.2; the paper uses 2) */
+    int guess;             /* remaining shifts: 1 = Lagrange guess over the nearest <= 8 solved
+                              shifts (Sec. 4.2.1), 0 = zero start */
+    double mg_tol;         /* relative tolerance of each case-C MG solve (0 = 1e-6) */
+    int mg_maxiter, mg_restart, mg_nu;   /* 0 = 200, 8, 4 */
+} tmnd_hybrid_params;
+
+typedef struct {
+    int mms_iters;                         /* base iterations of the multi-shift part */
+    double guess_res[TMND_MAX_SHIFTS];     /* relative residual of each MG shift's initial guess (RHS 0) */
+    int mg_iters[TMND_MAX_SHIFTS];         /* outer MG iterations of the two case-C solves (RHS 0) */
+    double true_res[TMND_MAX_SHIFTS];      /* final FP64 relative residuals (max over RHS) */
+    int fp64_applies;                      /* FP64 operator applications */
+    int refine_iters;                      /* sloppy defect-correction iterations */
+} tmnd_hybrid_info;
+
+/* Hybrid solve of (Qhat^2 + sigma_i) x_i = b (Sec. 4.3): multi-shift CG for
+ * the n_mms largest shifts, case-C multigrid solves from guesses for the rest
+ * (see above), every shift finished by FP64 defect correction to hp->rho.
+ * b, x as in mms_cg_solve (FP64 internal odd spinors).  Synchronous. */
+tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void *b, int nrhs, const double *sigma, int nshift,
+                              int n_mms, void *const *x, const tmnd_hybrid_params *hp, tmnd_hybrid_info *info,
+                              void *stream);
+
+/* Copy P, D_W,c and G_odd to host buffers (any may be NULL); for tests and inspection. */
+tmnd_status tmnd_mg_export(const tmnd_mg *mg, void *P_host, void *Dc_host, void *Godd_host);
+
 /* Message for the last error on this host thread ("" if none). */
 const char *tmnd_last_error(void);
 

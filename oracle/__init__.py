@@ -287,3 +287,19 @@ def mg_coarse_nd(Dcw, nblock, nv, mu_c, eps_c) -> np.ndarray:
     out[i0, i1] = -eps_c
     out[i1, i0] = -eps_c
     return out
+
+
+def dnd_odd_shift(act: Action, links, psi_full, s) -> np.ndarray:
+    """D' psi = D_ND psi + i s (gamma_5 (x) tau_1) psi on odd sites: the
+    full-lattice operator whose odd Schur complement is Mhat + i s gamma_5 tau_1,
+    the case-C system (Qhat + i s) y = b written as (Mhat + i s g5 t1) y = g5 t1 b
+    (Sec. 3.1, Eq. "lindif")."""
+    psi = _c128(psi_full)
+    out = dnd(act, links, psi)
+    T, X, Y, Z = act.dims
+    t, x, y, z = np.meshgrid(np.arange(T), np.arange(X), np.arange(Y), np.arange(Z), indexing="ij")
+    odd = (((t + x + y + z) & 1) == 1).ravel()
+    g5 = np.array([1.0, 1.0, -1.0, -1.0])
+    term = 1j * s * g5[None, None, :, None] * psi[:, ::-1]   # tau_1 swaps the flavours
+    out[odd] += term[odd]
+    return out

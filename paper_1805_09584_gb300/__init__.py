@@ -30,7 +30,9 @@ STATUS = {0: "TMND_OK", 1: "TMND_ERR_ARG", 2: "TMND_ERR_CUDA", 3: "TMND_ERR_OOM"
 EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd_spinor_bytes_prec",
            "tmnd_spinor_convert", "tmnd_spinor_pack",
            "tmnd_spinor_unpack", "tm_nd_apply", "tm_nd_apply_noalloc", "mms_cg_solve", "lagrange_guess",
-           "tmnd_last_error")
+           "tmnd_last_error", "tmnd_mg_create", "tmnd_mg_destroy", "tmnd_mg_coarse_bytes", "tmnd_mg_restrict",
+           "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export", "tmnd_dnd_full_apply", "tmnd_mg_solve",
+           "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve")
 NOALLOC_MAX_VH = 32768
 
 
@@ -43,6 +45,23 @@ class TmndError(RuntimeError):
 class Action(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int * 4), ("kappa", ctypes.c_double), ("mu_bar", ctypes.c_double),
                 ("eps_bar", ctypes.c_double), ("antiperiodic_t", ctypes.c_int)]
+
+
+class MGParams(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int * 4), ("nvec", ctypes.c_int), ("coarse_mu_factor", ctypes.c_double)]
+
+
+class HybridParams(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("maxiter", ctypes.c_int), ("prec", ctypes.c_int),
+                ("rho_inner", ctypes.c_double), ("n_guess", ctypes.c_int), ("guess", ctypes.c_int),
+                ("mg_tol", ctypes.c_double), ("mg_maxiter", ctypes.c_int), ("mg_restart", ctypes.c_int),
+                ("mg_nu", ctypes.c_int)]
+
+
+class HybridInfo(ctypes.Structure):
+    _fields_ = [("mms_iters", ctypes.c_int), ("guess_res", ctypes.c_double * MAX_SHIFTS),
+                ("mg_iters", ctypes.c_int * MAX_SHIFTS), ("true_res", ctypes.c_double * MAX_SHIFTS),
+                ("fp64_applies", ctypes.c_int), ("refine_iters", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
@@ -88,6 +107,21 @@ def lib() -> ctypes.CDLL:
         L.lagrange_guess.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(vp), i, d, vp, i,
                                      ctypes.POINTER(d), vp]
         L.tmnd_last_error.restype = ctypes.c_char_p
+        L.tmnd_mg_create.argtypes = [vp, ctypes.POINTER(MGParams), vp, ctypes.POINTER(vp)]
+        L.tmnd_mg_destroy.argtypes = [vp]
+        L.tmnd_mg_destroy.restype = None
+        L.tmnd_mg_coarse_bytes.argtypes = [vp]
+        L.tmnd_mg_coarse_bytes.restype = ctypes.c_size_t
+        L.tmnd_mg_restrict.argtypes = [vp, vp, vp, i, vp]
+        L.tmnd_mg_prolong.argtypes = [vp, vp, vp, i, vp]
+        L.mg_coarse_apply.argtypes = [vp, vp, vp, i, d, vp]
+        L.tmnd_mg_export.argtypes = [vp, vp, vp, vp]
+        L.tmnd_dnd_full_apply.argtypes = [vp, vp, vp, d, vp]
+        L.tmnd_mg_solve.argtypes = [vp, vp, vp, d, d, i, i, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]
+        for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
+                     "tmnd_dnd_full_apply", "tmnd_mg_solve",
+           "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_gauge_create", "tmnd_spinor_pack", "tmnd_spinor_unpack", "tm_nd_apply",
                      "tm_nd_apply_noalloc", "mms_cg_solve", "lagrange_guess"):
             getattr(L, name).restype = ctypes.c_int
@@ -197,6 +231,80 @@ def lagrange_guess(h, nodes, xs, target: float, out, nrhs: int = 1, stream=None)
     _check(lib().lagrange_guess(h, nd.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), arr, k, float(target),
                                 _ptr(out), int(nrhs), ctypes.byref(leb), _stream(stream)))
     return leb.value
+
+
+def tmnd_mg_create(h, block, nvec: int, test_vectors, coarse_mu_factor: float = 1.0):
+    p = MGParams()
+    for k in range(4):
+        p.block[k] = int(block[k])
+    p.nvec, p.coarse_mu_factor = int(nvec), float(coarse_mu_factor)
+    out = ctypes.c_void_p()
+    _check(lib().tmnd_mg_create(h, ctypes.byref(p), _ptr(test_vectors), ctypes.byref(out)))
+    return out
+
+
+def tmnd_mg_destroy(mg) -> None:
+    lib().tmnd_mg_destroy(mg)
+
+
+def tmnd_mg_coarse_bytes(mg) -> int:
+    return int(lib().tmnd_mg_coarse_bytes(mg))
+
+
+def tmnd_mg_restrict(mg, out_c, in_fine, nrhs: int = 1, stream=None) -> None:
+    _check(lib().tmnd_mg_restrict(mg, _ptr(out_c), _ptr(in_fine), int(nrhs), _stream(stream)))
+
+
+def tmnd_mg_prolong(mg, out_fine, in_c, nrhs: int = 1, stream=None) -> None:
+    _check(lib().tmnd_mg_prolong(mg, _ptr(out_fine), _ptr(in_c), int(nrhs), _stream(stream)))
+
+
+def mg_coarse_apply(mg, out_c, in_c, nrhs: int = 1, odd_shift_s: float = 0.0, stream=None) -> None:
+    _check(lib().mg_coarse_apply(mg, _ptr(out_c), _ptr(in_c), int(nrhs), float(odd_shift_s), _stream(stream)))
+
+
+def tmnd_mg_export(mg, P_host=None, Dc_host=None, Godd_host=None) -> None:
+    _check(lib().tmnd_mg_export(mg, _hp(P_host), _hp(Dc_host), _hp(Godd_host)))
+
+
+def tmnd_dnd_full_apply(h, out, inp, s: float = 0.0, stream=None) -> None:
+    _check(lib().tmnd_dnd_full_apply(h, _ptr(out), _ptr(inp), float(s), _stream(stream)))
+
+
+def tmnd_mg_solve(mg, x, b, s: float = 0.0, tol: float = 1e-6, maxiter: int = 200, restart: int = 8, nu: int = 4,
+                  stream=None) -> dict:
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    _check(lib().tmnd_mg_solve(mg, _ptr(x), _ptr(b), float(s), float(tol), int(maxiter), int(restart), int(nu),
+                               ctypes.byref(it), ctypes.byref(res), _stream(stream)))
+    return {"iters": it.value, "res": res.value}
+
+
+def tmnd_mg_smooth_vectors(h, vecs, nvec: int, iters: int, stream=None) -> None:
+    _check(lib().tmnd_mg_smooth_vectors(h, _ptr(vecs), int(nvec), int(iters), _stream(stream)))
+
+
+def tmnd_hybrid_solve(h, mg, b, nrhs: int, sigma, n_mms: int, x, rho: float = 1e-10, maxiter: int = 100000,
+                      prec: int = TMND_F64, rho_inner: float = 0.0, n_guess: int = 2, guess: int = 1,
+                      mg_tol: float = 0.0, mg_maxiter: int = 0, mg_restart: int = 0, mg_nu: int = 0,
+                      stream=None) -> dict:
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    ns = len(sig)
+    xs = (ctypes.c_void_p * ns)(*[_ptr(v) for v in x])
+    p = HybridParams(float(rho), int(maxiter), int(prec), float(rho_inner), int(n_guess), int(guess), float(mg_tol),
+                     int(mg_maxiter), int(mg_restart), int(mg_nu))
+    info = HybridInfo()
+    st = lib().tmnd_hybrid_solve(h, mg, _ptr(b), int(nrhs), sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns,
+                                 int(n_mms), xs, ctypes.byref(p), ctypes.byref(info), _stream(stream))
+    out = {"status": st, "mms_iters": info.mms_iters, "guess_res": list(info.guess_res[:ns]),
+           "mg_iters": list(info.mg_iters[:ns]), "true_res": list(info.true_res[:ns]),
+           "fp64_applies": info.fp64_applies, "refine_iters": info.refine_iters}
+    _check(st)
+    return out
+
+
+def _hp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
 # ------------------------------------------------------------ conveniences

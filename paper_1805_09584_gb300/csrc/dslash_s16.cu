@@ -15,13 +15,6 @@
 //     rebuilt as conj(row0 x row1) (det U = +1, Sec. 2: U in SU(3)).  The
 //     antiperiodic sign is applied in the kernel, never folded into links.
 //
-// Memory pipeline: each thread walks its sites direction by direction; the
-// neighbour's spinor words, scale and link words for the next NST-1
-// directions are fetched with cp.async into per-thread shared-memory slots
-// while the current direction is computed, so several directions are in
-// flight without holding registers (the first version, with plain loads, was
-// latency bound at ~30 % of HBM).
-//
 // Arithmetic: the spin projection is done on the integers (exact), the sum is
 // converted to float with an exponent-bias trick on the integer pipe (I2F runs
 // at quarter rate on this GPU), and the link is applied to the integer-valued
@@ -44,7 +37,7 @@ struct cf2 {
     float x, y;
 };
 
-// 12 words of one flavour of one site (direct loads, for the site's own vectors)
+// 12 words of one flavour of one site
 __device__ __forceinline__ void load_flavour(const int4 *__restrict__ q, int Vh, int f, int h, int w[12]) {
     const int4 a = __ldg(&q[(f * 3 + 0) * Vh + h]);
     const int4 b = __ldg(&q[(f * 3 + 1) * Vh + h]);
@@ -52,6 +45,31 @@ __device__ __forceinline__ void load_flavour(const int4 *__restrict__ q, int Vh,
     w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
     w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
     w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
+}
+
+// link rows 0, 1 (integer-valued floats, scale 32767) and rebuilt row 2 (same scale)
+__device__ __forceinline__ void load_link(const int2 *__restrict__ L, int Vh, int hl, cf2 u[3][3]) {
+    const int2 a = __ldg(&L[0 * Vh + hl]);
+    const int2 b = __ldg(&L[1 * Vh + hl]);
+    const int2 c = __ldg(&L[2 * Vh + hl]);
+    const int wv[6] = {a.x, a.y, b.x, b.y, c.x, c.y};
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        u[k / 3][k % 3].x = i2f_exact(lo16(wv[k]));
+        u[k / 3][k % 3].y = i2f_exact(hi16(wv[k]));
+    }
+    // row 2 = conj(row0 x row1) / 32767
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        const cf2 a1 = u[0][k1], a2 = u[0][k2], b1 = u[1][k1], b2 = u[1][k2];
+        float re = fmaf(a1.x, b2.x, -a1.y * b2.y);
+        float im = fmaf(a1.x, b2.y, a1.y * b2.x);
+        re = fmaf(-a2.x, b1.x, fmaf(a2.y, b1.y, re));
+        im = fmaf(-a2.x, b1.y, fmaf(-a2.y, b1.x, im));
+        u[2][k].x = re * INV_QMAX;
+        u[2][k].y = -im * INV_QMAX;
+    }
 }
 
 // integer projection chi = up -+ B lo for one flavour, as exact floats.
@@ -95,115 +113,17 @@ __device__ __forceinline__ cf2 Bdag(const cf2 v[2][3], int s, int c) {
     return s == 0 ? cf2{-v[0][c].y, v[0][c].x} : cf2{v[1][c].y, -v[1][c].x};     // i sigma_3
 }
 
-// ------------------------------------------------------------ staging
-constexpr int NST = 3;  // shared-memory slots per thread: NST-1 directions in flight
-
-struct StageSmem {
-    int4 q[NST][6][S16_THREADS];   // neighbour spinor words (planes 0..5)
-    int2 l[NST][3][S16_THREADS];   // link words (rows 0, 1)
-    float n[NST][S16_THREADS];     // neighbour scale
-};
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// link rows 0, 1 from three words and rebuilt row 2 (all at scale 32767)
-__device__ __forceinline__ void link_from_words(int2 a, int2 b, int2 c, cf2 u[3][3]) {
-    const int wv[6] = {a.x, a.y, b.x, b.y, c.x, c.y};
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-        u[k / 3][k % 3].x = i2f_exact(lo16(wv[k]));
-        u[k / 3][k % 3].y = i2f_exact(hi16(wv[k]));
-    }
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-        const cf2 a1 = u[0][k1], a2 = u[0][k2], b1 = u[1][k1], b2 = u[1][k2];
-        float re = fmaf(a1.x, b2.x, -a1.y * b2.y);
-        float im = fmaf(a1.x, b2.y, a1.y * b2.x);
-        re = fmaf(-a2.x, b1.x, fmaf(a2.y, b1.y, re));
-        im = fmaf(-a2.x, b1.y, fmaf(-a2.y, b1.x, im));
-        u[2][k].x = re * INV_QMAX;
-        u[2][k].y = -im * INV_QMAX;
-    }
-}
-
-// Site coordinates of half-index h on parity P.
-struct Coord {
-    int t, x, y, z;
-};
-template <int P>
-__device__ __forceinline__ Coord coord_of(const Geom &g, int h) {
-    Coord c;
-    const int zh = h % g.Zh;
-    int r = h / g.Zh;
-    c.y = r % g.Y;
-    r /= g.Y;
-    c.x = r % g.X;
-    c.t = r / g.X;
-    c.z = 2 * zh + ((P + c.t + c.x + c.y) & 1);
-    return c;
-}
-
-// Queue the loads of direction d (0 t+, 1 t-, 2 x+, 3 x-, 4 y+, 5 y-, 6 z+, 7 z-) of site h into slot st.
-template <int P>
-__device__ __forceinline__ void issue_dir(StageSmem &S, int st, const Geom &g, const Coord &c, int h, int d,
-                                          const int4 *__restrict__ q, const float *__restrict__ nrm,
-                                          const int2 *__restrict__ links) {
-    const int tid = threadIdx.x;
-    const int mu = d >> 1;
-    const bool fwd = (d & 1) == 0;
-    int t = c.t, x = c.x, y = c.y, z = c.z;
-    if (mu == 0) {
-        t = fwd ? ((t + 1 == g.T) ? 0 : t + 1) : ((t == 0) ? g.T - 1 : t - 1);
-    } else if (mu == 1) {
-        x = fwd ? ((x + 1 == g.X) ? 0 : x + 1) : ((x == 0) ? g.X - 1 : x - 1);
-    } else if (mu == 2) {
-        y = fwd ? ((y + 1 == g.Y) ? 0 : y + 1) : ((y == 0) ? g.Y - 1 : y - 1);
-    } else {
-        z = fwd ? ((z + 1 == g.Z) ? 0 : z + 1) : ((z == 0) ? g.Z - 1 : z - 1);
-    }
-    const int Vh = g.Vh;
-    const int hn = ((t * g.X + x) * g.Y + y) * g.Zh + (z >> 1);
-    const int hl = fwd ? h : hn;
-    const int lpar = fwd ? P : 1 - P;
-    const int2 *L = links + ((size_t)(lpar * 4 + mu) * 3) * Vh;
-#pragma unroll
-    for (int j = 0; j < 6; j++) cp_async16(&S.q[st][j][tid], &q[(size_t)j * Vh + hn]);
-#pragma unroll
-    for (int j = 0; j < 3; j++) cp_async8(&S.l[st][j][tid], &L[(size_t)j * Vh + hl]);
-    cp_async4(&S.n[st][tid], &nrm[hn]);
-}
-
-// One direction from slot st, accumulated into acc (zeroed at the start of a site).
-template <int MU, int DIR, bool G5IN>
-__device__ __forceinline__ void dir_compute(const StageSmem &S, int st, float sign, float acc[2][4][3][2]) {
-    const int tid = threadIdx.x;
+template <int MU, int DIR, bool G5IN, bool FIRST>
+__device__ __forceinline__ void hop_dir(const int4 *__restrict__ q, const float *__restrict__ nrm, int Vh, int hn,
+                                        const int2 *__restrict__ L, int hl, float sign, float acc[2][4][3][2]) {
     cf2 u[3][3];
-    link_from_words(S.l[st][0][tid], S.l[st][1][tid], S.l[st][2][tid], u);
-    const float cscale = sign * S.n[st][tid] * INV_QMAX;
+    load_link(L, Vh, hl, u);
+    const float cscale = sign * __ldg(&nrm[hn]) * INV_QMAX;
     constexpr bool plus = (DIR < 0) != G5IN;
 #pragma unroll
     for (int f = 0; f < 2; f++) {
         int w[12];
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            const int4 v = S.q[st][f * 3 + j][tid];
-            w[4 * j + 0] = v.x; w[4 * j + 1] = v.y; w[4 * j + 2] = v.z; w[4 * j + 3] = v.w;
-        }
+        load_flavour(q, Vh, f, hn, w);
         cf2 chi[2][3];
         project<MU, plus>(w, chi);
         cf2 v[2][3];
@@ -212,7 +132,7 @@ __device__ __forceinline__ void dir_compute(const StageSmem &S, int st, float si
 #pragma unroll
             for (int i = 0; i < 3; i++) {
                 float re, im;
-                if (DIR > 0) {
+                if (DIR > 0) {  // U chi
                     re = u[i][0].x * chi[s][0].x;
                     im = u[i][0].x * chi[s][0].y;
                     re = fmaf(-u[i][0].y, chi[s][0].y, re);
@@ -222,7 +142,7 @@ __device__ __forceinline__ void dir_compute(const StageSmem &S, int st, float si
                         re = fmaf(u[i][j].x, chi[s][j].x, fmaf(-u[i][j].y, chi[s][j].y, re));
                         im = fmaf(u[i][j].x, chi[s][j].y, fmaf(u[i][j].y, chi[s][j].x, im));
                     }
-                } else {
+                } else {  // U^+ chi
                     re = u[0][i].x * chi[s][0].x;
                     im = u[0][i].x * chi[s][0].y;
                     re = fmaf(u[0][i].y, chi[s][0].y, re);
@@ -241,81 +161,64 @@ __device__ __forceinline__ void dir_compute(const StageSmem &S, int st, float si
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 const cf2 b = Bdag<MU>(v, s, c);
-                acc[f][s][c][0] = fmaf(cscale, v[s][c].x, acc[f][s][c][0]);
-                acc[f][s][c][1] = fmaf(cscale, v[s][c].y, acc[f][s][c][1]);
-                acc[f][s + 2][c][0] = fmaf(cl, b.x, acc[f][s + 2][c][0]);
-                acc[f][s + 2][c][1] = fmaf(cl, b.y, acc[f][s + 2][c][1]);
+                if (FIRST) {
+                    acc[f][s][c][0] = cscale * v[s][c].x;
+                    acc[f][s][c][1] = cscale * v[s][c].y;
+                    acc[f][s + 2][c][0] = cl * b.x;
+                    acc[f][s + 2][c][1] = cl * b.y;
+                } else {
+                    acc[f][s][c][0] = fmaf(cscale, v[s][c].x, acc[f][s][c][0]);
+                    acc[f][s][c][1] = fmaf(cscale, v[s][c].y, acc[f][s][c][1]);
+                    acc[f][s + 2][c][0] = fmaf(cl, b.x, acc[f][s + 2][c][0]);
+                    acc[f][s + 2][c][1] = fmaf(cl, b.y, acc[f][s + 2][c][1]);
+                }
             }
     }
 }
 
-// sign: the antiperiodic factor of a time hop that crosses the boundary
-template <bool G5IN>
-__device__ __forceinline__ void dir_dispatch(const StageSmem &S, int st, int d, float sign, float acc[2][4][3][2]) {
-    switch (d) {
-        case 0: dir_compute<0, +1, G5IN>(S, st, sign, acc); break;
-        case 1: dir_compute<0, -1, G5IN>(S, st, sign, acc); break;
-        case 2: dir_compute<1, +1, G5IN>(S, st, 1.0f, acc); break;
-        case 3: dir_compute<1, -1, G5IN>(S, st, 1.0f, acc); break;
-        case 4: dir_compute<2, +1, G5IN>(S, st, 1.0f, acc); break;
-        case 5: dir_compute<2, -1, G5IN>(S, st, 1.0f, acc); break;
-        case 6: dir_compute<3, +1, G5IN>(S, st, 1.0f, acc); break;
-        default: dir_compute<3, -1, G5IN>(S, st, 1.0f, acc); break;
+template <int P, bool G5IN>
+__device__ __forceinline__ void hop_all(const Geom &g, const int2 *__restrict__ links, const int4 *__restrict__ q,
+                                        const float *__restrict__ nrm, int h, float acc[2][4][3][2]) {
+    const int Vh = g.Vh;
+    int zh = h % g.Zh;
+    int r = h / g.Zh;
+    int y = r % g.Y;
+    r /= g.Y;
+    int x = r % g.X;
+    int t = r / g.X;
+    int z = 2 * zh + ((P + t + x + y) & 1);
+    const int2 *Lp = links + (size_t)P * 4 * 3 * Vh;
+    const int2 *Lq = links + (size_t)(1 - P) * 4 * 3 * Vh;
+    auto idx = [&](int tt, int xx, int yy, int zz) { return ((tt * g.X + xx) * g.Y + yy) * g.Zh + (zz >> 1); };
+    {
+        int tf = (t + 1 == g.T) ? 0 : t + 1;
+        int tb = (t == 0) ? g.T - 1 : t - 1;
+        float sf = (g.apbc && t + 1 == g.T) ? -1.0f : 1.0f;
+        float sb = (g.apbc && t == 0) ? -1.0f : 1.0f;
+        int hf = idx(tf, x, y, z), hb = idx(tb, x, y, z);
+        hop_dir<0, +1, G5IN, true>(q, nrm, Vh, hf, Lp + 0 * 3 * (size_t)Vh, h, sf, acc);
+        hop_dir<0, -1, G5IN, false>(q, nrm, Vh, hb, Lq + 0 * 3 * (size_t)Vh, hb, sb, acc);
     }
-}
-
-// The pipelined walk over this block's sites: for every site (half-index h on
-// parity P, input field on parity 1-P), accumulate H applied to the input and
-// call finish(h, acc).  All threads of the block run the same number of steps.
-template <int P, bool G5IN, typename Finish>
-__device__ __forceinline__ void staged_hop(StageSmem &S, const Geom &g, const int2 *__restrict__ links,
-                                           const int4 *__restrict__ q, const float *__restrict__ nrm, int base,
-                                           int end, Finish finish) {
-    const int tid = threadIdx.x;
-    const int nk = (end - base + S16_THREADS - 1) / S16_THREADS;
-    const int nsteps = nk * 8;
-    Coord ic = {0, 0, 0, 0};
-    int ih = 0;
-    bool ivalid = false;
-    auto issue = [&](int i) {
-        const int k = i >> 3, d = i & 7;
-        if (d == 0) {
-            ih = base + tid + k * S16_THREADS;
-            ivalid = ih < end;
-            if (ivalid) ic = coord_of<P>(g, ih);
-        }
-        if (ivalid) issue_dir<P>(S, i % NST, g, ic, ih, d, q, nrm, links);
-        cp_commit();
-    };
-#pragma unroll
-    for (int i = 0; i < NST - 1; i++) {
-        if (i < nsteps) issue(i);
-        else cp_commit();
+    {
+        int xf = (x + 1 == g.X) ? 0 : x + 1;
+        int xb = (x == 0) ? g.X - 1 : x - 1;
+        int hf = idx(t, xf, y, z), hb = idx(t, xb, y, z);
+        hop_dir<1, +1, G5IN, false>(q, nrm, Vh, hf, Lp + 1 * 3 * (size_t)Vh, h, 1.0f, acc);
+        hop_dir<1, -1, G5IN, false>(q, nrm, Vh, hb, Lq + 1 * 3 * (size_t)Vh, hb, 1.0f, acc);
     }
-    float acc[2][4][3][2];
-    for (int i = 0; i < nsteps; i++) {
-        if (i + NST - 1 < nsteps) issue(i + NST - 1);
-        else cp_commit();
-        cp_wait<NST - 1>();
-        const int k = i >> 3, d = i & 7;
-        const int h = base + tid + k * S16_THREADS;
-        if (d == 0) {
-#pragma unroll
-            for (int f = 0; f < 2; f++)
-#pragma unroll
-                for (int s = 0; s < 4; s++)
-#pragma unroll
-                    for (int c = 0; c < 3; c++) acc[f][s][c][0] = acc[f][s][c][1] = 0.0f;
-        }
-        if (h < end) {
-            float sign = 1.0f;
-            if (d < 2 && g.apbc) {
-                const int t = h / (g.X * g.Y * g.Zh);
-                if ((d == 0 && t + 1 == g.T) || (d == 1 && t == 0)) sign = -1.0f;
-            }
-            dir_dispatch<G5IN>(S, i % NST, d, sign, acc);
-            if (d == 7) finish(h, acc);
-        }
+    {
+        int yf = (y + 1 == g.Y) ? 0 : y + 1;
+        int yb = (y == 0) ? g.Y - 1 : y - 1;
+        int hf = idx(t, x, yf, z), hb = idx(t, x, yb, z);
+        hop_dir<2, +1, G5IN, false>(q, nrm, Vh, hf, Lp + 2 * 3 * (size_t)Vh, h, 1.0f, acc);
+        hop_dir<2, -1, G5IN, false>(q, nrm, Vh, hb, Lq + 2 * 3 * (size_t)Vh, hb, 1.0f, acc);
+    }
+    {
+        int zf = (z + 1 == g.Z) ? 0 : z + 1;
+        int zb = (z == 0) ? g.Z - 1 : z - 1;
+        int hf = idx(t, x, y, zf), hb = idx(t, x, y, zb);
+        hop_dir<3, +1, G5IN, false>(q, nrm, Vh, hf, Lp + 3 * 3 * (size_t)Vh, h, 1.0f, acc);
+        hop_dir<3, -1, G5IN, false>(q, nrm, Vh, hb, Lq + 3 * 3 * (size_t)Vh, hb, 1.0f, acc);
     }
 }
 
@@ -367,13 +270,13 @@ template <bool DAG>
 __global__ void __launch_bounds__(S16_THREADS) k_hop_even_s16(Geom g, SiteTermF st, const int2 *__restrict__ links,
                                                              S16In in, S16Out out, const int *__restrict__ done,
                                                              int chunk) {
-    __shared__ StageSmem S;
     if (done && *done) return;
-    const int base = blockIdx.x * chunk;
-    const int end = min(g.Vh, base + chunk);
-    const float a = st.kappa2 * st.inv_det;
-    const float e = a * st.kpp;
-    auto finish = [&](int h, float (&acc)[2][4][3][2]) {
+    const int h_end = min(g.Vh, (int)(blockIdx.x + 1) * chunk);
+    for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) {
+        float acc[2][4][3][2];
+        hop_all<0, DAG>(g, links, in.q, in.nrm, h, acc);
+        const float a = st.kappa2 * st.inv_det;
+        const float e = a * st.kpp;
         float o[2][4][3][2];
 #pragma unroll
         for (int s = 0; s < 4; s++) {
@@ -389,15 +292,13 @@ __global__ void __launch_bounds__(S16_THREADS) k_hop_even_s16(Geom g, SiteTermF 
             }
         }
         store_site(out.q, out.nrm, g.Vh, h, o);
-    };
-    staged_hop<0, DAG>(S, g, links, in.q, in.nrm, base, end, finish);
+    }
 }
 
 template <bool DAG, int EPI>
 __global__ void __launch_bounds__(S16_THREADS) k_hop_odd_s16(Geom g, SiteTermF st, const int2 *__restrict__ links,
                                                             S16In psi, S16In te, S16Out out, S16EpiArgs ea,
                                                             int chunk) {
-    __shared__ StageSmem S;
     __shared__ double red[40];
     if (ea.done && *ea.done) return;
     const int Vh = g.Vh;
@@ -408,12 +309,13 @@ __global__ void __launch_bounds__(S16_THREADS) k_hop_odd_s16(Geom g, SiteTermF s
         alpha = (float)(*ea.rr / (yy + ea.sigma * pp));
     }
     double n1 = 0.0, n2 = 0.0;
-    const int base = blockIdx.x * chunk;
-    const int end = min(Vh, base + chunk);
-    const float kp = DAG ? -st.kp : st.kp;
-    auto finish = [&](int h, float (&acc)[2][4][3][2]) {
+    const int h_end = min(Vh, (int)(blockIdx.x + 1) * chunk);
+    for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) {
+        float acc[2][4][3][2];
+        hop_all<1, false>(g, links, te.q, te.nrm, h, acc);
         float p[2][4][3][2];
         load_site(psi.q, psi.nrm, Vh, h, p);
+        const float kp = DAG ? -st.kp : st.kp;
         float y[2][4][3][2];
         float s1 = 0.0f, s2 = 0.0f;
 #pragma unroll
@@ -445,21 +347,21 @@ __global__ void __launch_bounds__(S16_THREADS) k_hop_odd_s16(Geom g, SiteTermF s
             n1 += s1;
             n2 += s2;
         } else if (EPI == EPI_SHIFT) {
-            float av[2][4][3][2];
-            load_site(ea.aux.q, ea.aux.nrm, Vh, h, av);
+            float a[2][4][3][2];
+            load_site(ea.aux.q, ea.aux.nrm, Vh, h, a);
 #pragma unroll
             for (int f = 0; f < 2; f++)
 #pragma unroll
                 for (int s = 0; s < 4; s++)
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
-                        y[f][s][c][0] = fmaf((float)ea.sigma, av[f][s][c][0], y[f][s][c][0]);
-                        y[f][s][c][1] = fmaf((float)ea.sigma, av[f][s][c][1], y[f][s][c][1]);
+                        y[f][s][c][0] = fmaf((float)ea.sigma, a[f][s][c][0], y[f][s][c][0]);
+                        y[f][s][c][1] = fmaf((float)ea.sigma, a[f][s][c][1], y[f][s][c][1]);
                     }
             store_site(out.q, out.nrm, Vh, h, y);
-        } else {  // EPI_MMS_R
-            float av[2][4][3][2];
-            load_site(ea.aux.q, ea.aux.nrm, Vh, h, av);
+        } else {  // EPI_MMS_R: w = y + sigma aux; r' = r - alpha w (FP32 planes)
+            float a[2][4][3][2];
+            load_site(ea.aux.q, ea.aux.nrm, Vh, h, a);
             const float sg = (float)ea.sigma;
 #pragma unroll
             for (int f = 0; f < 2; f++)
@@ -469,16 +371,15 @@ __global__ void __launch_bounds__(S16_THREADS) k_hop_odd_s16(Geom g, SiteTermF s
                     for (int c = 0; c < 3; c++) {
                         const int i = (f * 12 + s * 3 + c) * Vh + h;
                         const float2 rv = ea.r_in[i];
-                        const float wx = fmaf(sg, av[f][s][c][0], y[f][s][c][0]);
-                        const float wy = fmaf(sg, av[f][s][c][1], y[f][s][c][1]);
+                        const float wx = fmaf(sg, a[f][s][c][0], y[f][s][c][0]);
+                        const float wy = fmaf(sg, a[f][s][c][1], y[f][s][c][1]);
                         const float2 rn = make_float2(fmaf(-alpha, wx, rv.x), fmaf(-alpha, wy, rv.y));
                         ea.r[i] = rn;
                         s1 = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, s1));
                     }
             n1 += s1;
         }
-    };
-    staged_hop<1, false>(S, g, links, te.q, te.nrm, base, end, finish);
+    }
     if (EPI == EPI_STORE_NORMS) {
         double t1 = block_sum(n1, red);
         double t2 = block_sum(n2, red);

@@ -350,6 +350,33 @@ __global__ void k_resid(long n, const double2 *__restrict__ b, const double2 *__
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+
+// ------------------------------------------------------------- hybrid helpers
+// out = in * (ar + i ai) + out (FP64 complex axpy)
+__global__ void k_zaxpy64(long n, double ar, double ai, const double2 *__restrict__ in, double2 *__restrict__ out) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double2 v = in[i];
+        double2 o = out[i];
+        o.x += ar * v.x - ai * v.y;
+        o.y += ar * v.y + ai * v.x;
+        out[i] = o;
+    }
+}
+// FP64 -> FP32 with a real scale
+__global__ void k_to_f32_scaled(long n, double a, const double2 *__restrict__ in, float2 *__restrict__ out) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        out[i] = make_float2((float)(a * in[i].x), (float)(a * in[i].y));
+}
+// x = i/(2s) (yp - ym), yp/ym FP32 odd parts, x FP64   (Sec. 3.1, Eq. "lindif")
+__global__ void k_casec_combine(long n, double s, const float2 *__restrict__ yp, const float2 *__restrict__ ym,
+                                double2 *__restrict__ x) {
+    const double c = 1.0 / (2.0 * s);
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double dr = (double)yp[i].x - ym[i].x, di = (double)yp[i].y - ym[i].y;
+        x[i] = make_double2(-c * di, c * dr);
+    }
+}
+
 int site_blocks(int Vh) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -736,6 +763,75 @@ static tmnd_status fp64_defect(tmnd_gauge *g, MixedWork &m, const double2 *b, co
     return TMND_OK;
 }
 
+struct RefineStats {
+    int fp64 = 0, rounds = 0, iters = 0;
+    long long launches = 0;
+    double hop_ms = 0, upd_ms = 0;
+};
+
+// FP64 defect correction of the shifts in `todo` (Sec. 3.1 stopping rule on
+// the true residual): per round and shift, r = b - (Qhat^2 + sigma_i) x_i in
+// FP64; stop the shift if |r| <= rho |b|, else solve (Qhat^2 + sigma_i) e = r
+// with the sloppy CG to the tolerance the target needs and add e in FP64.
+// res[i] receives the final FP64 relative residuals.
+static tmnd_status defect_correct(tmnd_gauge *g, MixedWork &m, const double2 *b, double2 *const *xk,
+                                  const double *sigma, std::vector<int> todo, double bb, double rho,
+                                  double rho_inner, int maxiter, int check_every, int profile, cudaStream_t s,
+                                  std::vector<double> &res, RefineStats &rs) {
+    const int Vh = g->geom.Vh;
+    const long n = 24L * Vh;
+    const int max_rounds = 8;
+    tmnd_status st;
+    for (int round = 0; !todo.empty(); round++) {
+        std::vector<int> next;
+        for (int i : todo) {
+            double rr = 0;
+            st = fp64_defect(g, m, b, xk[i], sigma[i], s, &rr);
+            if (st != TMND_OK) return st;
+            rs.fp64++;
+            rs.launches += 5;
+            res[i] = sqrt(rr / bb);
+            if (!isfinite(res[i])) {
+                tmnd_set_error("solve: NaN/Inf in the FP64 defect of shift %d", i);
+                return TMND_ERR_NAN;
+            }
+            if (res[i] <= rho) continue;
+            if (round >= max_rounds) {
+                next.push_back(i);
+                continue;
+            }
+            st = convert_spinor(Vh, m.b32, TMND_F32, m.r64, TMND_F64, 1, s);
+            if (st != TMND_OK) return st;
+            const double need = 0.3 * rho / res[i];
+            const double tol = need > rho_inner ? need : rho_inner;
+            MMSState hc;
+            LoopOut lc;
+            st = mms_sloppy(g, m, &sigma[i], 1, 1, tol, maxiter, check_every, profile, s, hc, lc);
+            if (st != TMND_OK) return st;
+            for (int k = 0; k < hc.iter && k < (int)lc.hop_t.size(); k++) {
+                rs.hop_ms += lc.hop_t[k];
+                rs.upd_ms += lc.upd_t[k];
+            }
+            rs.iters += hc.iter;
+            rs.launches += 2 + lc.nlaunch * ((long long)check_every * 6 + check_every / WIN) + 1;
+            k_add_f32_to_f64<<<stream_blocks(n), UPD_THREADS, 0, s>>>(n, m.x32[0], xk[i]);
+            TMND_CUDA_TRY(cudaGetLastError());
+            next.push_back(i);
+        }
+        if (round >= max_rounds) {
+            if (!next.empty()) {
+                tmnd_set_error("solve: shift %d not converged after %d defect-correction rounds (residual %g)",
+                               next[0], max_rounds, res[next[0]]);
+                return TMND_ERR_NOCONV;
+            }
+            break;
+        }
+        todo = next;
+        if (!todo.empty()) rs.rounds = round + 1;
+    }
+    return TMND_OK;
+}
+
 static tmnd_status mixed_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *x, const double *sigma,
                                  int nshift, int nsolve, double rho, double rho_inner, int maxiter, int check_every,
                                  int profile, tmnd_solve_info *info, cudaStream_t s, int rhs_index) {
@@ -793,48 +889,16 @@ static tmnd_status mixed_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const
     std::vector<double> res(nshift, 0.0);
     std::vector<int> todo;
     for (int i = 0; i < nsolve; i++) todo.push_back(i);
-    const int max_rounds = 8;
-    for (int round = 0; !todo.empty(); round++) {
-        std::vector<int> next;
-        for (int i : todo) {
-            double rr = 0;
-            st = fp64_defect(g, m, b, xk[i], sigma[i], s, &rr);
-            if (st != TMND_OK) return st;
-            fp64++;
-            launches += 5;
-            res[i] = sqrt(rr / bb);
-            if (!isfinite(res[i])) {
-                tmnd_set_error("mms_cg_solve: NaN/Inf in the FP64 defect of shift %d", i);
-                return TMND_ERR_NAN;
-            }
-            if (res[i] <= rho) continue;
-            if (round >= max_rounds) {
-                next.push_back(i);
-                continue;
-            }
-            // sloppy CG on the defect: (Qhat^2 + sigma_i) e = r, to the tolerance the target needs
-            st = convert_spinor(Vh, m.b32, TMND_F32, m.r64, TMND_F64, 1, s);
-            if (st != TMND_OK) return st;
-            const double need = 0.3 * rho / res[i];
-            const double tol = need > rho_inner ? need : rho_inner;
-            MMSState hc;
-            LoopOut lc;
-            st = mms_sloppy(g, m, &sigma[i], 1, 1, tol, maxiter, check_every, profile, s, hc, lc);
-            if (st != TMND_OK) return st;
-            add_prof(lc, hc.iter);
-            riters += hc.iter;
-            launches += 2 + lc.nlaunch * ((long long)check_every * 6 + check_every / WIN) + 1;
-            k_add_f32_to_f64<<<stream_blocks(n), UPD_THREADS, 0, s>>>(n, m.x32[0], xk[i]);
-            TMND_CUDA_TRY(cudaGetLastError());
-            next.push_back(i);
-        }
-        if (round >= max_rounds) {
-            todo = next;
-            break;
-        }
-        todo = next;
-        if (!todo.empty()) rounds = round + 1;
-    }
+    RefineStats rs;
+    st = defect_correct(g, m, b, xk, sigma, todo, bb, rho, rho_inner, maxiter, check_every, profile, s, res, rs);
+    if (st != TMND_OK && st != TMND_ERR_NOCONV) return st;
+    const tmnd_status conv = st;
+    fp64 += rs.fp64;
+    riters += rs.iters;
+    rounds = rs.rounds;
+    launches += rs.launches;
+    hop_ms += rs.hop_ms;
+    upd_ms += rs.upd_ms;
     if (info) {
         for (int i = 0; i < nshift; i++)
             if (rhs_index == 0 || res[i] > info->true_res[i]) info->true_res[i] = res[i];
@@ -845,12 +909,7 @@ static tmnd_status mixed_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const
         info->hop_ms += hop_ms;
         info->update_ms += upd_ms;
     }
-    if (!todo.empty()) {
-        tmnd_set_error("mms_cg_solve: shift %d not converged after %d defect-correction rounds (residual %g)",
-                       todo[0], max_rounds, res[todo[0]]);
-        return TMND_ERR_NOCONV;
-    }
-    return TMND_OK;
+    return conv;
 }
 
 extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, const double *sigma, int nshift,
@@ -915,4 +974,150 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     cudaEventDestroy(e0);
     cudaStreamDestroy(s);
     return res;
+}
+
+// ------------------------------------------------------------- hybrid solve
+// Sec. 4.3 (the paper's combined strategy): multi-shift CG for the n_mms largest
+// shifts, iterating the next `n_guess` shifts along as guesses (Sec. 4.2.2);
+// every remaining shift, in descending order, starts from a guess (MMS iterate,
+// else Lagrange interpolation over the nearest <= 8 solved shifts, Sec. 4.2.1)
+// and is solved as case C (Sec. 3.1, Eq. "lindif"):
+//   x = i/(2s) [ (Qhat + i s)^-1 b - (Qhat - i s)^-1 b ],  s = sqrt(sigma),
+// each single system by the two-level MG (full-lattice D_ND +- i s gamma_5 tau_1
+// Pi_odd, right-hand side (0, gamma_5 tau_1 b), initial guess (Qhat -+ i s) x~ with its
+// even part eliminated), then the FP64 defect correction to rho.
+tmnd_status mg_gcr_solve(tmnd_mg *mg, float2 *x, const float2 *b, double s, double tol, int maxiter, int restart,
+                         int nu, cudaStream_t st, int *iters_out, double *res_out, void *scratch);
+size_t mg_gcr_scratch_bytes(tmnd_mg *mg, int restart);
+__global__ void k_g5tau1(int Vh, const double2 *__restrict__ in, double2 *__restrict__ out);
+
+extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void *b, int nrhs, const double *sigma,
+                                         int nshift, int n_mms, void *const *x, const tmnd_hybrid_params *hp,
+                                         tmnd_hybrid_info *hinfo, void *stream) {
+    TMND_ARG_CHECK(g && mg && b && sigma && x && hp, "tmnd_hybrid_solve: NULL argument");
+    TMND_ARG_CHECK(nshift >= 1 && nshift <= TMND_MAX_SHIFTS && n_mms >= 1 && n_mms <= nshift && nrhs >= 1,
+                   "tmnd_hybrid_solve: bad shift counts");
+    for (int i = 0; i < nshift; i++)
+        TMND_ARG_CHECK(sigma[i] > 0 && (i == 0 || sigma[i] < sigma[i - 1]),
+                       "tmnd_hybrid_solve: shifts must be > 0 and strictly descending");
+    cudaGetLastError();
+    const int Vh = g->geom.Vh;
+    const long n = 24L * Vh;
+    const size_t sp = tmnd_spinor_bytes(g);
+    const int ng = hp->n_guess < 0 ? 0 : (n_mms + hp->n_guess > nshift ? nshift - n_mms : hp->n_guess);
+    const int nmms_all = n_mms + ng;
+    // 1. multi-shift CG on the largest shifts (+ guess shifts)
+    tmnd_solve_params sp1 = {};
+    sp1.rho = hp->rho;
+    sp1.maxiter = hp->maxiter;
+    sp1.nsolve = n_mms;
+    sp1.prec = hp->prec;
+    sp1.rho_inner = hp->rho_inner;
+    tmnd_solve_info si = {};
+    tmnd_status st = mms_cg_solve(g, b, nrhs, sigma, nmms_all, x, &sp1, &si, stream);
+    if (st != TMND_OK) return st;
+    if (hinfo) {
+        memset(hinfo, 0, sizeof *hinfo);
+        hinfo->mms_iters = si.iters;
+        hinfo->fp64_applies = si.fp64_applies;
+        hinfo->refine_iters = si.refine_iters;
+        for (int i = 0; i < n_mms; i++) hinfo->true_res[i] = si.true_res[i];
+    }
+    if (n_mms == nshift) return TMND_OK;
+    // 2. the remaining shifts one by one
+    const double rho_inner = hp->rho_inner > 0 ? hp->rho_inner : 1e-5;
+    st = tmnd_ensure_workspace(g, mixed_work_bytes(Vh, 1));
+    if (st != TMND_OK) return st;
+    const long nfull = 2 * n;  // full-lattice FP32 doublet (complex numbers)
+    const size_t f32b = sizeof(float2) * nfull;
+    const size_t scratch_b = 3 * sp + 4 * f32b + mg_gcr_scratch_bytes(mg, hp->mg_restart > 0 ? hp->mg_restart : 8);
+    char *scr = nullptr;
+    TMND_CUDA_TRY(cudaMalloc(&scr, scratch_b));
+    double2 *tq = (double2 *)scr, *te = (double2 *)(scr + sp), *gb = (double2 *)(scr + 2 * sp);
+    float2 *rhs = (float2 *)(scr + 3 * sp), *yp = (float2 *)(scr + 3 * sp + f32b);
+    float2 *ym = (float2 *)(scr + 3 * sp + 2 * f32b);
+    void *gcr = scr + 3 * sp + 4 * f32b;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nbs = stream_blocks(n);
+    MixedWork m = mixed_work(g->work, Vh, 1);
+    tmnd_status res_status = TMND_OK;
+    for (int k = 0; k < nrhs && res_status == TMND_OK; k++) {
+        const double2 *bk = (const double2 *)b + (size_t)k * n;
+        double2 *xk[NS];
+        for (int i = 0; i < nshift; i++) xk[i] = (double2 *)x[i] + (size_t)k * n;
+        double bb = 0;
+        {
+            double *part = (double *)g->partials;
+            cudaMemsetAsync(m.y64, 0, sizeof(double2) * n, s);
+            k_diff_norm<<<nbs, UPD_THREADS, 0, s>>>(n, bk, m.y64, part);
+            std::vector<double> h(nbs);
+            cudaMemcpyAsync(h.data(), part, sizeof(double) * nbs, cudaMemcpyDeviceToHost, s);
+            TMND_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int q = 0; q < nbs; q++) bb += h[q];
+        }
+        // case-C right-hand side (0, gamma_5 tau_1 b) in FP32 full layout (parity 0 even, 1 odd)
+        k_g5tau1<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Vh, bk, gb);
+        cudaMemsetAsync(rhs, 0, sizeof(float2) * n, s);
+        k_to_f32_scaled<<<nbs, 256, 0, s>>>(n, 1.0, gb, rhs + n);
+        for (int i = n_mms; i < nshift && res_status == TMND_OK; i++) {
+            // guess
+            if (i >= nmms_all) {
+                if (hp->guess >= 1) {
+                    const int kk = i < 8 ? i : 8;
+                    const void *xs[8];
+                    for (int j = 0; j < kk; j++) xs[j] = xk[i - kk + j];
+                    st = lagrange_guess(g, sigma + (i - kk), xs, kk, sigma[i], xk[i], 1, nullptr, stream);
+                    if (st != TMND_OK) { res_status = st; break; }
+                } else {
+                    cudaMemsetAsync(xk[i], 0, sizeof(double2) * n, s);
+                }
+            }
+            double rr0 = 0;
+            st = fp64_defect(g, m, bk, xk[i], sigma[i], s, &rr0);
+            if (st != TMND_OK) { res_status = st; break; }
+            if (hinfo && k == 0) hinfo->guess_res[i] = sqrt(rr0 / bb);
+            const double sq = sqrt(sigma[i]);
+            int mg_it = 0;
+            if (sqrt(rr0 / bb) > hp->rho) {
+                for (int sgn = 1; sgn >= -1; sgn -= 2) {
+                    float2 *y = sgn > 0 ? yp : ym;
+                    // odd guess (Qhat - sgn i s) x~ ; Qhat = g5 t1 Mhat
+                    HopEpiArgs ea = {};
+                    launch_hop_even_f64(g->geom, g->st, g->links, xk[i], te, false, nullptr, s);
+                    launch_hop_odd_f64(g->geom, g->st, g->links, xk[i], te, tq, false, EPI_STORE, ea, s);
+                    k_g5tau1<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Vh, tq, gb);
+                    k_zaxpy64<<<nbs, 256, 0, s>>>(n, 0.0, -sgn * sq, xk[i], gb);
+                    // even part eliminated: x_e = -D_ee^-1 D_eo x_o = kappa A^-1 H x_o = t_e / kappa
+                    launch_hop_even_f64(g->geom, g->st, g->links, gb, te, false, nullptr, s);
+                    k_to_f32_scaled<<<nbs, 256, 0, s>>>(n, 1.0 / g->act.kappa, te, y);
+                    k_to_f32_scaled<<<nbs, 256, 0, s>>>(n, 1.0, gb, y + n);
+                    int it = 0;
+                    double rres = 0;
+                    const double tol = hp->mg_tol > 0 ? hp->mg_tol : 1e-6;
+                    st = mg_gcr_solve(mg, y, rhs, sgn * sq, tol, hp->mg_maxiter > 0 ? hp->mg_maxiter : 200,
+                                      hp->mg_restart > 0 ? hp->mg_restart : 8, hp->mg_nu > 0 ? hp->mg_nu : 4, s, &it,
+                                      &rres, gcr);
+                    if (st != TMND_OK) { res_status = st; break; }
+                    mg_it += it;
+                }
+                if (res_status != TMND_OK) break;
+                k_casec_combine<<<nbs, 256, 0, s>>>(n, sq, yp + n, ym + n, xk[i]);
+            }
+            if (hinfo && k == 0) hinfo->mg_iters[i] = mg_it;
+            // FP64 defect correction to rho
+            std::vector<double> res(nshift, 0.0);
+            RefineStats rs;
+            st = defect_correct(g, m, bk, xk, sigma, std::vector<int>{i}, bb, hp->rho, rho_inner, hp->maxiter, 32,
+                                0, s, res, rs);
+            if (st != TMND_OK) { res_status = st; break; }
+            if (hinfo) {
+                hinfo->fp64_applies += rs.fp64 + 1;
+                hinfo->refine_iters += rs.iters;
+                if (k == 0 || res[i] > hinfo->true_res[i]) hinfo->true_res[i] = res[i];
+            }
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(scr);
+    return res_status;
 }

@@ -1,0 +1,171 @@
+"""Parity of the GPU multigrid pieces (Sec. 3, 3.2) with the FP64 oracle:
+prolongator (block Gram-Schmidt of the same test vectors), coarse Wilson
+operator P^+ D_W P, odd-site Gram G_odd, restriction / prolongation, and the
+coarse doublet stencil mg_coarse_apply.  FP32 on the device: tolerances 2e-5
+relative (sums of ~1e3 FP32 products of O(1) numbers)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import EPS, KAPPA, MU, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+NV = 4
+
+
+def to_mg_layout(dims, canon, ncomp):
+    """canonical [..., V, ncomp] (lexicographic) -> [..., 2 parity, ncomp, V/2]"""
+    V = int(np.prod(dims))
+    T, X, Y, Z = dims
+    t, x, y, z = np.meshgrid(np.arange(T), np.arange(X), np.arange(Y), np.arange(Z), indexing="ij")
+    par = ((t + x + y + z) & 1).ravel()
+    lead = canon.shape[:-2]
+    out = np.zeros(lead + (2, ncomp, V // 2), np.complex64)
+    lex = np.arange(V)
+    for pp in (0, 1):
+        sel = lex[par == pp]
+        out[..., pp, :, :] = np.moveaxis(canon[..., sel, :], -1, -2)
+    return out
+
+
+def from_mg_layout(dims, mg, ncomp):
+    V = int(np.prod(dims))
+    T, X, Y, Z = dims
+    t, x, y, z = np.meshgrid(np.arange(T), np.arange(X), np.arange(Y), np.arange(Z), indexing="ij")
+    par = ((t + x + y + z) & 1).ravel()
+    lead = mg.shape[:-3]
+    out = np.zeros(lead + (V, ncomp), np.complex128)
+    lex = np.arange(V)
+    for pp in (0, 1):
+        sel = lex[par == pp]
+        out[..., sel, :] = np.moveaxis(mg[..., pp, :, :], -2, -1)
+    return out
+
+
+@pytest.fixture(scope="module", params=[((4, 4, 4, 4), (2, 2, 2, 2)), ((8, 4, 4, 4), (2, 2, 2, 2))])
+def mgsetup(request):
+    tm = require_gpu()
+    dims, bdims = request.param
+    U = synth.random_su3_field(dims, 0.5, 99)
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(3)
+    vecs = (rng.standard_normal((NV, V, 12)) + 1j * rng.standard_normal((NV, V, 12))).astype(np.complex64)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    tv = torch.from_numpy(to_mg_layout(dims, vecs, 12)).cuda()
+    mg = tm.tmnd_mg_create(g.handle, bdims, NV, tv)
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    P = oracle.mg_prolongator(dims, bdims, vecs.astype(np.complex128).reshape(NV, V, 4, 3))
+    Dcw = oracle.mg_coarse_wilson(act, U, P)
+    nb = P.shape[1] // (2 * NV)
+    yield dict(tm=tm, g=g, mg=mg, dims=dims, bdims=bdims, U=U, P=P, Dcw=Dcw, nb=nb, act=act, vecs=vecs)
+    tm.tmnd_mg_destroy(mg)
+    g.close()
+
+
+def _gpu_P_dense(s):
+    dims, bdims, nb = s["dims"], s["bdims"], s["nb"]
+    nsb = int(np.prod(bdims))
+    V = int(np.prod(dims))
+    Ph = np.zeros((nb, 2, NV, nsb, 6), np.complex64)
+    s["tm"].tmnd_mg_export(s["mg"], P_host=Ph)
+    blk = oracle.mg_block_of_site(dims, bdims)
+    dense = np.zeros((V * 12, nb * 2 * NV), np.complex128)
+    for b in range(nb):
+        sites = np.nonzero(blk == b)[0]   # lexicographic order = block-local order
+        for chi in range(2):
+            for k in range(NV):
+                for si, site in enumerate(sites):
+                    dense[site * 12 + chi * 6: site * 12 + chi * 6 + 6, b * 2 * NV + chi * NV + k] = Ph[b, chi, k, si]
+    return dense
+
+
+def test_prolongator_matches_oracle(mgsetup):
+    s = mgsetup
+    Pg = _gpu_P_dense(s)
+    assert np.max(np.abs(Pg - s["P"])) < 2e-5
+
+
+def test_coarse_operator_matches_oracle(mgsetup):
+    s = mgsetup
+    nb, n2 = s["nb"], 2 * NV
+    Dh = np.zeros((nb, 9, n2, n2), np.complex64)
+    Gh = np.zeros((nb, n2, n2), np.complex64)
+    s["tm"].tmnd_mg_export(s["mg"], Dc_host=Dh, Godd_host=Gh)
+    nbd = [d // b for d, b in zip(s["dims"], s["bdims"])]
+    dense = np.zeros((nb * n2, nb * n2), np.complex128)
+    for b in range(nb):
+        c = list(np.unravel_index(b, nbd))
+        for d in range(9):
+            cc = list(c)
+            if d > 0:
+                mu = (d - 1) // 2
+                cc[mu] = (cc[mu] + (1 if (d - 1) % 2 == 0 else -1)) % nbd[mu]
+            b2 = int(np.ravel_multi_index(cc, nbd))
+            dense[b * n2:(b + 1) * n2, b2 * n2:(b2 + 1) * n2] += Dh[b, d]
+    scale = np.abs(s["Dcw"]).max()
+    assert np.max(np.abs(dense - s["Dcw"])) < 2e-5 * scale
+    # G_odd = P^+ gamma_5 Pi_odd P
+    V = int(np.prod(s["dims"]))
+    odd = np.zeros(V, bool)
+    odd[synth.odd_sites(s["dims"])] = True
+    g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), V) * np.repeat(odd, 12)
+    Gref = s["P"].conj().T @ (g5[:, None] * s["P"])
+    for b in range(nb):
+        assert np.max(np.abs(Gh[b] - Gref[b * n2:(b + 1) * n2, b * n2:(b + 1) * n2])) < 2e-5
+
+
+def test_restrict_prolong_match_oracle(mgsetup):
+    s = mgsetup
+    tm, mg, dims = s["tm"], s["mg"], s["dims"]
+    V = int(np.prod(dims))
+    nb = s["nb"]
+    rng = np.random.default_rng(11)
+    fine = rng.standard_normal((2, V, 24)) + 1j * rng.standard_normal((2, V, 24))   # 2 RHS, doublet
+    fin = torch.from_numpy(to_mg_layout(dims, fine.astype(np.complex64), 24)).cuda()
+    coarse = torch.zeros(2 * nb * 2 * 2 * NV, dtype=torch.complex64, device="cuda")
+    tm.tmnd_mg_restrict(mg, coarse, fin, 2)
+    got = coarse.cpu().numpy().reshape(2, nb, 2, 2 * NV)
+    P = s["P"]
+    for r in range(2):
+        for f in range(2):
+            ref = P.conj().T @ fine[r, :, f * 12:(f + 1) * 12].ravel()
+            assert np.max(np.abs(got[r, :, f, :].ravel() - ref)) < 2e-5 * np.abs(ref).max()
+    cv = rng.standard_normal((2, nb, 2, 2 * NV)) + 1j * rng.standard_normal((2, nb, 2, 2 * NV))
+    cin = torch.from_numpy(cv.astype(np.complex64).ravel()).cuda()
+    fout = torch.zeros(2 * 2 * 24 * (V // 2), dtype=torch.complex64, device="cuda")
+    tm.tmnd_mg_prolong(mg, fout, cin, 2)
+    back = from_mg_layout(dims, fout.cpu().numpy().reshape(2, 2, 24, V // 2), 24)
+    for r in range(2):
+        for f in range(2):
+            ref = P @ cv[r, :, f, :].ravel()
+            assert np.max(np.abs(back[r, :, f * 12:(f + 1) * 12].ravel() - ref)) < 2e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("s_odd", [0.0, 0.03])
+def test_coarse_apply_matches_oracle(mgsetup, s_odd):
+    s = mgsetup
+    tm, mg, nb = s["tm"], s["mg"], s["nb"]
+    n2 = 2 * NV
+    Dnd = oracle.mg_coarse_nd(s["Dcw"], nb, NV, 2 * KAPPA * MU, 2 * KAPPA * EPS)
+    if s_odd:
+        V = int(np.prod(s["dims"]))
+        odd = np.zeros(V, bool)
+        odd[synth.odd_sites(s["dims"])] = True
+        g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), V) * np.repeat(odd, 12)
+        G = s["P"].conj().T @ (g5[:, None] * s["P"])
+        for b in range(nb):
+            i0 = b * 2 * n2
+            blk = G[b * n2:(b + 1) * n2, b * n2:(b + 1) * n2]
+            Dnd[i0:i0 + n2, i0 + n2:i0 + 2 * n2] += 1j * s_odd * blk
+            Dnd[i0 + n2:i0 + 2 * n2, i0:i0 + n2] += 1j * s_odd * blk
+    rng = np.random.default_rng(5)
+    R = 3
+    xv = rng.standard_normal((R, nb * 2 * n2)) + 1j * rng.standard_normal((R, nb * 2 * n2))
+    xin = torch.from_numpy(xv.astype(np.complex64).ravel()).cuda()
+    yout = torch.zeros_like(xin)
+    tm.mg_coarse_apply(mg, yout, xin, R, s_odd)
+    got = yout.cpu().numpy().reshape(R, -1)
+    for r in range(R):
+        ref = Dnd @ xv[r]
+        assert np.max(np.abs(got[r] - ref)) < 2e-5 * np.abs(ref).max()
