@@ -303,3 +303,87 @@ def dnd_odd_shift(act: Action, links, psi_full, s) -> np.ndarray:
     term = 1j * s * g5[None, None, :, None] * psi[:, ::-1]   # tau_1 swaps the flavours
     out[odd] += term[odd]
     return out
+
+
+# ------------------------------------------------------------ learned guess
+# Not in the paper: a small network proposes interpolation weights over the
+# solutions x_j of 8 already-solved shifts for a smaller target shift sigma_t,
+# replacing the Lagrange weights of Sec. 4.2.1.  With sum_j w_j = 1 (partition
+# of unity, App. B Eq. "lagrange_id") and exact x_j, the residual of the guess is
+#   b - (Qhat^2 + sigma_t) sum_j w_j x_j = - sum_j w_j (sigma_t - sigma_j) x_j      (App. B)
+# so |residual|^2 = w^T H w with H = Re(D G D), G_jk = <x_j, x_k> / |b|^2,
+# D = diag(sigma_t - sigma_j): a loss that needs no operator application.
+# Network: F -> 64 -> 64 -> 8, tanh, then the affine projection w = o + (1 - sum o)/8.
+# Per-sample loss log(w^T H w) (scale free across shifts); batch loss = mean.
+MLP_H = 64
+MLP_K = 8
+
+
+def mlp_sizes(F):
+    return [(MLP_H, F), (MLP_H,), (MLP_H, MLP_H), (MLP_H,), (MLP_K, MLP_H), (MLP_K,)]
+
+
+def mlp_unflatten(theta, F):
+    out, o = [], 0
+    for shp in mlp_sizes(F):
+        n = int(np.prod(shp))
+        out.append(np.asarray(theta[o:o + n], np.float64).reshape(shp))
+        o += n
+    return out
+
+
+def mlp_forward(theta, X):
+    """Weights w [N, 8] (each row sums to 1) for features X [N, F]."""
+    X = np.asarray(X, np.float64)
+    W1, b1, W2, b2, W3, b3 = mlp_unflatten(theta, X.shape[1])
+    h1 = np.tanh(X @ W1.T + b1)
+    h2 = np.tanh(h1 @ W2.T + b2)
+    o = h2 @ W3.T + b3
+    return o + (1.0 - o.sum(axis=1, keepdims=True)) / MLP_K
+
+
+def mlp_loss_grad(theta, X, H):
+    """Mean over samples of log(w^T H w) and its gradient in theta (plain
+    backpropagation, written out layer by layer)."""
+    X = np.asarray(X, np.float64)
+    H = np.asarray(H, np.float64)
+    N, F = X.shape
+    W1, b1, W2, b2, W3, b3 = mlp_unflatten(theta, F)
+    a1 = X @ W1.T + b1
+    h1 = np.tanh(a1)
+    a2 = h1 @ W2.T + b2
+    h2 = np.tanh(a2)
+    o = h2 @ W3.T + b3
+    w = o + (1.0 - o.sum(axis=1, keepdims=True)) / MLP_K
+    q = np.einsum("ni,nij,nj->n", w, H, w)
+    loss = float(np.mean(np.log(q)))
+    dw = (2.0 * np.einsum("nij,nj->ni", H, w)) / q[:, None] / N
+    do = dw - dw.sum(axis=1, keepdims=True) / MLP_K
+    gW3 = do.T @ h2
+    gb3 = do.sum(axis=0)
+    dh2 = do @ W3
+    da2 = dh2 * (1 - h2 ** 2)
+    gW2 = da2.T @ h1
+    gb2 = da2.sum(axis=0)
+    dh1 = da2 @ W2
+    da1 = dh1 * (1 - h1 ** 2)
+    gW1 = da1.T @ X
+    gb1 = da1.sum(axis=0)
+    grad = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
+    return loss, grad
+
+
+def span_optimal_weights(H):
+    """argmin_w w^T H w subject to sum_j w_j = 1:  w = H^-1 1 / (1^T H^-1 1)."""
+    H = np.asarray(H, np.float64)
+    one = np.ones(H.shape[-1])
+    v = np.linalg.solve(H, one)
+    return v / v.sum()
+
+
+def guess_quadratic_form(sig_nodes, sig_t, xs, bnorm2):
+    """H = Re(D G D) with G_jk = <x_j, x_k> / |b|^2 and D = diag(sigma_t - sigma_j)."""
+    X = np.stack([np.asarray(x, np.complex128).ravel() for x in xs])
+    G = (X.conj() @ X.T) / bnorm2
+    d = float(sig_t) - np.asarray(sig_nodes, np.float64)
+    return np.real(d[:, None] * G * d[None, :])

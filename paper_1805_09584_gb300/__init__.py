@@ -106,6 +106,7 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp]
         L.lagrange_guess.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(vp), i, d, vp, i,
                                      ctypes.POINTER(d), vp]
+        L.tmnd_last_error.argtypes = []
         L.tmnd_last_error.restype = ctypes.c_char_p
         L.tmnd_mg_create.argtypes = [vp, ctypes.POINTER(MGParams), vp, ctypes.POINTER(vp)]
         L.tmnd_mg_destroy.argtypes = [vp]
@@ -118,9 +119,11 @@ def lib() -> ctypes.CDLL:
         L.tmnd_mg_export.argtypes = [vp, vp, vp, vp]
         L.tmnd_dnd_full_apply.argtypes = [vp, vp, vp, d, vp]
         L.tmnd_mg_solve.argtypes = [vp, vp, vp, d, d, i, i, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]
+        L.tmnd_mg_smooth_vectors.argtypes = [vp, vp, i, i, vp]
+        L.tmnd_hybrid_solve.argtypes = [vp, vp, vp, i, ctypes.POINTER(d), i, i, ctypes.POINTER(vp),
+                                        ctypes.POINTER(HybridParams), ctypes.POINTER(HybridInfo), vp]
         for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
-                     "tmnd_dnd_full_apply", "tmnd_mg_solve",
-           "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve"):
+                     "tmnd_dnd_full_apply", "tmnd_mg_solve", "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_gauge_create", "tmnd_spinor_pack", "tmnd_spinor_unpack", "tm_nd_apply",
                      "tm_nd_apply_noalloc", "mms_cg_solve", "lagrange_guess"):

@@ -30,6 +30,9 @@ def test_exports_match_header(tm):
     L = tm.lib()
     for name in declared:
         assert hasattr(L, name), name
+        # every entry point has its argument types declared: without them ctypes
+        # would pass 64-bit device pointers as 32-bit ints
+        assert getattr(L, name).argtypes is not None, name
 
 
 def test_rejects_bad_arguments_without_gpu(tm):
