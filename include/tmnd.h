@@ -184,6 +184,9 @@ typedef struct {
                               the defect to rho_inner, FP64 update, until every required
                               shift's FP64 true residual is <= rho. */
     double rho_inner;      /* TMND_S16: relative tolerance of each sloppy solve (0 = 1e-5) */
+    double *ab_hist;       /* optional host array: receives (alpha_k, beta_k), k = 1.., of the base
+                              recursion of the first RHS (the Lanczos coefficients), zero-padded */
+    int ab_hist_len;       /* length of ab_hist in doubles (2 per iteration) */
 } tmnd_solve_params;
 
 typedef struct {
@@ -304,8 +307,9 @@ typedef struct {
                               CG as guesses (Sec. 4.2.2; the paper uses 2) */
     int guess;             /* remaining shifts: 1 = Lagrange guess over the nearest <= 8 solved
                               shifts (Sec. 4.2.1), 0 = zero start */
-    double mg_tol;         /* relative tolerance of each case-C MG solve (0 = 1e-6) */
-    int mg_maxiter, mg_restart, mg_nu;   /* 0 = 200, 8, 4 */
+    double mg_tol;         /* relative tolerance of each case-C MG solve (0 = 1e-4; the solve is
+                              FP32, the FP64 defect correction finishes the shift) */
+    int mg_maxiter, mg_restart, mg_nu;   /* 0 = 100, 8, 4 */
 } tmnd_hybrid_params;
 
 typedef struct {
@@ -327,6 +331,55 @@ tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void *b, int nrh
 
 /* Copy P, D_W,c and G_odd to host buffers (any may be NULL); for tests and inspection. */
 tmnd_status tmnd_mg_export(const tmnd_mg *mg, void *P_host, void *Dc_host, void *Godd_host);
+
+/* ------------------------------------------------------------ learned guess
+ * Not in the paper; it extends the Lagrange guesses (Sec. 4.2.1).  A network
+ * F -> 64 -> 64 -> 2 (tanh) predicts two log-poles o_k for a target shift sigma_t;
+ * with p_k = exp(o_k) the weights over the solutions of 8 solved shifts sigma_j are
+ *   w_j = l_j(sigma_t) prod_k (p_k + sigma_j) / (p_k + sigma_t)
+ * (Lagrange interpolation of prod_k (p_k + sigma) x(sigma), divided back): they sum
+ * to 1 for any poles (partition of unity, App. B) and tend to the Lagrange weights
+ * as p_k -> infinity.
+ * Parameters: FP32 [mu (F) isd (F) W1 (64xF) b1 W2 (64x64) b2 W3 (2x64) b3], row-major;
+ * mu/isd standardise the inputs, x -> (x - mu) * isd, and are not trained.
+ * Samples: X device float [N][F] (features); S device double [N][9] = (sigma_t,
+ * sigma_1..sigma_8); H device double [N][8][8] row-major = Re(D G D), G = Gram matrix
+ * of the 8 solutions / |b|^2, D = diag(sigma_t - sigma_j).  Loss per sample:
+ * log(w^T H w + floor) -- with exact solutions and sum w = 1, w^T H w is the squared
+ * relative residual of the guess; floor (>= 0, e.g. rho^2 of the solves that made the
+ * data) stands for the residuals the solutions still carry.  Batch loss = mean. */
+typedef struct tmnd_mlp tmnd_mlp;
+int tmnd_mlp_num_params(int F);
+/* Parameters initialised from `seed` (Gaussian, scale 1/sqrt(fan-in); last layer x0.1;
+ * biases 0; mu = 0, isd = 1). */
+tmnd_status tmnd_mlp_create(int F, unsigned long long seed, tmnd_mlp **out);
+void tmnd_mlp_destroy(tmnd_mlp *m);
+/* Copy the FP32 parameters to host_get and/or set them from host_set (either may be NULL). */
+tmnd_status tmnd_mlp_params(tmnd_mlp *m, float *host_get, const float *host_set);
+/* Set mu/isd to the per-feature mean and 1/standard deviation of X [N][F] (device; isd = 1
+ * for a constant feature).  Call once on the training set before training. */
+tmnd_status tmnd_mlp_fit_inputs(tmnd_mlp *m, const void *X, int N, void *stream);
+/* Mean loss over N samples and its gradient (FP32 network, FP64 weights and loss);
+ * grad_host: host float[num_params] or NULL (zero on mu/isd). */
+tmnd_status tmnd_mlp_loss_grad(tmnd_mlp *m, const void *X, const void *S, const void *H, int N, double floor_q,
+                               double *loss, float *grad_host, void *stream);
+/* One Adam step (beta 0.9/0.999, eps 1e-8) on the mean loss of the N samples; loss may be NULL. */
+tmnd_status tmnd_mlp_train_step(tmnd_mlp *m, const void *X, const void *S, const void *H, int N, double lr,
+                                double floor_q, double *loss, void *stream);
+/* Weights W (device double [N][8], rows sum to 1) from X and S, with BF16 layer weights
+ * and FP32 accumulation; the weights themselves are formed in FP64. */
+tmnd_status tmnd_mlp_predict(tmnd_mlp *m, const void *X, const void *S, int N, void *W, void *stream);
+/* Network input (F = 20) for target shift `target` and 8 solved shifts `nodes`, from the
+ * base recursion's (alpha_k, beta_k) history of niter iterations on the base shift sigma0
+ * (host function; see mlp.cu for the feature list). */
+tmnd_status tmnd_mlp_features(const double *nodes, double target, const double *ab_hist, int niter, double sigma0,
+                              float *out);
+/* G_jk = <x_j, x_k> (complex, FP64) of k <= 8 internal FP64 spinors (one RHS each);
+ * G_host: 2*k*k doubles, row-major, interleaved re/im.  Synchronous. */
+tmnd_status tmnd_gram(const tmnd_gauge *g, const void *const *xs, int k, double *G_host, void *stream);
+/* out = sum_j w_j xs[j] for k <= 8 internal FP64 spinors with given FP64 weights (host). */
+tmnd_status tmnd_lincomb(const tmnd_gauge *g, const double *w, const void *const *xs, int k, void *out, int nrhs,
+                         void *stream);
 
 /* Message for the last error on this host thread ("" if none). */
 const char *tmnd_last_error(void);

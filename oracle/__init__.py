@@ -308,19 +308,31 @@ def dnd_odd_shift(act: Action, links, psi_full, s) -> np.ndarray:
 # ------------------------------------------------------------ learned guess
 # Not in the paper: a small network proposes interpolation weights over the
 # solutions x_j of 8 already-solved shifts for a smaller target shift sigma_t,
-# replacing the Lagrange weights of Sec. 4.2.1.  With sum_j w_j = 1 (partition
-# of unity, App. B Eq. "lagrange_id") and exact x_j, the residual of the guess is
+# extending the Lagrange weights of Sec. 4.2.1.  With sum_j w_j = 1 (partition
+# of unity, App. B) and exact x_j, the residual of the guess is
 #   b - (Qhat^2 + sigma_t) sum_j w_j x_j = - sum_j w_j (sigma_t - sigma_j) x_j      (App. B)
 # so |residual|^2 = w^T H w with H = Re(D G D), G_jk = <x_j, x_k> / |b|^2,
 # D = diag(sigma_t - sigma_j): a loss that needs no operator application.
-# Network: F -> 64 -> 64 -> 8, tanh, then the affine projection w = o + (1 - sum o)/8.
+#
+# Head: the network (F -> 64 -> 64 -> 2, tanh) outputs two log-poles o_k,
+# p_k = exp(o_k), and the weights are those of Lagrange interpolation (Sec.
+# 4.2.1) applied to prod_k (p_k + sigma) x(sigma) and divided back:
+#   w_j = l_j(sigma_t) prod_k (p_k + sigma_j) / (p_k + sigma_t).
+# They reproduce every x(sigma) = P_7(sigma) / prod_k (p_k + sigma) exactly, sum
+# to 1 for any poles (Lagrange reproduces the degree-2 numerator), and tend to
+# the Lagrange weights as p_k -> infinity.  The guess residual is tiny (down to
+# ~1e-9 |b|), which raw FP32 weights could not resolve; poles can be predicted
+# in FP32 and the weights are then formed in FP64.
 # Per-sample loss log(w^T H w) (scale free across shifts); batch loss = mean.
 MLP_H = 64
-MLP_K = 8
+MLP_K = 8      # solved shifts the guess combines
+MLP_P = 2      # network outputs: log-poles
 
 
 def mlp_sizes(F):
-    return [(MLP_H, F), (MLP_H,), (MLP_H, MLP_H), (MLP_H,), (MLP_K, MLP_H), (MLP_K,)]
+    """Parameter blocks: input mean mu and inverse std isd (x -> (x - mu) isd, not
+    trained), then W1 b1 W2 b2 W3 b3."""
+    return [(F,), (F,), (MLP_H, F), (MLP_H,), (MLP_H, MLP_H), (MLP_H,), (MLP_P, MLP_H), (MLP_P,)]
 
 
 def mlp_unflatten(theta, F):
@@ -332,33 +344,53 @@ def mlp_unflatten(theta, F):
     return out
 
 
-def mlp_forward(theta, X):
-    """Weights w [N, 8] (each row sums to 1) for features X [N, F]."""
-    X = np.asarray(X, np.float64)
-    W1, b1, W2, b2, W3, b3 = mlp_unflatten(theta, X.shape[1])
+def pole_weights(S, poles):
+    """w [N, 8] from S [N, 9] = (sigma_t, sigma_1..sigma_8) and poles [N, P]:
+    w_j = l_j(sigma_t) prod_k (p_k + sigma_j) / (p_k + sigma_t)."""
+    S = np.asarray(S, np.float64)
+    poles = np.asarray(poles, np.float64)
+    t, nodes = S[:, 0], S[:, 1:]
+    w = np.stack([lagrange_weights(nodes[n], t[n]) for n in range(len(S))])
+    for k in range(poles.shape[1]):
+        p = poles[:, k:k + 1]
+        w = w * (p + nodes) / (p + t[:, None])
+    return w
+
+
+def mlp_forward(theta, X, S):
+    """Weights w [N, 8] (each row sums to 1) for features X [N, F] and shifts S [N, 9]."""
+    mu, isd, W1, b1, W2, b2, W3, b3 = mlp_unflatten(theta, np.shape(X)[1])
+    X = (np.asarray(X, np.float64) - mu) * isd
     h1 = np.tanh(X @ W1.T + b1)
     h2 = np.tanh(h1 @ W2.T + b2)
     o = h2 @ W3.T + b3
-    return o + (1.0 - o.sum(axis=1, keepdims=True)) / MLP_K
+    return pole_weights(S, np.exp(o))
 
 
-def mlp_loss_grad(theta, X, H):
-    """Mean over samples of log(w^T H w) and its gradient in theta (plain
-    backpropagation, written out layer by layer)."""
-    X = np.asarray(X, np.float64)
+def mlp_loss_grad(theta, X, S, H, floor=0.0):
+    """Mean over samples of log(w^T H w + floor) and its gradient in theta (plain
+    backpropagation, written out layer by layer).  floor ~ rho^2 stands for the
+    residuals rho |b| that the solved x_j still carry (the guess residual is not
+    known below that)."""
+    S = np.asarray(S, np.float64)
     H = np.asarray(H, np.float64)
-    N, F = X.shape
-    W1, b1, W2, b2, W3, b3 = mlp_unflatten(theta, F)
+    N, F = np.shape(X)
+    mu, isd, W1, b1, W2, b2, W3, b3 = mlp_unflatten(theta, F)
+    X = (np.asarray(X, np.float64) - mu) * isd
     a1 = X @ W1.T + b1
     h1 = np.tanh(a1)
     a2 = h1 @ W2.T + b2
     h2 = np.tanh(a2)
     o = h2 @ W3.T + b3
-    w = o + (1.0 - o.sum(axis=1, keepdims=True)) / MLP_K
-    q = np.einsum("ni,nij,nj->n", w, H, w)
+    p = np.exp(o)
+    w = pole_weights(S, p)
+    q = np.einsum("ni,nij,nj->n", w, H, w) + floor
     loss = float(np.mean(np.log(q)))
     dw = (2.0 * np.einsum("nij,nj->ni", H, w)) / q[:, None] / N
-    do = dw - dw.sum(axis=1, keepdims=True) / MLP_K
+    # d w_j / d o_k = w_j p_k (1/(p_k + sigma_j) - 1/(p_k + sigma_t))
+    t, nodes = S[:, :1], S[:, 1:]
+    do = np.stack([np.sum(dw * w * p[:, k:k + 1] * (1.0 / (p[:, k:k + 1] + nodes) - 1.0 / (p[:, k:k + 1] + t)),
+                          axis=1) for k in range(MLP_P)], axis=1)
     gW3 = do.T @ h2
     gb3 = do.sum(axis=0)
     dh2 = do @ W3
@@ -369,7 +401,7 @@ def mlp_loss_grad(theta, X, H):
     da1 = dh1 * (1 - h1 ** 2)
     gW1 = da1.T @ X
     gb1 = da1.sum(axis=0)
-    grad = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
+    grad = np.concatenate([np.zeros(2 * F), gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
     return loss, grad
 
 

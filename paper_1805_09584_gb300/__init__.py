@@ -32,7 +32,9 @@ EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd
            "tmnd_spinor_unpack", "tm_nd_apply", "tm_nd_apply_noalloc", "mms_cg_solve", "lagrange_guess",
            "tmnd_last_error", "tmnd_mg_create", "tmnd_mg_destroy", "tmnd_mg_coarse_bytes", "tmnd_mg_restrict",
            "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export", "tmnd_dnd_full_apply", "tmnd_mg_solve",
-           "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve")
+           "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve", "tmnd_mlp_num_params", "tmnd_mlp_create",
+           "tmnd_mlp_destroy", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad", "tmnd_mlp_train_step", "tmnd_mlp_predict",
+           "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb")
 NOALLOC_MAX_VH = 32768
 
 
@@ -67,7 +69,8 @@ class HybridInfo(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("maxiter", ctypes.c_int), ("nsolve", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("profile", ctypes.c_int), ("prec", ctypes.c_int),
-                ("rho_inner", ctypes.c_double)]
+                ("rho_inner", ctypes.c_double), ("ab_hist", ctypes.POINTER(ctypes.c_double)),
+                ("ab_hist_len", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -122,6 +125,24 @@ def lib() -> ctypes.CDLL:
         L.tmnd_mg_smooth_vectors.argtypes = [vp, vp, i, i, vp]
         L.tmnd_hybrid_solve.argtypes = [vp, vp, vp, i, ctypes.POINTER(d), i, i, ctypes.POINTER(vp),
                                         ctypes.POINTER(HybridParams), ctypes.POINTER(HybridInfo), vp]
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.tmnd_mlp_num_params.argtypes = [i]
+        L.tmnd_mlp_num_params.restype = ctypes.c_int
+        L.tmnd_mlp_create.argtypes = [i, ctypes.c_ulonglong, ctypes.POINTER(vp)]
+        L.tmnd_mlp_destroy.argtypes = [vp]
+        L.tmnd_mlp_destroy.restype = None
+        L.tmnd_mlp_params.argtypes = [vp, vp, vp]
+        L.tmnd_mlp_fit_inputs.argtypes = [vp, vp, i, vp]
+        L.tmnd_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i, d, ctypes.POINTER(d), vp, vp]
+        L.tmnd_mlp_train_step.argtypes = [vp, vp, vp, vp, i, d, d, ctypes.POINTER(d), vp]
+        L.tmnd_mlp_predict.argtypes = [vp, vp, vp, i, vp, vp]
+        L.tmnd_mlp_features.argtypes = [ctypes.POINTER(d), d, vp, i, d, fp]
+        L.tmnd_gram.argtypes = [vp, ctypes.POINTER(vp), i, ctypes.POINTER(d), vp]
+        L.tmnd_lincomb.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(vp), i, vp, i, vp]
+        for name in ("tmnd_mlp_create", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad",
+                     "tmnd_mlp_train_step",
+                     "tmnd_mlp_predict", "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
                      "tmnd_dnd_full_apply", "tmnd_mg_solve", "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve"):
             getattr(L, name).restype = ctypes.c_int
@@ -208,12 +229,16 @@ def tm_nd_apply_noalloc(h, out, inp, op: int, sigma: float = 0.0, nrhs: int = 1,
 
 def mms_cg_solve(h, b, nrhs: int, sigma, x, rho: float = 1e-10, maxiter: int = 100000, nsolve: int = 0,
                  check_every: int = 0, profile: bool = False, prec: int = TMND_F64, rho_inner: float = 0.0,
-                 stream=None) -> dict:
+                 ab_hist=None, stream=None) -> dict:
     sig = np.ascontiguousarray(sigma, dtype=np.float64)
     ns = len(sig)
     xs = (ctypes.c_void_p * ns)(*[_ptr(v) for v in x])
     p = SolveParams(float(rho), int(maxiter), int(nsolve), int(check_every), int(bool(profile)), int(prec),
                     float(rho_inner))
+    if ab_hist is not None:
+        assert ab_hist.dtype == np.float64 and ab_hist.flags["C_CONTIGUOUS"]
+        p.ab_hist = ab_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.ab_hist_len = int(ab_hist.size)
     info = SolveInfo()
     st = lib().mms_cg_solve(h, _ptr(b), int(nrhs), sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns, xs,
                             ctypes.byref(p), ctypes.byref(info), _stream(stream))
@@ -304,6 +329,78 @@ def tmnd_hybrid_solve(h, mg, b, nrhs: int, sigma, n_mms: int, x, rho: float = 1e
            "fp64_applies": info.fp64_applies, "refine_iters": info.refine_iters}
     _check(st)
     return out
+
+
+def tmnd_mlp_num_params(F: int) -> int:
+    return int(lib().tmnd_mlp_num_params(int(F)))
+
+
+def tmnd_mlp_create(F: int = 20, seed: int = 0):
+    out = ctypes.c_void_p()
+    _check(lib().tmnd_mlp_create(int(F), ctypes.c_ulonglong(int(seed)), ctypes.byref(out)))
+    return out
+
+
+def tmnd_mlp_destroy(m) -> None:
+    lib().tmnd_mlp_destroy(m)
+
+
+def tmnd_mlp_params(m, get: np.ndarray = None, set_: np.ndarray = None) -> None:
+    for a in (get, set_):
+        if a is not None:
+            assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    _check(lib().tmnd_mlp_params(m, None if get is None else get.ctypes.data,
+                                 None if set_ is None else set_.ctypes.data))
+
+
+def tmnd_mlp_fit_inputs(m, X, N: int, stream=None) -> None:
+    _check(lib().tmnd_mlp_fit_inputs(m, _ptr(X), int(N), _stream(stream)))
+
+
+def tmnd_mlp_loss_grad(m, X, S, H, N: int, floor: float = 0.0, grad: np.ndarray = None, stream=None) -> float:
+    loss = ctypes.c_double()
+    if grad is not None:
+        assert grad.dtype == np.float32 and grad.flags["C_CONTIGUOUS"]
+    _check(lib().tmnd_mlp_loss_grad(m, _ptr(X), _ptr(S), _ptr(H), int(N), float(floor), ctypes.byref(loss),
+                                    None if grad is None else grad.ctypes.data, _stream(stream)))
+    return loss.value
+
+
+def tmnd_mlp_train_step(m, X, S, H, N: int, lr: float, floor: float = 0.0, stream=None) -> float:
+    loss = ctypes.c_double()
+    _check(lib().tmnd_mlp_train_step(m, _ptr(X), _ptr(S), _ptr(H), int(N), float(lr), float(floor),
+                                     ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def tmnd_mlp_predict(m, X, S, N: int, W, stream=None) -> None:
+    _check(lib().tmnd_mlp_predict(m, _ptr(X), _ptr(S), int(N), _ptr(W), _stream(stream)))
+
+
+def tmnd_mlp_features(nodes, target: float, ab_hist, niter: int, sigma0: float) -> np.ndarray:
+    nd = np.ascontiguousarray(nodes, np.float64)
+    out = np.zeros(20, np.float32)
+    hist = None if ab_hist is None else np.ascontiguousarray(ab_hist, np.float64)
+    _check(lib().tmnd_mlp_features(nd.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(target),
+                                   None if hist is None else hist.ctypes.data, int(niter), float(sigma0),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def tmnd_gram(h, xs, stream=None) -> np.ndarray:
+    k = len(xs)
+    arr = (ctypes.c_void_p * k)(*[_ptr(v) for v in xs])
+    G = np.zeros(2 * k * k, np.float64)
+    _check(lib().tmnd_gram(h, arr, k, G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
+    return (G[0::2] + 1j * G[1::2]).reshape(k, k)
+
+
+def tmnd_lincomb(h, w, xs, out, nrhs: int = 1, stream=None) -> None:
+    ww = np.ascontiguousarray(w, np.float64)
+    k = len(xs)
+    arr = (ctypes.c_void_p * k)(*[_ptr(v) for v in xs])
+    _check(lib().tmnd_lincomb(h, ww.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), arr, k, _ptr(out), int(nrhs),
+                              _stream(stream)))
 
 
 def _hp(a):

@@ -68,3 +68,25 @@ extern "C" tmnd_status lagrange_guess(const tmnd_gauge *g, const double *nodes, 
     TMND_CUDA_TRY(cudaGetLastError());
     return TMND_OK;
 }
+
+extern "C" tmnd_status tmnd_lincomb(const tmnd_gauge *g, const double *w, const void *const *xs, int k, void *out,
+                                    int nrhs, void *stream) {
+    TMND_ARG_CHECK(g && w && xs && out, "tmnd_lincomb: NULL argument");
+    TMND_ARG_CHECK(k >= 1 && k <= MAXK && nrhs >= 1, "tmnd_lincomb: k = %d not in [1, %d]", k, MAXK);
+    cudaGetLastError();
+    LinArgs a = {};
+    a.k = k;
+    for (int j = 0; j < k; j++) {
+        TMND_ARG_CHECK(xs[j] && xs[j] != out && isfinite(w[j]), "tmnd_lincomb: bad xs[%d] or weight", j);
+        a.x[j] = (const double2 *)xs[j];
+        a.w[j] = w[j];
+    }
+    const long n = (long)(tmnd_spinor_bytes(g) / sizeof(double2)) * nrhs;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long want = (n + 255) / 256, cap = (long)sms * 8;
+    k_lincomb<<<(unsigned)(want < cap ? want : cap), 256, 0, (cudaStream_t)stream>>>(n, a, (double2 *)out);
+    TMND_CUDA_TRY(cudaGetLastError());
+    return TMND_OK;
+}

@@ -125,7 +125,7 @@ __global__ void k_init_state(MMSState *st, const double *__restrict__ part, int 
 // Scalar step of the recursion (one block; thread 0 does the arithmetic).
 // j = position of this iteration inside its window.
 __global__ void k_scalars(MMSState *st, MMSCoef *cf, const double *__restrict__ part_norm, int nb_hop,
-                          const double *__restrict__ part_rr, MMSConst c, int j) {
+                          const double *__restrict__ part_rr, MMSConst c, int j, double *hist, int hist_cap) {
     __shared__ double red[40];
     const int was_done = st->done;
     double yy = 0, pp = 0, rr_new = 0;
@@ -158,6 +158,10 @@ __global__ void k_scalars(MMSState *st, MMSCoef *cf, const double *__restrict__ 
     cf->skip = 0;
     cf->beta = beta;
     const int it = st->iter + 1;
+    if (hist && it <= hist_cap) {  // scalar history of the base recursion (Lanczos coefficients)
+        hist[2 * (it - 1)] = alpha;
+        hist[2 * (it - 1) + 1] = beta;
+    }
     for (int s = 0; s < c.nshift; s++) {
         if (!st->active[s]) continue;
         const double z = st->zeta[s], zo = st->zeta_old[s];
@@ -436,6 +440,16 @@ tmnd_status run_graph_loop(cudaStream_t s, const int *done_dev, int maxiter, int
             ce = cudaStreamEndCapture(s, &graph);
         }
         if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec[inst], graph, 0);
+        if (ce != cudaSuccess) {
+            // never leave the stream in capture mode, nor the error pending for later calls
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g2 = nullptr;
+                cudaStreamEndCapture(s, &g2);
+                if (g2) cudaGraphDestroy(g2);
+            }
+            cudaGetLastError();
+        }
         if (graph) cudaGraphDestroy(graph);
         if (ce != cudaSuccess) {
             cleanup();
@@ -500,7 +514,7 @@ tmnd_status run_graph_loop(cudaStream_t s, const int *done_dev, int maxiter, int
 // or b at the start).
 static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *x, const double *sigma, int nshift,
                                int nsolve, double rho, int maxiter, int check_every, int profile,
-                               tmnd_solve_info *info, cudaStream_t s, int rhs_index) {
+                               tmnd_solve_info *info, cudaStream_t s, int rhs_index, double *hist, int hist_cap) {
     const size_t sp = tmnd_spinor_bytes(g);
     const long n = (long)(sp / sizeof(double2));
     char *w = (char *)g->work;
@@ -560,7 +574,7 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
         e2.done = &st->done;
         launch_hop_odd_f64(g->geom, g->st, g->links, y, te, nullptr, true, EPI_MMS_R, e2, s);
         mark(1);
-        k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c, j);
+        k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c, j, hist, hist_cap);
         k_pupdate<<<nb_str, UPD_THREADS, 0, s>>>(n, cf, slot[j], p);
         if (j == WIN - 1) k_window<double2><<<nb_str, UPD_THREADS, 0, s>>>(n, cf, ring, ptrs, nshift);
         mark(2);
@@ -668,7 +682,8 @@ static MixedWork mixed_work(void *base, int Vh, int nshift) {
 // m.x32[0..nshift).  Same recursion and kernel sequence as the FP64 solver,
 // with the stencil in FP32/16-bit (dslash_s16.cu).
 static tmnd_status mms_sloppy(tmnd_gauge *g, MixedWork &m, const double *sigma, int nshift, int nsolve, double rho,
-                              int maxiter, int check_every, int profile, cudaStream_t s, MMSState &hs, LoopOut &lo) {
+                              int maxiter, int check_every, int profile, cudaStream_t s, MMSState &hs, LoopOut &lo,
+                              double *hist = nullptr, int hist_cap = 0) {
     const int Vh = g->geom.Vh;
     const long n = 24L * Vh;
     const int nb_hop = hop_blocks_s16(g->geom);
@@ -724,7 +739,7 @@ static tmnd_status mms_sloppy(tmnd_gauge *g, MixedWork &m, const double *sigma, 
         e2.done = &st->done;
         launch_hop_odd_s16(g->geom, g->stf, g->links_s16, y16i, te16i, S16Out{}, true, EPI_MMS_R, e2, s);
         mark(1);
-        k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c, j);
+        k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c, j, hist, hist_cap);
         k_pupdate_s<<<nb_site, 128, 0, s>>>(Vh, cf, m.ring[j], p16);
         if (j == WIN - 1) k_window<float2><<<nb_str, UPD_THREADS, 0, s>>>(n, cf, ring, ptrs, nshift);
         mark(2);
@@ -834,7 +849,8 @@ static tmnd_status defect_correct(tmnd_gauge *g, MixedWork &m, const double2 *b,
 
 static tmnd_status mixed_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *x, const double *sigma,
                                  int nshift, int nsolve, double rho, double rho_inner, int maxiter, int check_every,
-                                 int profile, tmnd_solve_info *info, cudaStream_t s, int rhs_index) {
+                                 int profile, tmnd_solve_info *info, cudaStream_t s, int rhs_index, double *hist,
+                                 int hist_cap) {
     const int Vh = g->geom.Vh;
     const long n = 24L * Vh;
     MixedWork m = mixed_work(g->work, Vh, nshift);
@@ -862,7 +878,7 @@ static tmnd_status mixed_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const
     if (st != TMND_OK) return st;
     MMSState hs;
     LoopOut lo;
-    st = mms_sloppy(g, m, sigma, nshift, nsolve, rho_inner, maxiter, check_every, profile, s, hs, lo);
+    st = mms_sloppy(g, m, sigma, nshift, nsolve, rho_inner, maxiter, check_every, profile, s, hs, lo, hist, hist_cap);
     if (st != TMND_OK) return st;
     for (int i = 0; i < nshift; i++) {
         st = convert_spinor(Vh, xk[i], TMND_F64, m.x32[i], TMND_F32, 1, s);
@@ -950,10 +966,15 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     if (st != TMND_OK) return st;
     if (info) memset(info, 0, sizeof *info);
 
+    // optional scalar history (alpha_k, beta_k) of the base recursion, first RHS
+    double *dhist = nullptr;
+    const int hist_cap = params->ab_hist ? params->ab_hist_len / 2 : 0;
+    if (hist_cap > 0) TMND_CUDA_TRY(cudaMalloc(&dhist, sizeof(double) * 2 * hist_cap));
     // run on a private stream ordered after the caller's stream (capture needs a non-legacy stream)
     cudaStream_t user = (cudaStream_t)stream;
     cudaStream_t s;
     TMND_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    if (dhist) TMND_CUDA_TRY(cudaMemsetAsync(dhist, 0, sizeof(double) * 2 * hist_cap, s));
     cudaEvent_t e0;
     TMND_CUDA_TRY(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
     TMND_CUDA_TRY(cudaEventRecord(e0, user));
@@ -961,11 +982,12 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     tmnd_status res = TMND_OK;
     for (int k = 0; k < nrhs && res == TMND_OK; k++) {
         const double2 *bk = (const double2 *)b + (size_t)k * (sp / sizeof(double2));
+        double *hk = k == 0 ? dhist : nullptr;
         tmnd_status rk =
             mixed ? mixed_one_rhs(g, bk, (double2 *const *)x, sigma, nshift, nsolve, params->rho, rho_inner,
-                                  params->maxiter, check_every, params->profile ? 1 : 0, info, s, k)
+                                  params->maxiter, check_every, params->profile ? 1 : 0, info, s, k, hk, hist_cap)
                   : mms_one_rhs(g, bk, (double2 *const *)x, sigma, nshift, nsolve, params->rho, params->maxiter,
-                                check_every, params->profile ? 1 : 0, info, s, k);
+                                check_every, params->profile ? 1 : 0, info, s, k, hk, hist_cap);
         if (rk != TMND_OK) res = rk;
     }
     cudaEventRecord(e0, s);
@@ -973,6 +995,10 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     cudaStreamSynchronize(s);
     cudaEventDestroy(e0);
     cudaStreamDestroy(s);
+    if (dhist) {
+        cudaMemcpy(params->ab_hist, dhist, sizeof(double) * 2 * hist_cap, cudaMemcpyDeviceToHost);
+        cudaFree(dhist);
+    }
     return res;
 }
 
@@ -1037,7 +1063,18 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
     float2 *rhs = (float2 *)(scr + 3 * sp), *yp = (float2 *)(scr + 3 * sp + f32b);
     float2 *ym = (float2 *)(scr + 3 * sp + 2 * f32b);
     void *gcr = scr + 3 * sp + 4 * f32b;
-    cudaStream_t s = (cudaStream_t)stream;
+    // private stream ordered after the caller's (the defect correction captures graphs,
+    // which the legacy default stream does not allow)
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaStream_t s;
+    cudaEvent_t e0;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(scr);
+        TMND_CUDA_TRY(cudaGetLastError());
+    }
+    cudaEventCreateWithFlags(&e0, cudaEventDisableTiming);
+    cudaEventRecord(e0, user);
+    cudaStreamWaitEvent(s, e0, 0);
     const int nbs = stream_blocks(n);
     MixedWork m = mixed_work(g->work, Vh, 1);
     tmnd_status res_status = TMND_OK;
@@ -1052,7 +1089,12 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
             k_diff_norm<<<nbs, UPD_THREADS, 0, s>>>(n, bk, m.y64, part);
             std::vector<double> h(nbs);
             cudaMemcpyAsync(h.data(), part, sizeof(double) * nbs, cudaMemcpyDeviceToHost, s);
-            TMND_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                tmnd_set_error("tmnd_hybrid_solve: %s", cudaGetErrorString(e));
+                res_status = TMND_ERR_CUDA;
+                break;
+            }
             for (int q = 0; q < nbs; q++) bb += h[q];
         }
         // case-C right-hand side (0, gamma_5 tau_1 b) in FP32 full layout (parity 0 even, 1 odd)
@@ -1066,7 +1108,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
                     const int kk = i < 8 ? i : 8;
                     const void *xs[8];
                     for (int j = 0; j < kk; j++) xs[j] = xk[i - kk + j];
-                    st = lagrange_guess(g, sigma + (i - kk), xs, kk, sigma[i], xk[i], 1, nullptr, stream);
+                    st = lagrange_guess(g, sigma + (i - kk), xs, kk, sigma[i], xk[i], 1, nullptr, s);
                     if (st != TMND_OK) { res_status = st; break; }
                 } else {
                     cudaMemsetAsync(xk[i], 0, sizeof(double2) * n, s);
@@ -1093,8 +1135,8 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
                     k_to_f32_scaled<<<nbs, 256, 0, s>>>(n, 1.0, gb, y + n);
                     int it = 0;
                     double rres = 0;
-                    const double tol = hp->mg_tol > 0 ? hp->mg_tol : 1e-6;
-                    st = mg_gcr_solve(mg, y, rhs, sgn * sq, tol, hp->mg_maxiter > 0 ? hp->mg_maxiter : 200,
+                    const double tol = hp->mg_tol > 0 ? hp->mg_tol : 1e-4;
+                    st = mg_gcr_solve(mg, y, rhs, sgn * sq, tol, hp->mg_maxiter > 0 ? hp->mg_maxiter : 100,
                                       hp->mg_restart > 0 ? hp->mg_restart : 8, hp->mg_nu > 0 ? hp->mg_nu : 4, s, &it,
                                       &rres, gcr);
                     if (st != TMND_OK) { res_status = st; break; }
@@ -1117,7 +1159,15 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
             }
         }
     }
-    cudaStreamSynchronize(s);
+    cudaEventRecord(e0, s);
+    cudaStreamWaitEvent(user, e0, 0);
+    cudaError_t fin = cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaStreamDestroy(s);
     cudaFree(scr);
+    if (res_status == TMND_OK && fin != cudaSuccess) {
+        tmnd_set_error("tmnd_hybrid_solve: %s", cudaGetErrorString(fin));
+        return TMND_ERR_CUDA;
+    }
     return res_status;
 }

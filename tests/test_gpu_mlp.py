@@ -1,0 +1,134 @@
+"""Learned-guess network on the GPU against the FP64 oracle: loss and
+gradient (FP32 network with atomic accumulation, FP64 weights and loss: 1e-5
+relative on the loss, 1e-4 norm-wise on the gradient), BF16 inference (bf16
+layer weights, 8 significand bits: the poles move by a few per cent, so the
+weights agree to 5e-2 relative and rows sum to 1 to FP64 rounding), input
+standardisation, features and Gram matrix against independent numpy formulas,
+and a small training run whose network beats the Lagrange weights (Sec. 4.2.1)
+on held-out solves, by the guess residual and by the iterations of the exact
+solve that finishes each guess."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import EPS, KAPPA, MU, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _rand(N=37, F=20, seed=0):
+    rng = np.random.default_rng(seed)
+    X = (3.0 + 2.0 * rng.standard_normal((N, F))).astype(np.float32)
+    A = rng.standard_normal((N, 8, 8))
+    H = np.einsum("nij,nkj->nik", A, A) + 0.1 * np.eye(8)
+    sig = synth.shift_set(12, 1e-5, 2.0)
+    S = np.array([np.concatenate([[sig[8 + n % 4]], sig[:8]]) for n in range(N)])
+    return X, S, H
+
+
+def test_loss_grad_and_inference_match_oracle():
+    tm = require_gpu()
+    X, S, H = _rand()
+    m = tm.tmnd_mlp_create(20, 7)
+    n = tm.tmnd_mlp_num_params(20)
+    Xd, Sd, Hd = torch.from_numpy(X).cuda(), torch.from_numpy(S).cuda(), torch.from_numpy(H).cuda()
+    tm.tmnd_mlp_fit_inputs(m, Xd, len(X))
+    theta = np.zeros(n, np.float32)
+    tm.tmnd_mlp_params(m, get=theta)
+    assert np.allclose(theta[:20], X.astype(np.float64).mean(0), rtol=1e-5, atol=1e-5)
+    assert np.allclose(theta[20:40], 1 / X.astype(np.float64).std(0), rtol=1e-4)
+    g = np.zeros(n, np.float32)
+    loss = tm.tmnd_mlp_loss_grad(m, Xd, Sd, Hd, len(X), floor=1e-6, grad=g)
+    lref, gref = oracle.mlp_loss_grad(theta.astype(np.float64), X.astype(np.float64), S, H, floor=1e-6)
+    assert abs(loss - lref) <= 1e-5 * abs(lref) + 1e-6
+    assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+    W = torch.empty((len(X), 8), dtype=torch.float64, device="cuda")
+    tm.tmnd_mlp_predict(m, Xd, Sd, len(X), W)
+    w = W.cpu().numpy()
+    wref = oracle.mlp_forward(theta.astype(np.float64), X.astype(np.float64), S)
+    assert np.max(np.abs(w - wref) / (np.abs(wref) + 1e-12 * np.abs(wref).max())) < 5e-2
+    assert np.allclose(w.sum(axis=1), 1.0, atol=1e-12)
+    tm.tmnd_mlp_destroy(m)
+
+
+def test_features_and_gram():
+    tm = require_gpu()
+    nodes = synth.shift_set(12, 1e-5, 2.0)[:8]
+    tgt = 3.0e-5
+    rng = np.random.default_rng(1)
+    alpha = 0.5 + rng.random(30)
+    beta = 0.2 + 0.5 * rng.random(30)
+    hist = np.stack([alpha, beta], 1).ravel()
+    f = tm.tmnd_mlp_features(nodes, tgt, hist, 30, nodes[-1])
+    assert f[0] == pytest.approx(np.log10(tgt), rel=1e-6)
+    assert np.allclose(f[1:9], np.log10(nodes / tgt), rtol=1e-5)
+    assert np.allclose(f[9:17], np.arcsinh(oracle.lagrange_weights(nodes, tgt)), rtol=1e-5, atol=1e-6)
+    # Lanczos tridiagonal of the CG scalars (alpha_k, beta_k)
+    d = 1 / alpha + np.concatenate([[0.0], beta[:-1] / alpha[:-1]])
+    e = np.sqrt(beta[:-1]) / alpha[:-1]
+    ev = np.linalg.eigvalsh(np.diag(d) + np.diag(e, 1) + np.diag(e, -1))
+    assert f[17] == pytest.approx(np.log10(ev[0] - nodes[-1]), rel=1e-4)
+    assert f[18] == pytest.approx(np.log10(ev[-1] - nodes[-1]), rel=1e-4)
+    dims = (4, 4, 4, 4)
+    gauge = tm.Gauge(synth.random_su3_field(dims, 0.3, 1), dims, KAPPA, MU, EPS)
+    vs = synth.gaussian_rhs(dims, 3, nrhs=5)
+    xs = [gauge.pack(torch.from_numpy(v[None]).cuda()) for v in vs]
+    G = tm.tmnd_gram(gauge.handle, xs)
+    Gref = np.array([[np.vdot(a, b2) for b2 in vs] for a in vs])
+    assert np.max(np.abs(G - Gref)) < 1e-12 * np.abs(Gref).max()
+    gauge.close()
+
+
+def test_training_beats_lagrange_on_held_out_solves():
+    """Small run on 4^4 fields (roughness 0.3-0.7): 8-shift multi-shift CG per
+    right-hand side, 4 targets each.  On held-out fields the trained network's
+    mean log guess residual must be below the Lagrange weights' (its gain over
+    the method without it), and the exact solves that finish its guesses take
+    fewer iterations in total."""
+    tm = require_gpu()
+    from paper_1805_09584_gb300 import learned
+    dims = (4, 4, 4, 4)
+    sig = synth.shift_set(12, 1e-5, 2.0)
+
+    def data(seeds, keep=False):
+        Xs, Ss, Hs, kept = [], [], [], []
+        for fs in seeds:
+            r = 0.3 + 0.4 * ((fs * 37) % 100) / 100.0
+            gauge = tm.Gauge(synth.random_su3_field(dims, r, 5000 + fs), dims, KAPPA, MU, EPS)
+            bs = synth.gaussian_rhs(dims, 7000 + 16 * fs, nrhs=4)
+            for k in range(4):
+                bd = gauge.pack(torch.from_numpy(bs[k:k + 1]).cuda())
+                xs, info, hist = learned.solve_nodes(gauge, bd, sig)
+                X, S, H = learned.samples(gauge, bd, sig, xs, info, hist)
+                Xs.append(X)
+                Ss.append(S)
+                Hs.append(H)
+                if keep and k == 0:
+                    kept.append((gauge, bd, xs, len(Xs) - 1))
+            if not (keep and kept and kept[-1][0] is gauge):
+                gauge.close()
+        return np.concatenate(Xs), np.concatenate(Ss), np.concatenate(Hs), kept
+
+    Xtr, Str, Htr, _ = data(range(8))
+    Xte, Ste, Hte, kept = data(range(100, 103), keep=True)
+    m, losses = learned.train(Xtr, Str, Htr, epochs=600, lr=3e-3)
+    assert losses[-1] < losses[0] - 1.0, (losses[0], losses[-1])
+    w_net = learned.predict(m, Xte, Ste)
+    q_net, q_lag = [], []
+    for n in range(len(Xte)):
+        wl = learned.lagrange_weights(Ste[n, 1:], Ste[n, 0])
+        q_lag.append(np.log(wl @ Hte[n] @ wl + 1e-20))
+        q_net.append(np.log(w_net[n] @ Hte[n] @ w_net[n] + 1e-20))
+    assert np.mean(q_net) < np.mean(q_lag) - 1.0, (np.mean(q_net), np.mean(q_lag))
+    # iterations of the exact solve from each guess (first right-hand side of each held-out field)
+    it_net = it_lag = 0
+    for gauge, bd, xs, blk in kept:
+        for t in range(4):
+            n = 4 * blk + t
+            wl = learned.lagrange_weights(Ste[n, 1:], Ste[n, 0])
+            it_lag += learned.iterations_from_guess(gauge, bd, xs, wl, Ste[n, 0])[0]
+            it_net += learned.iterations_from_guess(gauge, bd, xs, w_net[n], Ste[n, 0])[0]
+        gauge.close()
+    assert it_net < it_lag, (it_net, it_lag)
+    tm.tmnd_mlp_destroy(m)
