@@ -9,9 +9,7 @@
 
 namespace {
 
-constexpr float QMAX = 32767.0f;
-
-__device__ __forceinline__ float i2f_exact(int n) { return __int_as_float(n + 0x4B400000) - 12582912.0f; }
+constexpr float QMAX = S16_QMAX;
 
 // one site at a time: read 24 complex numbers as floats
 template <int SRC>
@@ -41,8 +39,8 @@ __device__ __forceinline__ void read_site(const void *src, int Vh, int h, float 
             const int ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                v[4 * j + k][0] = i2f_exact((ws[k] << 16) >> 16) * sc;
-                v[4 * j + k][1] = i2f_exact(ws[k] >> 16) * sc;
+                v[4 * j + k][0] = s16_lo(ws[k]) * sc;
+                v[4 * j + k][1] = s16_hi(ws[k]) * sc;
             }
         }
     }
@@ -60,7 +58,7 @@ __global__ void k_s16_to_f64(int Vh, int nrhs, const char *src, char *dst) {
             const int4 w = s.q[(size_t)j * Vh + h];
             const int ws[4] = {w.x, w.y, w.z, w.w};
             for (int m = 0; m < 4; m++)
-                d[(size_t)(4 * j + m) * Vh + h] = make_double2((double)((ws[m] << 16) >> 16) * sc, (double)(ws[m] >> 16) * sc);
+                d[(size_t)(4 * j + m) * Vh + h] = make_double2((double)s16_int_lo(ws[m]) * sc, (double)s16_int_hi(ws[m]) * sc);
         }
     }
 }
@@ -79,11 +77,7 @@ __global__ void k_to_s16(int Vh, int nrhs, const char *src, size_t src_rhs_bytes
         o.nrm[h] = m / QMAX;
         for (int j = 0; j < 6; j++) {
             int w[4];
-            for (int q = 0; q < 4; q++) {
-                const int re = __float_as_int(fmaf(v[4 * j + q][0], sc, 12582912.0f));
-                const int im = __float_as_int(fmaf(v[4 * j + q][1], sc, 12582912.0f));
-                w[q] = __byte_perm(re, im, 0x5410);
-            }
+            for (int q = 0; q < 4; q++) w[q] = s16_pack_fma(v[4 * j + q][0], v[4 * j + q][1], sc);
             o.q[(size_t)j * Vh + h] = make_int4(w[0], w[1], w[2], w[3]);
         }
     }
@@ -99,7 +93,7 @@ __global__ void k_f32_to_f64(long n, const float2 *src, double2 *dst) {
 }
 
 // links: canonical complex128 [4][T][X][Y][Z][3][3] -> int2 [2 parity][4 mu][3 planes][Vh],
-// rows 0 and 1 rounded to int16 at scale 32767
+// rows 0 and 1 rounded to integers at scale 32767, stored in the 16-bit word codec
 __global__ void k_pack_links_s16(Geom g, const double2 *__restrict__ canon, int2 *__restrict__ out) {
     const long V = 2L * g.Vh;
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;  // over 4 * V links
@@ -116,9 +110,7 @@ __global__ void k_pack_links_s16(Geom g, const double2 *__restrict__ canon, int2
     const double2 *u = canon + i * 9;
     int w[6];
     for (int k = 0; k < 6; k++) {
-        const int re = (int)rint(u[k].x * 32767.0);
-        const int im = (int)rint(u[k].y * 32767.0);
-        w[k] = (int)(((unsigned)re & 0xffffu) | ((unsigned)im << 16));
+        w[k] = s16_word((int)rint(u[k].x * 32767.0), (int)rint(u[k].y * 32767.0));
     }
     int2 *o = out + ((size_t)par * 4 + mu) * 3 * g.Vh;
     o[0 * (size_t)g.Vh + h] = make_int2(w[0], w[1]);

@@ -209,10 +209,37 @@ size_t spinor_bytes_prec(int Vh, int prec);
 tmnd_status convert_spinor(int Vh, void *dst, int dst_prec, const void *src, int src_prec, int nrhs,
                            cudaStream_t s);
 
+// 16-bit word codec shared by every kernel that reads or writes 16-bit data.
+// One 32-bit word holds one complex number: the real part in the low 16 bits,
+// the imaginary part in the high 16 bits, each an integer n in [-32767, 32767]
+// stored biased as n + 32768.  Encoding: fmaf(x, scale, S16_ENC_MAGIC) leaves
+// n + 32768 in the low 16 bits of the float's bits (1.5*2^23 + 32768 + n lies in
+// [2^23, 2^24), where floats are the integers).  Decoding: one byte permute puts
+// the field under the exponent of 2^23, giving the float 2^23 + n + 32768 exactly
+// (S16_DEC_BIAS + n); differences of two such floats are exact integers.
+constexpr float S16_QMAX = 32767.0f;
+constexpr float S16_ENC_MAGIC = 12615680.0f;  // 1.5 * 2^23 + 32768
+constexpr float S16_DEC_BIAS = 8421376.0f;    // 2^23 + 32768
+__device__ __forceinline__ float s16_flo(int w) { return __int_as_float(__byte_perm(w, 0x4B000000, 0x7410)); }
+__device__ __forceinline__ float s16_fhi(int w) { return __int_as_float(__byte_perm(w, 0x4B000000, 0x7432)); }
+__device__ __forceinline__ float s16_lo(int w) { return s16_flo(w) - S16_DEC_BIAS; }
+__device__ __forceinline__ float s16_hi(int w) { return s16_fhi(w) - S16_DEC_BIAS; }
+// pack two values already multiplied by their scale (|x| <= 32767)
+__device__ __forceinline__ int s16_pack(float re_scaled, float im_scaled) {
+    return __byte_perm(__float_as_int(re_scaled + S16_ENC_MAGIC), __float_as_int(im_scaled + S16_ENC_MAGIC), 0x5410);
+}
+__device__ __forceinline__ int s16_pack_fma(float re, float im, float sc) {
+    return __byte_perm(__float_as_int(fmaf(re, sc, S16_ENC_MAGIC)), __float_as_int(fmaf(im, sc, S16_ENC_MAGIC)), 0x5410);
+}
+// integer fields, for exact FP64 decoding
+__host__ __device__ inline int s16_int_lo(int w) { return (int)((unsigned)w & 0xffffu) - 32768; }
+__host__ __device__ inline int s16_int_hi(int w) { return (int)((unsigned)w >> 16) - 32768; }
+__host__ __device__ inline int s16_word(int re, int im) {
+    return (int)(((unsigned)(re + 32768) & 0xffffu) | ((unsigned)(im + 32768) << 16));
+}
+
 // Site-level 16-bit (de)quantisation shared by the sloppy solver kernels.
 // v[c][0/1] = real/imaginary part of component c = flavour*12 + spin*3 + colour.
-__device__ __forceinline__ float s16_i2f(int n) { return __int_as_float(n + 0x4B400000) - 12582912.0f; }
-
 __device__ __forceinline__ void s16_load_site(S16In in, int Vh, int h, float v[24][2]) {
     const float sc = in.nrm[h];
 #pragma unroll
@@ -221,8 +248,8 @@ __device__ __forceinline__ void s16_load_site(S16In in, int Vh, int h, float v[2
         const int ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            v[4 * j + k][0] = s16_i2f((ws[k] << 16) >> 16) * sc;
-            v[4 * j + k][1] = s16_i2f(ws[k] >> 16) * sc;
+            v[4 * j + k][0] = s16_lo(ws[k]) * sc;
+            v[4 * j + k][1] = s16_hi(ws[k]) * sc;
         }
     }
 }
@@ -231,17 +258,13 @@ __device__ __forceinline__ void s16_store_site(S16Out out, int Vh, int h, const 
     float m = 0.0f;
 #pragma unroll
     for (int c = 0; c < 24; c++) m = fmaxf(m, fmaxf(fabsf(v[c][0]), fabsf(v[c][1])));
-    const float sc = m > 0.0f ? 32767.0f / m : 0.0f;
-    out.nrm[h] = m * (1.0f / 32767.0f);
+    const float sc = m > 0.0f ? S16_QMAX / m : 0.0f;
+    out.nrm[h] = m * (1.0f / S16_QMAX);
 #pragma unroll
     for (int j = 0; j < 6; j++) {
         int w[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int re = __float_as_int(fmaf(v[4 * j + k][0], sc, 12582912.0f));
-            const int im = __float_as_int(fmaf(v[4 * j + k][1], sc, 12582912.0f));
-            w[k] = __byte_perm(re, im, 0x5410);
-        }
+        for (int k = 0; k < 4; k++) w[k] = s16_pack_fma(v[4 * j + k][0], v[4 * j + k][1], sc);
         out.q[(size_t)j * Vh + h] = make_int4(w[0], w[1], w[2], w[3]);
     }
 }

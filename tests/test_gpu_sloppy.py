@@ -43,7 +43,11 @@ def test_s16_roundtrip_bound(dims):
     g.close()
 
 
-@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 6, 8), (8, 4, 6, 2), (2, 2, 2, 4)])
+# The two larger lattices are big enough for the stencil's column-march launch
+# shape (blocks walking up t over (x, y, z) columns); (58, 16, 16, 16) also has
+# blocks whose run of time slices continues into the next column.
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 6, 8), (8, 4, 6, 2), (2, 2, 2, 4), (32, 16, 16, 16),
+                                  (58, 16, 16, 16)])
 @pytest.mark.parametrize("op,tol", [("mhat", 1e-4), ("mhat_dag", 1e-4), ("qhat2", 2e-4)])
 def test_s16_apply_matches_oracle(dims, op, tol):
     tm, U, g = _gauge(dims)
