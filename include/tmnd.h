@@ -127,8 +127,11 @@ tmnd_status tmnd_spinor_unpack(const tmnd_gauge *g, void *dev_canonical, const v
 /* out = op(in) for nrhs internal spinors (see tmnd_op).  `sigma` is used by
  * TMND_OP_QHAT2 only.  With TMND_OP_S16 in `op`, in and out are TMND_S16
  * spinors and the operator is the sloppy one (FP32 arithmetic on 16-bit links,
- * intermediates rounded to 16 bits per site).  `out` and `in` must not overlap.  Uses the handle's
- * workspace (one even-site and one odd-site spinor), growing it on first use.
+ * intermediates rounded to 16 bits per site); then 1 <= nrhs <= 16 and every
+ * stencil launch covers all nrhs right-hand sides (the links are read once per
+ * launch and shared through the cache).  `out` and `in` must not overlap.  Uses
+ * the handle's workspace (one even-site and one odd-site spinor per right-hand
+ * side for TMND_OP_S16, one of each otherwise), growing it on first use.
  * (Sec. 2 even-odd Schur complement; Eq. "g5tau1-hermiticity".) */
 tmnd_status tm_nd_apply(tmnd_gauge *g, void *out, const void *in, int op, double sigma,
                         int nrhs, void *stream);
@@ -187,6 +190,9 @@ typedef struct {
     double *ab_hist;       /* optional host array: receives (alpha_k, beta_k), k = 1.., of the base
                               recursion of the first RHS (the Lanczos coefficients), zero-padded */
     int ab_hist_len;       /* length of ab_hist in doubles (2 per iteration) */
+    int batch;             /* TMND_S16: right-hand sides the sloppy solver iterates together, every
+                              16-bit stencil launch covering all of them (0 = min(nrhs, 16);
+                              1 = one at a time); the FP64 defect correction stays per RHS */
 } tmnd_solve_params;
 
 typedef struct {

@@ -70,7 +70,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("maxiter", ctypes.c_int), ("nsolve", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("profile", ctypes.c_int), ("prec", ctypes.c_int),
                 ("rho_inner", ctypes.c_double), ("ab_hist", ctypes.POINTER(ctypes.c_double)),
-                ("ab_hist_len", ctypes.c_int)]
+                ("ab_hist_len", ctypes.c_int), ("batch", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -229,7 +229,7 @@ def tm_nd_apply_noalloc(h, out, inp, op: int, sigma: float = 0.0, nrhs: int = 1,
 
 def mms_cg_solve(h, b, nrhs: int, sigma, x, rho: float = 1e-10, maxiter: int = 100000, nsolve: int = 0,
                  check_every: int = 0, profile: bool = False, prec: int = TMND_F64, rho_inner: float = 0.0,
-                 ab_hist=None, stream=None) -> dict:
+                 ab_hist=None, batch: int = 0, stream=None) -> dict:
     sig = np.ascontiguousarray(sigma, dtype=np.float64)
     ns = len(sig)
     xs = (ctypes.c_void_p * ns)(*[_ptr(v) for v in x])
@@ -239,6 +239,7 @@ def mms_cg_solve(h, b, nrhs: int, sigma, x, rho: float = 1e-10, maxiter: int = 1
         assert ab_hist.dtype == np.float64 and ab_hist.flags["C_CONTIGUOUS"]
         p.ab_hist = ab_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         p.ab_hist_len = int(ab_hist.size)
+    p.batch = int(batch)
     info = SolveInfo()
     st = lib().mms_cg_solve(h, _ptr(b), int(nrhs), sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns, xs,
                             ctypes.byref(p), ctypes.byref(info), _stream(stream))

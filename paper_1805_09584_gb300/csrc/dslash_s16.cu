@@ -51,6 +51,13 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 
+__device__ __forceinline__ S16In s16_at(S16In a, size_t off) {
+    return S16In{(const int4 *)((const char *)a.q + off), (const float *)((const char *)a.nrm + off)};
+}
+__device__ __forceinline__ S16Out s16_at(S16Out a, size_t off) {
+    return S16Out{(int4 *)((char *)a.q + off), (float *)((char *)a.nrm + off)};
+}
+
 // the words one direction needs: neighbour spinor (both flavours), link, scale
 struct Raw {
     int4 q[2][3];
@@ -318,46 +325,63 @@ __device__ __forceinline__ void load_site(const int4 *__restrict__ q, const floa
 template <bool DAG, bool PF>
 __global__ void __launch_bounds__(S16_THREADS, S16_MINB) k_hop_even_s16(Geom g, SiteTermF st, const int2 *__restrict__ links,
                                                              S16In in, S16Out out, const int *__restrict__ done,
-                                                             int chunk) {
+                                                             int chunk, S16Batch bt) {
     if (done && *done) return;
     const int h_end = min(g.Vh, (int)(blockIdx.x + 1) * chunk);
     for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) {
-        f2 acc[4][3][2];
-        hop_all<0, DAG, PF>(g, links, in.q, in.nrm, h, acc);
-        // kappa^2 A^-1 per spin sign g: [[a - i kp g, kpp], [kpp, a + i kp g]] / det
-        const float a = st.kappa2 * st.inv_det;
-        const float e = a * st.kpp;
-        f2 o[4][3][2];
+        for (int k = 0; k < bt.nrhs; k++) {
+            if (bt.rdone && bt.rdone[k * bt.rdone_stride]) continue;
+            const S16In ik = s16_at(in, k * bt.stride);
+            f2 acc[4][3][2];
+            hop_all<0, DAG, PF>(g, links, ik.q, ik.nrm, h, acc);
+            // kappa^2 A^-1 per spin sign g: [[a - i kp g, kpp], [kpp, a + i kp g]] / det
+            const float a = st.kappa2 * st.inv_det;
+            const float e = a * st.kpp;
+            f2 o[4][3][2];
 #pragma unroll
-        for (int s = 0; s < 4; s++) {
-            const float b = a * (DAG ? -st.kp : st.kp) * (s < 2 ? 1.0f : -1.0f);
+            for (int s = 0; s < 4; s++) {
+                const float b = a * (DAG ? -st.kp : st.kp) * (s < 2 ? 1.0f : -1.0f);
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const f2 pr = acc[s][c][0], pi = acc[s][c][1];
-                o[s][c][0] = make_float2(fmaf(a, pr.x, fmaf(b, pi.x, e * pr.y)), fmaf(a, pr.y, fmaf(-b, pi.y, e * pr.x)));
-                o[s][c][1] = make_float2(fmaf(a, pi.x, fmaf(-b, pr.x, e * pi.y)), fmaf(a, pi.y, fmaf(b, pr.y, e * pi.x)));
+                for (int c = 0; c < 3; c++) {
+                    const f2 pr = acc[s][c][0], pi = acc[s][c][1];
+                    o[s][c][0] = make_float2(fmaf(a, pr.x, fmaf(b, pi.x, e * pr.y)), fmaf(a, pr.y, fmaf(-b, pi.y, e * pr.x)));
+                    o[s][c][1] = make_float2(fmaf(a, pi.x, fmaf(-b, pr.x, e * pi.y)), fmaf(a, pi.y, fmaf(b, pr.y, e * pi.x)));
+                }
             }
+            const S16Out ok = s16_at(out, k * bt.stride);
+            store_site(ok.q, ok.nrm, g.Vh, h, o);
         }
-        store_site(out.q, out.nrm, g.Vh, h, o);
     }
 }
 
+// Per-right-hand-side block partials: each thread keeps its running sums in its own
+// slots of dynamic shared memory, part[(q * nrhs + k) * blockDim + tid], q = 0, 1.
 template <bool DAG, int EPI, bool PF>
 __global__ void __launch_bounds__(S16_THREADS, S16_MINB) k_hop_odd_s16(Geom g, SiteTermF st, const int2 *__restrict__ links,
-                                                            S16In psi, S16In te, S16Out out, S16EpiArgs ea,
-                                                            int chunk) {
+                                                            S16In psi_all, S16In te_all, S16Out out_all, S16EpiArgs ea,
+                                                            int chunk, S16Batch bt) {
     __shared__ double red[40];
+    __shared__ float alpha_s[TMND_MAX_BATCH];
+    extern __shared__ double part[];
     if (ea.done && *ea.done) return;
     const int Vh = g.Vh;
-    float alpha = 0.0f;
+    constexpr bool SUMS = EPI == EPI_STORE_NORMS || EPI == EPI_MMS_R;
     if (EPI == EPI_MMS_R) {
-        const double yy = block_reduce_partials(ea.part_in, ea.npart_in, red);
-        const double pp = block_reduce_partials(ea.part_in + ea.npart_in, ea.npart_in, red);
-        alpha = (float)(*ea.rr / (yy + ea.sigma * pp));
+        for (int k = 0; k < bt.nrhs; k++) {
+            const double yy = block_reduce_partials(ea.part_in + (size_t)(2 * k) * ea.npart_in, ea.npart_in, red);
+            const double pp = block_reduce_partials(ea.part_in + (size_t)(2 * k + 1) * ea.npart_in, ea.npart_in, red);
+            if (threadIdx.x == 0) alpha_s[k] = (float)(ea.rr[(size_t)k * ea.rr_stride] / (yy + ea.sigma * pp));
+        }
     }
-    double n1 = 0.0, n2 = 0.0;
+    if (SUMS)
+        for (int k = 0; k < 2 * bt.nrhs; k++) part[k * blockDim.x + threadIdx.x] = 0.0;
+    __syncthreads();
     const int h_end = min(Vh, (int)(blockIdx.x + 1) * chunk);
-    for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) {
+    for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x)
+      for (int k = 0; k < bt.nrhs; k++) {
+        if (bt.rdone && bt.rdone[k * bt.rdone_stride]) continue;
+        const S16In te = s16_at(te_all, k * bt.stride), psi = s16_at(psi_all, k * bt.stride);
+        const S16Out out = s16_at(out_all, k * bt.stride);
         f2 acc[4][3][2];
         hop_all<1, false, PF>(g, links, te.q, te.nrm, h, acc);
         f2 p[4][3][2];
@@ -389,57 +413,62 @@ __global__ void __launch_bounds__(S16_THREADS, S16_MINB) k_hop_odd_s16(Geom g, S
         }
         if (EPI == EPI_STORE || EPI == EPI_STORE_NORMS) {
             store_site(out.q, out.nrm, Vh, h, y);
-            n1 += s1;
-            n2 += s2;
+            if (EPI == EPI_STORE_NORMS) {
+                part[k * blockDim.x + threadIdx.x] += s1;
+                part[(bt.nrhs + k) * blockDim.x + threadIdx.x] += s2;
+            }
         } else if (EPI == EPI_SHIFT) {  // y + sigma aux, aux streamed plane by plane
-            const float sa = (float)ea.sigma * __ldg(&ea.aux.nrm[h]);
+            const S16In aux = s16_at(ea.aux, k * bt.stride);
+            const float sa = (float)ea.sigma * __ldg(&aux.nrm[h]);
             const f2 sa2 = dup(sa), nb2 = dup(-S16_DEC_BIAS);
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-                const int4 a0 = __ldg(&ea.aux.q[(0 * 3 + j) * Vh + h]), a1 = __ldg(&ea.aux.q[(1 * 3 + j) * Vh + h]);
+                const int4 a0 = __ldg(&aux.q[(0 * 3 + j) * Vh + h]), a1 = __ldg(&aux.q[(1 * 3 + j) * Vh + h]);
 #pragma unroll
                 for (int m = 0; m < 4; m++) {
-                    const int k = 4 * j + m, w0 = word(a0, m), w1 = word(a1, m);
+                    const int kk = 4 * j + m, w0 = word(a0, m), w1 = word(a1, m);
                     const f2 ar = add2(make_float2(s16_flo(w0), s16_flo(w1)), nb2);
                     const f2 ai = add2(make_float2(s16_fhi(w0), s16_fhi(w1)), nb2);
-                    y[k / 3][k % 3][0] = fma2(sa2, ar, y[k / 3][k % 3][0]);
-                    y[k / 3][k % 3][1] = fma2(sa2, ai, y[k / 3][k % 3][1]);
+                    y[kk / 3][kk % 3][0] = fma2(sa2, ar, y[kk / 3][kk % 3][0]);
+                    y[kk / 3][kk % 3][1] = fma2(sa2, ai, y[kk / 3][kk % 3][1]);
                 }
             }
             store_site(out.q, out.nrm, Vh, h, y);
         } else {  // EPI_MMS_R: w = y + sigma aux; r' = r - alpha w (FP32 planes); aux streamed
-            const float sa = (float)ea.sigma * __ldg(&ea.aux.nrm[h]);
+            const S16In aux = s16_at(ea.aux, k * bt.stride);
+            const float sa = (float)ea.sigma * __ldg(&aux.nrm[h]);
+            const float alpha = alpha_s[k];
+            const float2 *rin = ea.r_in + k * ea.r_stride;
+            float2 *rout = ea.r + k * ea.r_stride;
 #pragma unroll
             for (int f = 0; f < 2; f++)
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
-                    const int4 aw = __ldg(&ea.aux.q[(f * 3 + j) * Vh + h]);
+                    const int4 aw = __ldg(&aux.q[(f * 3 + j) * Vh + h]);
 #pragma unroll
                     for (int m = 0; m < 4; m++) {
-                        const int k = 4 * j + m, s = k / 3, c = k % 3;
-                        const int i = (f * 12 + k) * Vh + h;
-                        const float2 rv = ea.r_in[i];
+                        const int kk = 4 * j + m, s = kk / 3, c = kk % 3;
+                        const int i = (f * 12 + kk) * Vh + h;
+                        const float2 rv = rin[i];
                         const float yr = f ? y[s][c][0].y : y[s][c][0].x, yi = f ? y[s][c][1].y : y[s][c][1].x;
                         const float wx = fmaf(sa, s16_lo(word(aw, m)), yr);
                         const float wy = fmaf(sa, s16_hi(word(aw, m)), yi);
                         const float2 rn = make_float2(fmaf(-alpha, wx, rv.x), fmaf(-alpha, wy, rv.y));
-                        ea.r[i] = rn;
+                        rout[i] = rn;
                         s1 = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, s1));
                     }
                 }
-            n1 += s1;
+            part[k * blockDim.x + threadIdx.x] += s1;
         }
-    }
-    if (EPI == EPI_STORE_NORMS) {
-        double t1 = block_sum(n1, red);
-        double t2 = block_sum(n2, red);
-        if (threadIdx.x == 0) {
-            ea.part_out[blockIdx.x] = t1;
-            ea.part_out[gridDim.x + blockIdx.x] = t2;
-        }
-    } else if (EPI == EPI_MMS_R) {
-        double t1 = block_sum(n1, red);
-        if (threadIdx.x == 0) ea.part_out[blockIdx.x] = t1;
+      }
+    if (SUMS) {
+        const int nq = EPI == EPI_STORE_NORMS ? 2 : 1;
+        for (int q = 0; q < nq; q++)
+            for (int k = 0; k < bt.nrhs; k++) {
+                const double t = block_sum(part[(q * bt.nrhs + k) * blockDim.x + threadIdx.x], red);
+                if (threadIdx.x == 0) ea.part_out[(size_t)(nq * k + q) * gridDim.x + blockIdx.x] = t;
+                __syncthreads();
+            }
     }
 }
 
@@ -469,20 +498,22 @@ int hop_blocks_s16(const Geom &g) {
 }
 
 void launch_hop_even_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In in, S16Out out, bool dag,
-                         const int *done, cudaStream_t s) {
+                         const int *done, cudaStream_t s, const S16Batch &bt) {
     const int nb = hop_blocks_s16(g);
     const int chunk = (g.Vh + nb - 1) / nb;
     if (dag)
-        k_hop_even_s16<true, PFD><<<nb, S16_THREADS, 0, s>>>(g, st, links, in, out, done, chunk);
+        k_hop_even_s16<true, PFD><<<nb, S16_THREADS, 0, s>>>(g, st, links, in, out, done, chunk, bt);
     else
-        k_hop_even_s16<false, PFD><<<nb, S16_THREADS, 0, s>>>(g, st, links, in, out, done, chunk);
+        k_hop_even_s16<false, PFD><<<nb, S16_THREADS, 0, s>>>(g, st, links, in, out, done, chunk, bt);
 }
 
 void launch_hop_odd_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In psi, S16In te, S16Out out,
-                        bool dag, HopEpi epi, const S16EpiArgs &ea, cudaStream_t s) {
+                        bool dag, HopEpi epi, const S16EpiArgs &ea, cudaStream_t s, const S16Batch &bt) {
     const int nb = hop_blocks_s16(g);
     const int chunk = (g.Vh + nb - 1) / nb;
-#define TMND_ODD16(D, E) k_hop_odd_s16<D, E, PFD><<<nb, S16_THREADS, 0, s>>>(g, st, links, psi, te, out, ea, chunk)
+    const size_t smem = sizeof(double) * 2 * bt.nrhs * S16_THREADS;
+#define TMND_ODD16(D, E) \
+    k_hop_odd_s16<D, E, PFD><<<nb, S16_THREADS, smem, s>>>(g, st, links, psi, te, out, ea, chunk, bt)
     if (!dag) {
         switch (epi) {
             case EPI_STORE: TMND_ODD16(false, EPI_STORE); break;

@@ -246,42 +246,44 @@ static void apply_mhat(const tmnd_gauge *g, const double2 *in, double2 *out, dou
     launch_hop_odd_f64(g->geom, g->st, g->links, in, te, out, dag, epi, ea, s);
 }
 
-// Sloppy operator on TMND_S16 spinors.
+// Sloppy operator on TMND_S16 spinors: all right-hand sides in each stencil launch.
 static tmnd_status apply_s16(tmnd_gauge *g, void *out, const void *in, int op, double sigma, int nrhs,
                              cudaStream_t s) {
     const int Vh = g->geom.Vh;
     const size_t sb = spinor_bytes_prec(Vh, TMND_S16);
-    tmnd_status st = tmnd_ensure_workspace(g, 2 * sb);
+    tmnd_status st = tmnd_ensure_workspace(g, 2 * (size_t)nrhs * sb);
     if (st != TMND_OK) return st;
     S16Out te = s16_out(g->work, Vh);
-    S16Out yo = s16_out((char *)g->work + sb, Vh);
+    S16Out yo = s16_out((char *)g->work + (size_t)nrhs * sb, Vh);
     S16In te_in{te.q, te.nrm}, yo_in{yo.q, yo.nrm};
     S16EpiArgs ea = {};
-    for (int k = 0; k < nrhs; k++) {
-        S16In ik = s16_in((const char *)in + k * sb, Vh);
-        S16Out ok = s16_out((char *)out + k * sb, Vh);
-        switch (op) {
-            case TMND_OP_MHAT:
-            case TMND_OP_MHAT_DAG: {
-                const bool dag = op == TMND_OP_MHAT_DAG;
-                launch_hop_even_s16(g->geom, g->stf, g->links_s16, ik, te, dag, nullptr, s);
-                launch_hop_odd_s16(g->geom, g->stf, g->links_s16, ik, te_in, ok, dag, EPI_STORE, ea, s);
-                break;
-            }
-            case TMND_OP_QHAT2: {
-                launch_hop_even_s16(g->geom, g->stf, g->links_s16, ik, te, false, nullptr, s);
-                launch_hop_odd_s16(g->geom, g->stf, g->links_s16, ik, te_in, yo, false, EPI_STORE, ea, s);
-                S16EpiArgs e2 = {};
-                e2.sigma = sigma;
-                e2.aux = ik;
-                launch_hop_even_s16(g->geom, g->stf, g->links_s16, yo_in, te, true, nullptr, s);
-                launch_hop_odd_s16(g->geom, g->stf, g->links_s16, yo_in, te_in, ok, true, EPI_SHIFT, e2, s);
-                break;
-            }
-            default:
-                tmnd_set_error("tm_nd_apply: op %d not available for TMND_S16 spinors", op);
-                return TMND_ERR_ARG;
+    // the even temporaries of all right-hand sides sit sb apart, like the vectors
+    S16Batch bt;
+    bt.nrhs = nrhs;
+    bt.stride = sb;
+    const S16In ik = s16_in(in, Vh);
+    const S16Out ok = s16_out(out, Vh);
+    switch (op) {
+        case TMND_OP_MHAT:
+        case TMND_OP_MHAT_DAG: {
+            const bool dag = op == TMND_OP_MHAT_DAG;
+            launch_hop_even_s16(g->geom, g->stf, g->links_s16, ik, te, dag, nullptr, s, bt);
+            launch_hop_odd_s16(g->geom, g->stf, g->links_s16, ik, te_in, ok, dag, EPI_STORE, ea, s, bt);
+            break;
         }
+        case TMND_OP_QHAT2: {
+            launch_hop_even_s16(g->geom, g->stf, g->links_s16, ik, te, false, nullptr, s, bt);
+            launch_hop_odd_s16(g->geom, g->stf, g->links_s16, ik, te_in, yo, false, EPI_STORE, ea, s, bt);
+            S16EpiArgs e2 = {};
+            e2.sigma = sigma;
+            e2.aux = ik;
+            launch_hop_even_s16(g->geom, g->stf, g->links_s16, yo_in, te, true, nullptr, s, bt);
+            launch_hop_odd_s16(g->geom, g->stf, g->links_s16, yo_in, te_in, ok, true, EPI_SHIFT, e2, s, bt);
+            break;
+        }
+        default:
+            tmnd_set_error("tm_nd_apply: op %d not available for TMND_S16 spinors", op);
+            return TMND_ERR_ARG;
     }
     TMND_CUDA_TRY(cudaGetLastError());
     return TMND_OK;
@@ -291,9 +293,9 @@ extern "C" tmnd_status tm_nd_apply(tmnd_gauge *g, void *out, const void *in, int
                                    void *stream) {
     TMND_ARG_CHECK(g && out && in, "tm_nd_apply: NULL argument");
     if (op & TMND_OP_S16) {
-        TMND_ARG_CHECK(nrhs >= 1 && out != in && ((uintptr_t)out & 15) == 0 && ((uintptr_t)in & 15) == 0 &&
-                           isfinite(sigma),
-                       "tm_nd_apply: bad arguments");
+        TMND_ARG_CHECK(nrhs >= 1 && nrhs <= TMND_MAX_BATCH && out != in && ((uintptr_t)out & 15) == 0 &&
+                           ((uintptr_t)in & 15) == 0 && isfinite(sigma),
+                       "tm_nd_apply: bad arguments (16-bit spinors: 1 <= nrhs <= %d)", TMND_MAX_BATCH);
         cudaGetLastError();
         return apply_s16(g, out, in, op & ~TMND_OP_S16, sigma, nrhs, (cudaStream_t)stream);
     }

@@ -102,8 +102,8 @@ __global__ void k_init(long n, const double2 *__restrict__ b, double2 *__restric
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-__global__ void k_init_state(MMSState *st, const double *__restrict__ part, int npart, MMSConst c) {
-    __shared__ double red[40];
+__device__ void init_state(MMSState *st, const double *__restrict__ part, int npart, const MMSConst &c,
+                           double *red) {
     double bb = block_reduce_partials(part, npart, red);
     if (threadIdx.x != 0) return;
     st->rr = bb;
@@ -122,11 +122,23 @@ __global__ void k_init_state(MMSState *st, const double *__restrict__ part, int 
     if (!isfinite(bb)) st->done = 1;
 }
 
+__global__ void k_init_state(MMSState *st, const double *__restrict__ part, int npart, MMSConst c) {
+    __shared__ double red[40];
+    init_state(st, part, npart, c, red);
+}
+
+// batched: block k initialises right-hand side k from partials [k][npart]
+__global__ void k_init_state_b(MMSState *st, size_t st_stride, const double *__restrict__ part, int npart,
+                               MMSConst c) {
+    __shared__ double red[40];
+    init_state((MMSState *)((char *)st + blockIdx.x * st_stride), part + (size_t)blockIdx.x * npart, npart, c, red);
+}
+
 // Scalar step of the recursion (one block; thread 0 does the arithmetic).
 // j = position of this iteration inside its window.
-__global__ void k_scalars(MMSState *st, MMSCoef *cf, const double *__restrict__ part_norm, int nb_hop,
-                          const double *__restrict__ part_rr, MMSConst c, int j, double *hist, int hist_cap) {
-    __shared__ double red[40];
+__device__ void scalars_step(MMSState *st, MMSCoef *cf, const double *__restrict__ part_norm, int nb_hop,
+                             const double *__restrict__ part_rr, const MMSConst &c, int j, double *hist, int hist_cap,
+                             double *red) {
     const int was_done = st->done;
     double yy = 0, pp = 0, rr_new = 0;
     if (!was_done) {
@@ -190,6 +202,32 @@ __global__ void k_scalars(MMSState *st, MMSCoef *cf, const double *__restrict__ 
     st->beta_old = beta;
     st->iter = it;
     if (!st->active[c.nsolve - 1] || it >= c.maxiter) st->done = 1;
+}
+
+__global__ void k_scalars(MMSState *st, MMSCoef *cf, const double *__restrict__ part_norm, int nb_hop,
+                          const double *__restrict__ part_rr, MMSConst c, int j, double *hist, int hist_cap) {
+    __shared__ double red[40];
+    scalars_step(st, cf, part_norm, nb_hop, part_rr, c, j, hist, hist_cap, red);
+}
+
+// Batched: block k runs the scalar step of right-hand side k (state and
+// coefficients stride apart; partials [k][2][nb_hop] and [k][nb_hop]); the
+// scalar history is kept for k = 0.
+__global__ void k_scalars_b(MMSState *st, MMSCoef *cf, size_t st_stride, size_t cf_stride,
+                            const double *__restrict__ part_norm, int nb_hop, const double *__restrict__ part_rr,
+                            MMSConst c, int j, double *hist, int hist_cap) {
+    __shared__ double red[40];
+    const int k = blockIdx.x;
+    scalars_step((MMSState *)((char *)st + k * st_stride), (MMSCoef *)((char *)cf + k * cf_stride),
+                 part_norm + (size_t)2 * k * nb_hop, nb_hop, part_rr + (size_t)k * nb_hop, c, j,
+                 k == 0 ? hist : nullptr, hist_cap, red);
+}
+
+// done_all = every right-hand side's solve is done
+__global__ void k_all_done(const MMSState *st, size_t st_stride, int nrhs, int *done_all) {
+    int d = 1;
+    for (int k = 0; k < nrhs; k++) d &= ((const MMSState *)((const char *)st + k * st_stride))->done;
+    *done_all = d;
 }
 
 // p = r' + beta p (base search direction, every iteration)
@@ -283,48 +321,118 @@ __global__ void k_diff_norm(long n, const double2 *__restrict__ b, const double2
 
 
 // ------------------------------------------------------------ sloppy path
-// One site per thread: r = b, p = quantise(b), p_i = b, x_i = 0, partial |b|^2.
-__global__ void k_init_s(int Vh, const float2 *__restrict__ b, float2 *__restrict__ r, S16Out p,
-                         ShiftPtrsT<float2> sp, int nshift, double *__restrict__ part) {
+// Sloppy vectors of R right-hand sides (right-hand side k's block follows k-1's):
+//   ring slot l of k: ring0 + (k WIN + l) n;  b of k: b0 + k n;
+//   p_s, x_s of k: p0/x0 + (k nshift + s) n;  16-bit p of k: p16 + k sb.
+struct SloppyVecs {
+    float2 *ring0, *b0, *p0, *x0;
+    S16Out p16;
+    long n;
+    size_t sb;
+    int nshift;
+};
+
+// One site per thread, right-hand side blockIdx.y: r = b (last ring slot),
+// p = quantise(b), p_i = b, x_i = 0, partial |b|^2 into part[k][gridDim.x].
+__global__ void k_init_s(int Vh, SloppyVecs v, double *__restrict__ part) {
     __shared__ double red[40];
+    const int k = blockIdx.y;
+    const float2 *b = v.b0 + k * v.n;
+    float2 *r = v.ring0 + ((size_t)k * WIN + WIN - 1) * v.n;
+    const S16Out p{(int4 *)((char *)v.p16.q + k * v.sb), (float *)((char *)v.p16.nrm + k * v.sb)};
     double acc = 0.0;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
-        float v[24][2];
+        float w[24][2];
         float a = 0.0f;
 #pragma unroll
         for (int c = 0; c < 24; c++) {
             const float2 bv = b[(size_t)c * Vh + h];
-            v[c][0] = bv.x;
-            v[c][1] = bv.y;
+            w[c][0] = bv.x;
+            w[c][1] = bv.y;
             r[(size_t)c * Vh + h] = bv;
             a = fmaf(bv.x, bv.x, fmaf(bv.y, bv.y, a));
-            for (int s = 0; s < nshift; s++) {
-                sp.p[s][(size_t)c * Vh + h] = bv;
-                sp.x[s][(size_t)c * Vh + h] = make_float2(0.f, 0.f);
+            for (int s = 0; s < v.nshift; s++) {
+                v.p0[((size_t)k * v.nshift + s) * v.n + (size_t)c * Vh + h] = bv;
+                v.x0[((size_t)k * v.nshift + s) * v.n + (size_t)c * Vh + h] = make_float2(0.f, 0.f);
             }
         }
-        s16_store_site(p, Vh, h, v);
+        s16_store_site(p, Vh, h, w);
         acc += a;
     }
     double t = block_sum(acc, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = t;
 }
 
-// p = r' + beta p, p stored in 16 bits (in place, one site per thread)
-__global__ void k_pupdate_s(int Vh, const MMSCoef *__restrict__ cf, const float2 *__restrict__ r, S16Out p) {
+// p = r' + beta p for right-hand side blockIdx.y (slot j of its ring), p stored in 16 bits
+__global__ void k_pupdate_s(int Vh, const MMSCoef *__restrict__ cf0, size_t cf_stride, SloppyVecs v, int j) {
+    const int k = blockIdx.y;
+    const MMSCoef *cf = (const MMSCoef *)((const char *)cf0 + k * cf_stride);
     if (cf->skip) return;
     const float beta = (float)cf->beta;
+    const float2 *r = v.ring0 + ((size_t)k * WIN + j) * v.n;
+    const S16Out p{(int4 *)((char *)v.p16.q + k * v.sb), (float *)((char *)v.p16.nrm + k * v.sb)};
     const S16In pin{p.q, p.nrm};
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
-        float v[24][2];
-        s16_load_site(pin, Vh, h, v);
+        float w[24][2];
+        s16_load_site(pin, Vh, h, w);
 #pragma unroll
         for (int c = 0; c < 24; c++) {
             const float2 rv = r[(size_t)c * Vh + h];
-            v[c][0] = fmaf(beta, v[c][0], rv.x);
-            v[c][1] = fmaf(beta, v[c][1], rv.y);
+            w[c][0] = fmaf(beta, w[c][0], rv.x);
+            w[c][1] = fmaf(beta, w[c][1], rv.y);
         }
-        s16_store_site(p, Vh, h, v);
+        s16_store_site(p, Vh, h, w);
+    }
+}
+
+// Windowed multi-shift update of right-hand side blockIdx.y (see k_window), FP32.
+__global__ void __launch_bounds__(UPD_THREADS) k_window_s(const MMSCoef *__restrict__ cf0, size_t cf_stride,
+                                                          SloppyVecs v) {
+    __shared__ float s_P[NS], s_a[NS], s_Q[NS][WIN], s_e[NS][WIN];
+    __shared__ int s_idx[NS];
+    __shared__ int s_n;
+    const int k = blockIdx.y;
+    const MMSCoef *cf = (const MMSCoef *)((const char *)cf0 + k * cf_stride);
+    if (threadIdx.x == 0) {
+        int m = 0;
+        for (int s = 0; s < v.nshift; s++)
+            if (cf->touched[s]) {
+                s_idx[m] = s;
+                s_P[m] = (float)cf->P[s];
+                s_a[m] = (float)cf->a[s];
+                for (int l = 0; l < WIN; l++) {
+                    s_Q[m][l] = (float)cf->Q[s][l];
+                    s_e[m][l] = (float)cf->e[s][l];
+                }
+                m++;
+            }
+        s_n = m;
+    }
+    __syncthreads();
+    const int m = s_n;
+    if (m == 0) return;
+    const float2 *ring = v.ring0 + (size_t)k * WIN * v.n;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < v.n; i += (long)gridDim.x * blockDim.x) {
+        float2 rv[WIN];
+#pragma unroll
+        for (int l = 0; l < WIN; l++) rv[l] = ring[l * v.n + i];
+        for (int q = 0; q < m; q++) {
+            const size_t off = ((size_t)k * v.nshift + s_idx[q]) * v.n + i;
+            const float2 pi = v.p0[off];
+            float2 xv = v.x0[off];
+            float2 pn = make_float2(s_P[q] * pi.x, s_P[q] * pi.y);
+            xv.x = fmaf(s_a[q], pi.x, xv.x);
+            xv.y = fmaf(s_a[q], pi.y, xv.y);
+#pragma unroll
+            for (int l = 0; l < WIN; l++) {
+                xv.x = fmaf(s_e[q][l], rv[l].x, xv.x);
+                xv.y = fmaf(s_e[q][l], rv[l].y, xv.y);
+                pn.x = fmaf(s_Q[q][l], rv[l].x, pn.x);
+                pn.y = fmaf(s_Q[q][l], rv[l].y, pn.y);
+            }
+            v.x0[off] = xv;
+            v.p0[off] = pn;
+        }
     }
 }
 
@@ -645,22 +753,32 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
 
 
 // ---------------------------------------------------------- mixed precision
-// Workspace of the mixed solve (one right-hand side at a time).
+// Workspace of the mixed solve: FP64 vectors for one right-hand side at a time
+// (defect correction), sloppy vectors for nrhs right-hand sides at once.
 struct MixedWork {
     double2 *r64, *y64, *te64;          // FP64: defect, (Qhat^2+sigma) x, even temporary
-    float2 *ring[WIN];                  // FP32 residual slots of the sloppy MMS-CG
-    float2 *b32;                        // FP32 right-hand side of the sloppy solve
-    float2 *p32[NS], *x32[NS];          // FP32 shifted directions and sloppy solutions
-    void *p16, *y16, *te16;             // 16-bit stencil vectors
+    SloppyVecs v;                       // FP32 ring, b, p_i, x_i and the 16-bit p (nrhs blocks)
+    void *y16, *te16;                   // 16-bit stencil temporaries, nrhs blocks of v.sb
+    int nrhs;
+    float2 *ring(int k, int l) const { return v.ring0 + ((size_t)k * WIN + l) * v.n; }
+    float2 *b32(int k) const { return v.b0 + (size_t)k * v.n; }
+    float2 *x32(int k, int s) const { return v.x0 + ((size_t)k * v.nshift + s) * v.n; }
+    // a view for one right-hand side and one shift on the same memory (right-hand side 0's slots)
+    MixedWork single() const {
+        MixedWork w = *this;
+        w.v.nshift = 1;
+        w.nrhs = 1;
+        return w;
+    }
 };
 
-static size_t mixed_work_bytes(int Vh, int nshift) {
+static size_t mixed_work_bytes(int Vh, int nshift, int nrhs = 1) {
     const size_t s64 = spinor_bytes_prec(Vh, TMND_F64), s32 = spinor_bytes_prec(Vh, TMND_F32),
                  s16 = spinor_bytes_prec(Vh, TMND_S16);
-    return 3 * s64 + (WIN + 1 + 2 * (size_t)nshift) * s32 + 3 * s16;
+    return 3 * s64 + (size_t)nrhs * ((WIN + 1 + 2 * (size_t)nshift) * s32 + 3 * s16);
 }
 
-static MixedWork mixed_work(void *base, int Vh, int nshift) {
+static MixedWork mixed_work(void *base, int Vh, int nshift, int nrhs = 1) {
     const size_t s64 = spinor_bytes_prec(Vh, TMND_F64), s32 = spinor_bytes_prec(Vh, TMND_F32),
                  s16 = spinor_bytes_prec(Vh, TMND_S16);
     char *w = (char *)base;
@@ -668,34 +786,45 @@ static MixedWork mixed_work(void *base, int Vh, int nshift) {
     m.r64 = (double2 *)w; w += s64;
     m.y64 = (double2 *)w; w += s64;
     m.te64 = (double2 *)w; w += s64;
-    for (int l = 0; l < WIN; l++) { m.ring[l] = (float2 *)w; w += s32; }
-    m.b32 = (float2 *)w; w += s32;
-    for (int i = 0; i < nshift; i++) { m.p32[i] = (float2 *)w; w += s32; }
-    for (int i = 0; i < nshift; i++) { m.x32[i] = (float2 *)w; w += s32; }
-    m.p16 = w; w += s16;
-    m.y16 = w; w += s16;
+    m.v.n = 24L * Vh;
+    m.v.sb = s16;
+    m.v.nshift = nshift;
+    m.nrhs = nrhs;
+    m.v.ring0 = (float2 *)w; w += (size_t)nrhs * WIN * s32;
+    m.v.b0 = (float2 *)w; w += (size_t)nrhs * s32;
+    m.v.p0 = (float2 *)w; w += (size_t)nrhs * nshift * s32;
+    m.v.x0 = (float2 *)w; w += (size_t)nrhs * nshift * s32;
+    m.v.p16 = s16_out(w, Vh); w += (size_t)nrhs * s16;
+    m.y16 = w; w += (size_t)nrhs * s16;
     m.te16 = w;
     return m;
 }
 
-// Sloppy multi-shift CG on m.b32 for shifts sigma[0..nshift), solutions into
-// m.x32[0..nshift).  Same recursion and kernel sequence as the FP64 solver,
-// with the stencil in FP32/16-bit (dslash_s16.cu).
-static tmnd_status mms_sloppy(tmnd_gauge *g, MixedWork &m, const double *sigma, int nshift, int nsolve, double rho,
-                              int maxiter, int check_every, int profile, cudaStream_t s, MMSState &hs, LoopOut &lo,
-                              double *hist = nullptr, int hist_cap = 0) {
+// Sloppy multi-shift CG on m's right-hand sides b32(k), k < m.nrhs, for shifts
+// sigma[0..nshift), solutions into x32(k, i).  Same recursion and kernel sequence
+// as the FP64 solver, with the stencil in FP32/16-bit (dslash_s16.cu).  All
+// right-hand sides iterate in lockstep: each stencil launch covers all of them,
+// each has its own scalars and stops on its own (later launches skip it), and the
+// loop ends when all are done.  hs receives the final state of each.
+static tmnd_status mms_sloppy(tmnd_gauge *g, const MixedWork &m, const double *sigma, int nshift, int nsolve,
+                              double rho, int maxiter, int check_every, int profile, cudaStream_t s,
+                              std::vector<MMSState> &hs, LoopOut &lo, double *hist = nullptr, int hist_cap = 0) {
     const int Vh = g->geom.Vh;
     const long n = 24L * Vh;
+    const int R = m.nrhs;
     const int nb_hop = hop_blocks_s16(g->geom);
     const int nb_str = stream_blocks(n);
     const int nb_site = site_blocks(Vh);
-    double *part_norm = (double *)g->partials;
-    double *part_rr = part_norm + 2 * nb_hop;
-    double *part_str = part_rr + nb_hop;
-    char *tail = (char *)(part_str + (nb_str > nb_site ? nb_str : nb_site));
+    double *part_norm = (double *)g->partials;                 // [R][2][nb_hop]
+    double *part_rr = part_norm + (size_t)2 * R * nb_hop;      // [R][nb_hop]
+    double *part_str = part_rr + (size_t)R * nb_hop;           // [R][nb_site]
+    char *tail = (char *)(part_str + (size_t)R * (nb_str > nb_site ? nb_str : nb_site));
     tail = (char *)(((uintptr_t)tail + 255) & ~(uintptr_t)255);
+    const size_t st_stride = (sizeof(MMSState) + 255) & ~(size_t)255;
+    const size_t cf_stride = (sizeof(MMSCoef) + 255) & ~(size_t)255;
     MMSState *st = (MMSState *)tail;
-    MMSCoef *cf = (MMSCoef *)(tail + ((sizeof(MMSState) + 255) & ~(size_t)255));
+    MMSCoef *cf = (MMSCoef *)(tail + R * st_stride);
+    int *done_all = (int *)(tail + R * (st_stride + cf_stride));
 
     MMSConst c = {};
     c.nshift = nshift;
@@ -704,18 +833,19 @@ static tmnd_status mms_sloppy(tmnd_gauge *g, MixedWork &m, const double *sigma, 
     c.sigma0 = sigma[nsolve - 1];
     for (int i = 0; i < nshift; i++) c.delta[i] = sigma[i] - c.sigma0;
     c.rho2 = rho * rho;
-    ShiftPtrsT<float2> ptrs = {};
-    for (int i = 0; i < nshift; i++) {
-        ptrs.x[i] = m.x32[i];
-        ptrs.p[i] = m.p32[i];
-    }
-    RingPtrsT<float2> ring;
-    for (int l = 0; l < WIN; l++) ring.r[l] = m.ring[l];
-    const S16Out p16 = s16_out(m.p16, Vh), y16 = s16_out(m.y16, Vh), te16 = s16_out(m.te16, Vh);
+    SloppyVecs v = m.v;
+    v.nshift = nshift;
+    const S16Out p16 = v.p16, y16 = s16_out(m.y16, Vh), te16 = s16_out(m.te16, Vh);
     const S16In p16i{p16.q, p16.nrm}, y16i{y16.q, y16.nrm}, te16i{te16.q, te16.nrm};
+    S16Batch bt;
+    bt.nrhs = R;
+    bt.stride = v.sb;
+    bt.rdone = &st->done;
+    bt.rdone_stride = (int)(st_stride / sizeof(int));
 
-    k_init_s<<<nb_site, 128, 0, s>>>(Vh, m.b32, m.ring[WIN - 1], p16, ptrs, nshift, part_str);
-    k_init_state<<<1, 256, 0, s>>>(st, part_str, nb_site, c);
+    k_init_s<<<dim3(nb_site, R), 128, 0, s>>>(Vh, v, part_str);
+    k_init_state_b<<<R, 256, 0, s>>>(st, st_stride, part_str, nb_site, c);
+    k_all_done<<<1, 1, 0, s>>>(st, st_stride, R, done_all);
     TMND_CUDA_TRY(cudaGetLastError());
 
     auto body = [&](int k, auto mark) {
@@ -723,39 +853,58 @@ static tmnd_status mms_sloppy(tmnd_gauge *g, MixedWork &m, const double *sigma, 
         mark(0);
         S16EpiArgs e1 = {};
         e1.part_out = part_norm;
-        e1.done = &st->done;
-        launch_hop_even_s16(g->geom, g->stf, g->links_s16, p16i, te16, false, &st->done, s);
-        launch_hop_odd_s16(g->geom, g->stf, g->links_s16, p16i, te16i, y16, false, EPI_STORE_NORMS, e1, s);
-        launch_hop_even_s16(g->geom, g->stf, g->links_s16, y16i, te16, true, &st->done, s);
+        e1.done = done_all;
+        launch_hop_even_s16(g->geom, g->stf, g->links_s16, p16i, te16, false, done_all, s, bt);
+        launch_hop_odd_s16(g->geom, g->stf, g->links_s16, p16i, te16i, y16, false, EPI_STORE_NORMS, e1, s, bt);
+        launch_hop_even_s16(g->geom, g->stf, g->links_s16, y16i, te16, true, done_all, s, bt);
         S16EpiArgs e2 = {};
         e2.sigma = c.sigma0;
         e2.aux = p16i;
-        e2.r_in = m.ring[(j + WIN - 1) % WIN];
-        e2.r = m.ring[j];
+        e2.r_in = m.ring(0, (j + WIN - 1) % WIN);
+        e2.r = m.ring(0, j);
+        e2.r_stride = (long)WIN * n;
         e2.part_out = part_rr;
         e2.part_in = part_norm;
         e2.npart_in = nb_hop;
         e2.rr = &st->rr;
-        e2.done = &st->done;
-        launch_hop_odd_s16(g->geom, g->stf, g->links_s16, y16i, te16i, S16Out{}, true, EPI_MMS_R, e2, s);
+        e2.rr_stride = (int)(st_stride / sizeof(double));
+        e2.done = done_all;
+        launch_hop_odd_s16(g->geom, g->stf, g->links_s16, y16i, te16i, S16Out{}, true, EPI_MMS_R, e2, s, bt);
         mark(1);
-        k_scalars<<<1, 256, 0, s>>>(st, cf, part_norm, nb_hop, part_rr, c, j, hist, hist_cap);
-        k_pupdate_s<<<nb_site, 128, 0, s>>>(Vh, cf, m.ring[j], p16);
-        if (j == WIN - 1) k_window<float2><<<nb_str, UPD_THREADS, 0, s>>>(n, cf, ring, ptrs, nshift);
+        k_scalars_b<<<R, 256, 0, s>>>(st, cf, st_stride, cf_stride, part_norm, nb_hop, part_rr, c, j, hist,
+                                      hist_cap);
+        k_all_done<<<1, 1, 0, s>>>(st, st_stride, R, done_all);
+        k_pupdate_s<<<dim3(nb_site, R), 128, 0, s>>>(Vh, cf, cf_stride, v, j);
+        if (j == WIN - 1) k_window_s<<<dim3(nb_str, R), UPD_THREADS, 0, s>>>(cf, cf_stride, v);
         mark(2);
     };
-    tmnd_status ls = run_graph_loop(s, &st->done, maxiter, check_every, profile, body, lo);
+    tmnd_status ls = run_graph_loop(s, done_all, maxiter, check_every, profile, body, lo);
     if (ls != TMND_OK) return ls;
-    TMND_CUDA_TRY(cudaMemcpy(&hs, st, sizeof hs, cudaMemcpyDeviceToHost));
-    if (hs.status == TMND_ERR_NAN) {
-        tmnd_set_error("mms_cg_solve: NaN/Inf in a sloppy reduction at iteration %d", hs.iter);
-        return TMND_ERR_NAN;
-    }
+    hs.resize(R);
+    for (int k = 0; k < R; k++)
+        TMND_CUDA_TRY(cudaMemcpy(&hs[k], (char *)st + k * st_stride, sizeof(MMSState), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < R; k++)
+        if (hs[k].status == TMND_ERR_NAN) {
+            tmnd_set_error("mms_cg_solve: NaN/Inf in a sloppy reduction at iteration %d (right-hand side %d)",
+                           hs[k].iter, k);
+            return TMND_ERR_NAN;
+        }
     return TMND_OK;
 }
 
+// partial-buffer bytes the sloppy solve of nrhs right-hand sides needs
+static size_t sloppy_partial_bytes(const Geom &geom, int nrhs) {
+    const long n = 24L * geom.Vh;
+    const int nb_hop = hop_blocks_s16(geom);
+    const int nb_str = stream_blocks(n), nb_site = site_blocks(geom.Vh);
+    const size_t st_stride = (sizeof(MMSState) + 255) & ~(size_t)255;
+    const size_t cf_stride = (sizeof(MMSCoef) + 255) & ~(size_t)255;
+    return sizeof(double) * (size_t)nrhs * (3 * (size_t)nb_hop + (nb_str > nb_site ? nb_str : nb_site)) + 256 +
+           (size_t)nrhs * (st_stride + cf_stride) + 256;
+}
+
 // (Qhat^2 + sigma) x - b in FP64 into m.r64 (as b - (...)), returns |r|^2 on the host.
-static tmnd_status fp64_defect(tmnd_gauge *g, MixedWork &m, const double2 *b, const double2 *x, double sigma,
+static tmnd_status fp64_defect(tmnd_gauge *g, const MixedWork &m, const double2 *b, const double2 *x, double sigma,
                                cudaStream_t s, double *rr) {
     const long n = 24L * g->geom.Vh;
     const int nb = stream_blocks(n);
@@ -789,7 +938,7 @@ struct RefineStats {
 // FP64; stop the shift if |r| <= rho |b|, else solve (Qhat^2 + sigma_i) e = r
 // with the sloppy CG to the tolerance the target needs and add e in FP64.
 // res[i] receives the final FP64 relative residuals.
-static tmnd_status defect_correct(tmnd_gauge *g, MixedWork &m, const double2 *b, double2 *const *xk,
+static tmnd_status defect_correct(tmnd_gauge *g, const MixedWork &m, const double2 *b, double2 *const *xk,
                                   const double *sigma, std::vector<int> todo, double bb, double rho,
                                   double rho_inner, int maxiter, int check_every, int profile, cudaStream_t s,
                                   std::vector<double> &res, RefineStats &rs) {
@@ -815,21 +964,23 @@ static tmnd_status defect_correct(tmnd_gauge *g, MixedWork &m, const double2 *b,
                 next.push_back(i);
                 continue;
             }
-            st = convert_spinor(Vh, m.b32, TMND_F32, m.r64, TMND_F64, 1, s);
+            const MixedWork m1 = m.single();
+            st = convert_spinor(Vh, m1.b32(0), TMND_F32, m.r64, TMND_F64, 1, s);
             if (st != TMND_OK) return st;
             const double need = 0.3 * rho / res[i];
             const double tol = need > rho_inner ? need : rho_inner;
-            MMSState hc;
+            std::vector<MMSState> hv;
             LoopOut lc;
-            st = mms_sloppy(g, m, &sigma[i], 1, 1, tol, maxiter, check_every, profile, s, hc, lc);
+            st = mms_sloppy(g, m1, &sigma[i], 1, 1, tol, maxiter, check_every, profile, s, hv, lc);
             if (st != TMND_OK) return st;
+            const MMSState &hc = hv[0];
             for (int k = 0; k < hc.iter && k < (int)lc.hop_t.size(); k++) {
                 rs.hop_ms += lc.hop_t[k];
                 rs.upd_ms += lc.upd_t[k];
             }
             rs.iters += hc.iter;
             rs.launches += 2 + lc.nlaunch * ((long long)check_every * 6 + check_every / WIN) + 1;
-            k_add_f32_to_f64<<<stream_blocks(n), UPD_THREADS, 0, s>>>(n, m.x32[0], xk[i]);
+            k_add_f32_to_f64<<<stream_blocks(n), UPD_THREADS, 0, s>>>(n, m1.x32(0, 0), xk[i]);
             TMND_CUDA_TRY(cudaGetLastError());
             next.push_back(i);
         }
@@ -847,77 +998,87 @@ static tmnd_status defect_correct(tmnd_gauge *g, MixedWork &m, const double2 *b,
     return TMND_OK;
 }
 
-static tmnd_status mixed_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *x, const double *sigma,
-                                 int nshift, int nsolve, double rho, double rho_inner, int maxiter, int check_every,
-                                 int profile, tmnd_solve_info *info, cudaStream_t s, int rhs_index, double *hist,
-                                 int hist_cap) {
+// Mixed-precision solve of right-hand sides k0 .. k0+R-1: one batched sloppy
+// multi-shift CG for all of them (m holds R sloppy blocks), then per right-hand
+// side the FP64 defect correction of the shifts that must converge.
+static tmnd_status mixed_batch(tmnd_gauge *g, const double2 *b, double2 *const *x, const double *sigma, int nshift,
+                               int nsolve, double rho, double rho_inner, int maxiter, int check_every, int profile,
+                               tmnd_solve_info *info, cudaStream_t s, int k0, int R, double *hist, int hist_cap) {
     const int Vh = g->geom.Vh;
     const long n = 24L * Vh;
-    MixedWork m = mixed_work(g->work, Vh, nshift);
-    double2 *xk[NS];
-    for (int i = 0; i < nshift; i++) xk[i] = x[i] + (size_t)rhs_index * n;
+    MixedWork m = mixed_work(g->work, Vh, nshift, R);
     tmnd_status st;
-    // |b|^2 in FP64
-    double bb = 0;
-    {
+    // |b_k|^2 in FP64
+    std::vector<double> bb(R, 0.0);
+    for (int k = 0; k < R; k++) {
         const int nb = stream_blocks(n);
         double *part = (double *)g->partials;
         TMND_CUDA_TRY(cudaMemsetAsync(m.y64, 0, sizeof(double2) * n, s));
-        k_diff_norm<<<nb, UPD_THREADS, 0, s>>>(n, b, m.y64, part);
+        k_diff_norm<<<nb, UPD_THREADS, 0, s>>>(n, b + (size_t)(k0 + k) * n, m.y64, part);
         std::vector<double> h(nb);
         TMND_CUDA_TRY(cudaMemcpyAsync(h.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
         TMND_CUDA_TRY(cudaStreamSynchronize(s));
-        for (int k = 0; k < nb; k++) bb += h[k];
-    }
-    if (bb == 0.0) {
-        for (int i = 0; i < nshift; i++) TMND_CUDA_TRY(cudaMemsetAsync(xk[i], 0, sizeof(double2) * n, s));
-        return TMND_OK;
-    }
-    // 1. sloppy multi-shift CG on b
-    st = convert_spinor(Vh, m.b32, TMND_F32, b, TMND_F64, 1, s);
-    if (st != TMND_OK) return st;
-    MMSState hs;
-    LoopOut lo;
-    st = mms_sloppy(g, m, sigma, nshift, nsolve, rho_inner, maxiter, check_every, profile, s, hs, lo, hist, hist_cap);
-    if (st != TMND_OK) return st;
-    for (int i = 0; i < nshift; i++) {
-        st = convert_spinor(Vh, xk[i], TMND_F64, m.x32[i], TMND_F32, 1, s);
+        for (int q = 0; q < nb; q++) bb[k] += h[q];
+        st = convert_spinor(Vh, m.b32(k), TMND_F32, b + (size_t)(k0 + k) * n, TMND_F64, 1, s);
         if (st != TMND_OK) return st;
     }
-    int fp64 = 0, rounds = 0, riters = 0;
-    long long launches = 2 + lo.nlaunch * ((long long)check_every * 6 + check_every / WIN) + 2 + nshift;
+    // 1. batched sloppy multi-shift CG (a zero right-hand side is done at once)
+    std::vector<MMSState> hs;
+    LoopOut lo;
+    st = mms_sloppy(g, m, sigma, nshift, nsolve, rho_inner, maxiter, check_every, profile, s, hs, lo,
+                    k0 == 0 ? hist : nullptr, hist_cap);
+    if (st != TMND_OK) return st;
+    long long launches = 3 + lo.nlaunch * ((long long)check_every * 7 + check_every / WIN);
     double hop_ms = 0, upd_ms = 0;
-    auto add_prof = [&](const LoopOut &l, int iters) {
-        for (int k = 0; k < iters && k < (int)l.hop_t.size(); k++) {
-            hop_ms += l.hop_t[k];
-            upd_ms += l.upd_t[k];
-        }
-    };
-    add_prof(lo, hs.iter);
-    if (info) {
-        if (rhs_index == 0 || hs.iter > info->iters) info->iters = hs.iter;
-        for (int i = 0; i < nshift; i++) {
-            info->conv_iter[i] = hs.conv_iter[i];
-            info->zeta[i] = hs.zeta[i];
-        }
+    int maxit = 0;
+    for (int k = 0; k < R; k++) maxit = hs[k].iter > maxit ? hs[k].iter : maxit;
+    for (int q = 0; q < maxit && q < (int)lo.hop_t.size(); q++) {
+        hop_ms += lo.hop_t[q];
+        upd_ms += lo.upd_t[q];
     }
-    // 2. FP64 defect correction, shift by shift, for the shifts that must converge
-    std::vector<double> res(nshift, 0.0);
-    std::vector<int> todo;
-    for (int i = 0; i < nsolve; i++) todo.push_back(i);
-    RefineStats rs;
-    st = defect_correct(g, m, b, xk, sigma, todo, bb, rho, rho_inner, maxiter, check_every, profile, s, res, rs);
-    if (st != TMND_OK && st != TMND_ERR_NOCONV) return st;
-    const tmnd_status conv = st;
-    fp64 += rs.fp64;
-    riters += rs.iters;
-    rounds = rs.rounds;
-    launches += rs.launches;
-    hop_ms += rs.hop_ms;
-    upd_ms += rs.upd_ms;
+    tmnd_status conv = TMND_OK;
+    int fp64 = 0, rounds = 0, riters = 0;
+    for (int k = 0; k < R; k++) {
+        const int rhs = k0 + k;
+        double2 *xk[NS];
+        for (int i = 0; i < nshift; i++) xk[i] = x[i] + (size_t)rhs * n;
+        if (bb[k] == 0.0) {
+            for (int i = 0; i < nshift; i++) TMND_CUDA_TRY(cudaMemsetAsync(xk[i], 0, sizeof(double2) * n, s));
+            continue;
+        }
+        for (int i = 0; i < nshift; i++) {
+            st = convert_spinor(Vh, xk[i], TMND_F64, m.x32(k, i), TMND_F32, 1, s);
+            if (st != TMND_OK) return st;
+        }
+        launches += nshift + 2;
+        if (info) {
+            if (rhs == 0 || hs[k].iter > info->iters) info->iters = hs[k].iter;
+            for (int i = 0; i < nshift; i++) {
+                if (rhs == 0 || hs[k].conv_iter[i] > info->conv_iter[i] || hs[k].conv_iter[i] < 0)
+                    info->conv_iter[i] = hs[k].conv_iter[i];
+                info->zeta[i] = hs[k].zeta[i];
+            }
+        }
+        // 2. FP64 defect correction, shift by shift, for the shifts that must converge
+        std::vector<double> res(nshift, 0.0);
+        std::vector<int> todo;
+        for (int i = 0; i < nsolve; i++) todo.push_back(i);
+        RefineStats rs;
+        st = defect_correct(g, m, b + (size_t)rhs * n, xk, sigma, todo, bb[k], rho, rho_inner, maxiter,
+                            check_every, profile, s, res, rs);
+        if (st != TMND_OK && st != TMND_ERR_NOCONV) return st;
+        if (st == TMND_ERR_NOCONV) conv = st;
+        fp64 += rs.fp64;
+        riters += rs.iters;
+        rounds = rs.rounds > rounds ? rs.rounds : rounds;
+        launches += rs.launches;
+        hop_ms += rs.hop_ms;
+        upd_ms += rs.upd_ms;
+        if (info)
+            for (int i = 0; i < nshift; i++)
+                if (rhs == 0 || res[i] > info->true_res[i]) info->true_res[i] = res[i];
+    }
     if (info) {
-        for (int i = 0; i < nshift; i++)
-            if (rhs_index == 0 || res[i] > info->true_res[i]) info->true_res[i] = res[i];
         info->fp64_applies += fp64;
         info->refine_iters += riters;
         if (rounds > info->refine_rounds) info->refine_rounds = rounds;
@@ -954,14 +1115,20 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     TMND_ARG_CHECK(params->prec == TMND_F64 || mixed, "mms_cg_solve: prec %d not supported", params->prec);
     const double rho_inner = params->rho_inner > 0 ? params->rho_inner : 1e-5;
     TMND_ARG_CHECK(rho_inner < 1, "mms_cg_solve: rho_inner = %g not in (0, 1)", rho_inner);
+    TMND_ARG_CHECK(params->batch >= 0 && params->batch <= TMND_MAX_BATCH, "mms_cg_solve: batch = %d not in [0, %d]",
+                   params->batch, TMND_MAX_BATCH);
+    // right-hand sides iterated together by the sloppy solver of the mixed path
+    int R = params->batch > 0 ? params->batch : TMND_MAX_BATCH;
+    if (R > nrhs) R = nrhs;
     const size_t sp = tmnd_spinor_bytes(g);
     tmnd_status st = tmnd_ensure_workspace(
-        g, mixed ? mixed_work_bytes(g->geom.Vh, nshift) : (WIN + 3 + (size_t)nshift) * sp);
+        g, mixed ? mixed_work_bytes(g->geom.Vh, nshift, R) : (WIN + 3 + (size_t)nshift) * sp);
     if (st != TMND_OK) return st;
     const long n = (long)(sp / sizeof(double2));
     const int nbh = hop_blocks(g->geom) > hop_blocks_s16(g->geom) ? hop_blocks(g->geom) : hop_blocks_s16(g->geom);
     const int nbs = stream_blocks(n) > site_blocks(g->geom.Vh) ? stream_blocks(n) : site_blocks(g->geom.Vh);
     size_t pbytes = sizeof(double) * (3 * (size_t)nbh + nbs) + 256 + 2 * 4096 + sizeof(MMSState) + sizeof(MMSCoef);
+    if (mixed && sloppy_partial_bytes(g->geom, R) > pbytes) pbytes = sloppy_partial_bytes(g->geom, R);
     st = tmnd_ensure_partials(g, pbytes);
     if (st != TMND_OK) return st;
     if (info) memset(info, 0, sizeof *info);
@@ -980,15 +1147,23 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     TMND_CUDA_TRY(cudaEventRecord(e0, user));
     TMND_CUDA_TRY(cudaStreamWaitEvent(s, e0, 0));
     tmnd_status res = TMND_OK;
-    for (int k = 0; k < nrhs && res == TMND_OK; k++) {
-        const double2 *bk = (const double2 *)b + (size_t)k * (sp / sizeof(double2));
-        double *hk = k == 0 ? dhist : nullptr;
-        tmnd_status rk =
-            mixed ? mixed_one_rhs(g, bk, (double2 *const *)x, sigma, nshift, nsolve, params->rho, rho_inner,
-                                  params->maxiter, check_every, params->profile ? 1 : 0, info, s, k, hk, hist_cap)
-                  : mms_one_rhs(g, bk, (double2 *const *)x, sigma, nshift, nsolve, params->rho, params->maxiter,
-                                check_every, params->profile ? 1 : 0, info, s, k, hk, hist_cap);
-        if (rk != TMND_OK) res = rk;
+    if (mixed) {
+        for (int k0 = 0; k0 < nrhs && res == TMND_OK; k0 += R) {
+            const int r = nrhs - k0 < R ? nrhs - k0 : R;
+            tmnd_status rk = mixed_batch(g, (const double2 *)b, (double2 *const *)x, sigma, nshift, nsolve,
+                                         params->rho, rho_inner, params->maxiter, check_every,
+                                         params->profile ? 1 : 0, info, s, k0, r, dhist, hist_cap);
+            if (rk != TMND_OK) res = rk;
+        }
+    } else {
+        for (int k = 0; k < nrhs && res == TMND_OK; k++) {
+            const double2 *bk = (const double2 *)b + (size_t)k * (sp / sizeof(double2));
+            double *hk = k == 0 ? dhist : nullptr;
+            tmnd_status rk = mms_one_rhs(g, bk, (double2 *const *)x, sigma, nshift, nsolve, params->rho,
+                                         params->maxiter, check_every, params->profile ? 1 : 0, info, s, k, hk,
+                                         hist_cap);
+            if (rk != TMND_OK) res = rk;
+        }
     }
     cudaEventRecord(e0, s);
     cudaStreamWaitEvent(user, e0, 0);

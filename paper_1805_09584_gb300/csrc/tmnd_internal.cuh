@@ -191,18 +191,32 @@ struct S16EpiArgs {
     S16In aux;              // EPI_SHIFT / EPI_MMS_R: vector multiplied by sigma
     float2 *r;              // EPI_MMS_R: updated residual (FP32 planes, written)
     const float2 *r_in;     // EPI_MMS_R: residual before the update
-    double *part_out;
-    const double *part_in;
+    double *part_out;       // block partials: EPI_STORE_NORMS [rhs][2][grid], EPI_MMS_R [rhs][grid]
+    const double *part_in;  // EPI_MMS_R: the previous launch's [rhs][2][npart_in]
     int npart_in;
-    const double *rr;
+    const double *rr;       // EPI_MMS_R: (r, r) of right-hand side k at rr[k * rr_stride]
     const int *done;
+    long r_stride;          // EPI_MMS_R: float2 elements between right-hand sides of r / r_in
+    int rr_stride;          // doubles between right-hand sides of rr
+};
+
+// Several right-hand sides in one stencil launch (links read once, shared in cache):
+// right-hand side k of every 16-bit vector argument starts k * stride bytes after
+// the first; k is skipped while rdone[k * rdone_stride] is set (rdone may be NULL).
+constexpr int TMND_MAX_BATCH = 16;
+struct S16Batch {
+    int nrhs = 1;
+    size_t stride = 0;
+    const int *rdone = nullptr;
+    int rdone_stride = 0;
 };
 
 int hop_blocks_s16(const Geom &g);
 void launch_hop_even_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In in, S16Out out, bool dag,
-                         const int *done, cudaStream_t s);
+                         const int *done, cudaStream_t s, const S16Batch &bt = S16Batch());
 void launch_hop_odd_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In psi, S16In te, S16Out out,
-                        bool dag, HopEpi epi, const S16EpiArgs &ea, cudaStream_t s);
+                        bool dag, HopEpi epi, const S16EpiArgs &ea, cudaStream_t s,
+                        const S16Batch &bt = S16Batch());
 
 void launch_pack_links_s16(const Geom &g, const double2 *canon, int2 *out, cudaStream_t s);
 size_t spinor_bytes_prec(int Vh, int prec);

@@ -69,3 +69,53 @@ def test_mixed_bench_lattice_certified():
         tr = oracle.true_residual(act, U, b, xs[i][0], s)
         assert tr <= 1.01e-10, (i, tr, info)
     g.close()
+
+
+@pytest.mark.parametrize("nrhs,batch", [(3, 0), (5, 2)])
+def test_mixed_batched_rhs_match_one_at_a_time(nrhs, batch):
+    """Batched sloppy solve (all right-hand sides in every stencil launch, each
+    with its own scalars and stopping point; 5 RHS in batches of 2 leaves a
+    ragged last batch): every shift of every RHS certified by the oracle, and
+    the solutions agree with the one-at-a-time solve to the certified accuracy."""
+    tm = require_gpu()
+    dims = (8, 6, 6, 6)
+    U = synth.random_su3_field(dims, 0.5, 78)
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    b = synth.gaussian_rhs(dims, 101, nrhs=nrhs)
+    b[1] *= 1e-3   # right-hand sides of very different size converge at different iterations
+    sig = synth.shift_set(8, 1e-3, 2.0)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    bi = g.pack(torch.from_numpy(b).cuda(), nrhs=nrhs)
+    xb = [g.spinor(nrhs) for _ in sig]
+    x1 = [g.spinor(nrhs) for _ in sig]
+    tm.mms_cg_solve(g.handle, bi, nrhs, sig, xb, prec=tm.TMND_S16, batch=batch)
+    tm.mms_cg_solve(g.handle, bi, nrhs, sig, x1, prec=tm.TMND_S16, batch=1)
+    for i, s in enumerate(sig):
+        a = g.unpack(xb[i], nrhs).cpu().numpy()
+        c = g.unpack(x1[i], nrhs).cpu().numpy()
+        for k in range(nrhs):
+            assert oracle.true_residual(act, U, b[k], a[k], s) <= 1.01e-10, (i, k)
+            # both are certified solutions: they differ by at most ~ rho |b| / sigma
+            assert np.linalg.norm(a[k] - c[k]) <= 2e-10 * np.linalg.norm(b[k]) / s
+    g.close()
+
+
+def test_s16_multi_rhs_apply_equals_single():
+    """One 16-bit stencil launch over 3 right-hand sides gives, bit for bit, the
+    three single applications (same arithmetic per right-hand side)."""
+    tm = require_gpu()
+    dims = (8, 6, 6, 6)
+    U = synth.random_su3_field(dims, 0.4, 79)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    b = synth.gaussian_rhs(dims, 103, nrhs=3)
+    q = g.convert(g.pack(torch.from_numpy(b).cuda(), nrhs=3), tm.TMND_F64, tm.TMND_S16, nrhs=3)
+    for op in (tm.OP_MHAT, tm.OP_QHAT2):
+        out3 = g.spinor(3, prec=tm.TMND_S16)
+        tm.tm_nd_apply(g.handle, out3, q, op | tm.OP_S16, 0.0213, nrhs=3)
+        nb = tm.tmnd_spinor_bytes_prec(g.handle, tm.TMND_S16)
+        q8, o8 = q.view(torch.uint8), out3.view(torch.uint8)
+        for k in range(3):
+            one = g.spinor(1, prec=tm.TMND_S16)
+            tm.tm_nd_apply(g.handle, one, q8[k * nb:(k + 1) * nb], op | tm.OP_S16, 0.0213, nrhs=1)
+            assert torch.equal(one.view(torch.uint8), o8[k * nb:(k + 1) * nb]), (op, k)
+    g.close()
