@@ -253,6 +253,9 @@ typedef struct {
     int block[4];              /* aggregate size {bt, bx, by, bz}; each divides dims */
     int nvec;                  /* test vectors per chirality, 1..32 (N_v of Sec. 3) */
     double coarse_mu_factor;   /* d of Sec. 3: coarse twisted mass d*mu_bar (<= 0: 1) */
+    int coarse_simt;           /* 0: mg_coarse_apply on the tensor cores (tcgen05, TF32 operands,
+                                  FP32 accumulation) whenever 2 nvec % 4 == 0 and nrhs <= 16,
+                                  else FP32 CUDA cores; 1: always FP32 CUDA cores */
 } tmnd_mg_params;
 
 /* Build the hierarchy from `nvec` caller-provided test vectors (device, FP32
@@ -277,7 +280,13 @@ tmnd_status tmnd_mg_prolong(const tmnd_mg *mg, void *out_fine, const void *in_c,
  *   D'_c = D_W,c (x) 1 + i 2 kappa d mu_bar (Gamma_5,c (x) tau_3) - 2 kappa eps_bar (1 (x) tau_1)
  *          + i odd_shift_s (tau_1 (x) G_odd)
  * (the last term is the coarse image of + i s gamma_5 tau_1 on odd sites, the shift
- * of the case-C systems).  9-point stencil over blocks; nrhs * 4 nvec <= 1024. */
+ * of the case-C systems).  9-point stencil over blocks.  Vectors 16-byte aligned.
+ * Tensor cores (see tmnd_mg_params.coarse_simt): nrhs <= 16, 2 nvec % 4 == 0; the
+ * dense blocks and the vectors enter the products as TF32 (relative error ~1e-3),
+ * sums in FP32; a wait that gives up in the kernel is reported as TMND_ERR_TIMEOUT
+ * by the next tmnd_mg_solve / tmnd_hybrid_solve.  The handle holds the operand
+ * tiles of one application: one mg_coarse_apply at a time per handle.  CUDA cores:
+ * nrhs * 4 nvec <= 1024, FP32 throughout. */
 tmnd_status mg_coarse_apply(const tmnd_mg *mg, void *out_c, const void *in_c, int nrhs, double odd_shift_s,
                             void *stream);
 

@@ -50,7 +50,8 @@ class Action(ctypes.Structure):
 
 
 class MGParams(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_int * 4), ("nvec", ctypes.c_int), ("coarse_mu_factor", ctypes.c_double)]
+    _fields_ = [("block", ctypes.c_int * 4), ("nvec", ctypes.c_int), ("coarse_mu_factor", ctypes.c_double),
+                ("coarse_simt", ctypes.c_int)]
 
 
 class HybridParams(ctypes.Structure):
@@ -262,11 +263,11 @@ def lagrange_guess(h, nodes, xs, target: float, out, nrhs: int = 1, stream=None)
     return leb.value
 
 
-def tmnd_mg_create(h, block, nvec: int, test_vectors, coarse_mu_factor: float = 1.0):
+def tmnd_mg_create(h, block, nvec: int, test_vectors, coarse_mu_factor: float = 1.0, coarse_simt: bool = False):
     p = MGParams()
     for k in range(4):
         p.block[k] = int(block[k])
-    p.nvec, p.coarse_mu_factor = int(nvec), float(coarse_mu_factor)
+    p.nvec, p.coarse_mu_factor, p.coarse_simt = int(nvec), float(coarse_mu_factor), int(bool(coarse_simt))
     out = ctypes.c_void_p()
     _check(lib().tmnd_mg_create(h, ctypes.byref(p), _ptr(test_vectors), ctypes.byref(out)))
     return out

@@ -33,7 +33,19 @@ struct tmnd_mg {
     float2 *Godd;       // [block][2nv][2nv] P^+ gamma_5 Pi_odd P
     void *work;         // fine-vector scratch for the assembly
     size_t work_bytes;
+    int tc;             // coarse apply on the tensor cores where the shape allows
+    int *tc_err;        // device flag: a tensor-core kernel gave up waiting
+    void *Dt, *Gt;      // D_W,c and G_odd again, in the tensor-core operand-tile layout
+    void *Bt;           // B operand tiles of one application (up to 16 right-hand sides)
 };
+
+size_t coarse_tc_smem(int n2, int nrhs);
+size_t coarse_tc_atile_bytes(int nv);
+size_t coarse_tc_btile_bytes(int nblock, int nv, int nrhs);
+tmnd_status coarse_tc_make_atiles(const float2 *src, void *dst, long nmat, int nv, cudaStream_t s);
+tmnd_status launch_coarse_apply_tc(const void *Dt, const void *Gt, void *btiles, const float2 *x, float2 *y,
+                                   int nblock, const int nbd[4], int nv, int nrhs, float mu_c, float eps_c,
+                                   float s_odd, int *err, cudaStream_t s);
 
 namespace {
 
@@ -386,6 +398,7 @@ extern "C" tmnd_status tmnd_mg_create(tmnd_gauge *g, const tmnd_mg_params *p, co
     }
     TMND_ARG_CHECK(mg->nsb * 6 >= 2 * p->nvec || true, "");
     mg->nv = p->nvec;
+    mg->tc = p->coarse_simt ? 0 : 1;
     const double d = p->coarse_mu_factor > 0 ? p->coarse_mu_factor : 1.0;
     mg->mu_c = 2 * g->act.kappa * g->act.mu_bar * d;
     mg->eps_c = 2 * g->act.kappa * g->act.eps_bar;
@@ -398,6 +411,8 @@ extern "C" tmnd_status tmnd_mg_create(tmnd_gauge *g, const tmnd_mg_params *p, co
     cudaError_t e = cudaMalloc(&mg->P, pbytes);
     if (e == cudaSuccess) e = cudaMalloc(&mg->Dc, dbytes);
     if (e == cudaSuccess) e = cudaMalloc(&mg->Godd, gbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&mg->tc_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(mg->tc_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&mg->work, mg->work_bytes);
     if (e != cudaSuccess) {
         tmnd_mg_destroy(mg);
@@ -463,6 +478,16 @@ extern "C" tmnd_status tmnd_mg_create(tmnd_gauge *g, const tmnd_mg_params *p, co
     if (e == cudaSuccess) e = cudaMemcpy(mg->Dc, hD.data(), dbytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(mg->Godd, hG.data(), gbytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && mg->tc && coarse_tc_smem(n2, 1) > 0) {  // operand tiles for the tensor cores
+        const size_t at = coarse_tc_atile_bytes(mg->nv);
+        e = cudaMalloc(&mg->Dt, at * 9 * mg->nblock);
+        if (e == cudaSuccess) e = cudaMalloc(&mg->Gt, at * mg->nblock);
+        if (e == cudaSuccess) e = cudaMalloc(&mg->Bt, coarse_tc_btile_bytes(mg->nblock, mg->nv, 16));
+        if (e == cudaSuccess &&
+            (coarse_tc_make_atiles(mg->Dc, mg->Dt, 9L * mg->nblock, mg->nv, 0) != TMND_OK ||
+             coarse_tc_make_atiles(mg->Godd, mg->Gt, mg->nblock, mg->nv, 0) != TMND_OK))
+            e = cudaErrorLaunchFailure;
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(tmpc);
     if (e != cudaSuccess) {
@@ -479,6 +504,10 @@ extern "C" void tmnd_mg_destroy(tmnd_mg *mg) {
     cudaDeviceSynchronize();
     if (mg->P) cudaFree(mg->P);
     if (mg->Dc) cudaFree(mg->Dc);
+    if (mg->tc_err) cudaFree(mg->tc_err);
+    if (mg->Dt) cudaFree(mg->Dt);
+    if (mg->Gt) cudaFree(mg->Gt);
+    if (mg->Bt) cudaFree(mg->Bt);
     if (mg->Godd) cudaFree(mg->Godd);
     if (mg->work) cudaFree(mg->work);
     delete mg;
@@ -513,9 +542,15 @@ extern "C" tmnd_status mg_coarse_apply(const tmnd_mg *mg, void *out_c, const voi
     TMND_ARG_CHECK(mg && out_c && in_c, "mg_coarse_apply: NULL argument");
     TMND_ARG_CHECK(out_c != in_c, "mg_coarse_apply: out and in must not alias");
     const int n2 = 2 * mg->nv;
-    TMND_ARG_CHECK(nrhs >= 1 && n2 * 2 * nrhs <= 1024, "mg_coarse_apply: nrhs = %d too large for 2*nvec = %d",
-                   nrhs, n2);
+    TMND_ARG_CHECK(nrhs >= 1, "mg_coarse_apply: nrhs = %d", nrhs);
+    TMND_ARG_CHECK(((uintptr_t)out_c & 15) == 0 && ((uintptr_t)in_c & 15) == 0,
+                   "mg_coarse_apply: vectors must be 16-byte aligned");
     cudaGetLastError();
+    if (mg->tc && mg->Dt && coarse_tc_smem(n2, nrhs) > 0)
+        return launch_coarse_apply_tc(mg->Dt, mg->Gt, mg->Bt, (const float2 *)in_c, (float2 *)out_c, mg->nblock,
+                                      mg->nbd, mg->nv, nrhs, (float)mg->mu_c, (float)mg->eps_c, (float)odd_shift_s,
+                                      mg->tc_err, (cudaStream_t)stream);
+    TMND_ARG_CHECK(n2 * 2 * nrhs <= 1024, "mg_coarse_apply: nrhs = %d too large for 2*nvec = %d", nrhs, n2);
     MGGeom m = mg_geom(mg);
     const size_t smem = sizeof(float2) * 9 * n2 * 2 * nrhs;
     TMND_ARG_CHECK(smem <= 96 * 1024, "mg_coarse_apply: nrhs too large");
@@ -525,6 +560,18 @@ extern "C" tmnd_status mg_coarse_apply(const tmnd_mg *mg, void *out_c, const voi
         m, mg->Dc, mg->Godd, (const float2 *)in_c, (float2 *)out_c, nrhs, (float)mg->mu_c, (float)mg->eps_c,
         (float)odd_shift_s);
     TMND_CUDA_TRY(cudaGetLastError());
+    return TMND_OK;
+}
+
+// reads and clears the tensor-core timeout flag (synchronous)
+tmnd_status tmnd_mg_tc_status(const tmnd_mg *mg) {
+    int h = 0;
+    TMND_CUDA_TRY(cudaMemcpy(&h, mg->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        cudaMemset(mg->tc_err, 0, sizeof(int));
+        tmnd_set_error("mg_coarse_apply: a tensor-core kernel timed out waiting for its MMAs");
+        return TMND_ERR_TIMEOUT;
+    }
     return TMND_OK;
 }
 

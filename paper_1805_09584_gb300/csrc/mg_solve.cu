@@ -371,6 +371,8 @@ size_t mg_gcr_scratch_bytes(tmnd_mg *mg, int restart) {
     return al(n) * (6 + 2 * mr) + al(nc) * (3 + 32) + sizeof(double) * 2 * 1024;
 }
 
+tmnd_status tmnd_mg_tc_status(const tmnd_mg *mg);
+
 extern "C" tmnd_status tmnd_mg_solve(tmnd_mg *mg, void *x, const void *b, double s, double tol, int maxiter,
                                      int restart, int nu, int *iters, double *res, void *stream) {
     TMND_ARG_CHECK(mg && x && b, "tmnd_mg_solve: NULL argument");
@@ -381,7 +383,8 @@ extern "C" tmnd_status tmnd_mg_solve(tmnd_mg *mg, void *x, const void *b, double
     tmnd_status st = mg_gcr_solve(mg, (float2 *)x, (const float2 *)b, s, tol, maxiter, restart, nu,
                                   (cudaStream_t)stream, iters, res, scratch);
     cudaFree(scratch);
-    return st;
+    const tmnd_status tc = tmnd_mg_tc_status(mg);
+    return st != TMND_OK ? st : tc;
 }
 
 extern "C" tmnd_status tmnd_dnd_full_apply(tmnd_gauge *g, void *out, const void *in, double s, void *stream) {

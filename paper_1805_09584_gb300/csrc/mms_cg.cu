@@ -1190,6 +1190,7 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
 tmnd_status mg_gcr_solve(tmnd_mg *mg, float2 *x, const float2 *b, double s, double tol, int maxiter, int restart,
                          int nu, cudaStream_t st, int *iters_out, double *res_out, void *scratch);
 size_t mg_gcr_scratch_bytes(tmnd_mg *mg, int restart);
+tmnd_status tmnd_mg_tc_status(const tmnd_mg *mg);
 __global__ void k_g5tau1(int Vh, const double2 *__restrict__ in, double2 *__restrict__ out);
 
 extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void *b, int nrhs, const double *sigma,
@@ -1340,6 +1341,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
     cudaEventDestroy(e0);
     cudaStreamDestroy(s);
     cudaFree(scr);
+    if (res_status == TMND_OK) res_status = tmnd_mg_tc_status(mg);
     if (res_status == TMND_OK && fin != cudaSuccess) {
         tmnd_set_error("tmnd_hybrid_solve: %s", cudaGetErrorString(fin));
         return TMND_ERR_CUDA;

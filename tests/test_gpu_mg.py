@@ -2,7 +2,9 @@
 prolongator (block Gram-Schmidt of the same test vectors), coarse Wilson
 operator P^+ D_W P, odd-site Gram G_odd, restriction / prolongation, and the
 coarse doublet stencil mg_coarse_apply.  FP32 on the device: tolerances 2e-5
-relative (sums of ~1e3 FP32 products of O(1) numbers)."""
+relative (sums of ~1e3 FP32 products of O(1) numbers).  The tensor-core coarse
+apply rounds both operands to TF32 (10 mantissa bits, relative 2^-11 each):
+4e-3 of the largest output, max-norm."""
 import numpy as np
 import pytest
 
@@ -54,12 +56,15 @@ def mgsetup(request):
     g = tm.Gauge(U, dims, KAPPA, MU, EPS)
     tv = torch.from_numpy(to_mg_layout(dims, vecs, 12)).cuda()
     mg = tm.tmnd_mg_create(g.handle, bdims, NV, tv)
+    mg_simt = tm.tmnd_mg_create(g.handle, bdims, NV, tv, coarse_simt=True)
     act = oracle.action(dims, KAPPA, MU, EPS)
     P = oracle.mg_prolongator(dims, bdims, vecs.astype(np.complex128).reshape(NV, V, 4, 3))
     Dcw = oracle.mg_coarse_wilson(act, U, P)
     nb = P.shape[1] // (2 * NV)
-    yield dict(tm=tm, g=g, mg=mg, dims=dims, bdims=bdims, U=U, P=P, Dcw=Dcw, nb=nb, act=act, vecs=vecs)
+    yield dict(tm=tm, g=g, mg=mg, mg_simt=mg_simt, dims=dims, bdims=bdims, U=U, P=P, Dcw=Dcw, nb=nb, act=act,
+               vecs=vecs)
     tm.tmnd_mg_destroy(mg)
+    tm.tmnd_mg_destroy(mg_simt)
     g.close()
 
 
@@ -142,30 +147,78 @@ def test_restrict_prolong_match_oracle(mgsetup):
             assert np.max(np.abs(back[r, :, f * 12:(f + 1) * 12].ravel() - ref)) < 2e-5 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("s_odd", [0.0, 0.03])
-def test_coarse_apply_matches_oracle(mgsetup, s_odd):
-    s = mgsetup
-    tm, mg, nb = s["tm"], s["mg"], s["nb"]
-    n2 = 2 * NV
-    Dnd = oracle.mg_coarse_nd(s["Dcw"], nb, NV, 2 * KAPPA * MU, 2 * KAPPA * EPS)
+def _coarse_nd_dense(s, s_odd, nv, P, Dcw, nb):
+    n2 = 2 * nv
+    Dnd = oracle.mg_coarse_nd(Dcw, nb, nv, 2 * KAPPA * MU, 2 * KAPPA * EPS)
     if s_odd:
         V = int(np.prod(s["dims"]))
         odd = np.zeros(V, bool)
         odd[synth.odd_sites(s["dims"])] = True
         g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), V) * np.repeat(odd, 12)
-        G = s["P"].conj().T @ (g5[:, None] * s["P"])
+        G = P.conj().T @ (g5[:, None] * P)
         for b in range(nb):
             i0 = b * 2 * n2
             blk = G[b * n2:(b + 1) * n2, b * n2:(b + 1) * n2]
             Dnd[i0:i0 + n2, i0 + n2:i0 + 2 * n2] += 1j * s_odd * blk
             Dnd[i0 + n2:i0 + 2 * n2, i0:i0 + n2] += 1j * s_odd * blk
+    return Dnd
+
+
+@pytest.mark.parametrize("s_odd", [0.0, 0.03])
+@pytest.mark.parametrize("path,R,tol", [("simt", 3, 2e-5), ("tc", 1, 4e-3), ("tc", 3, 4e-3), ("tc", 8, 4e-3),
+                                        ("tc", 16, 4e-3)])
+def test_coarse_apply_matches_oracle(mgsetup, s_odd, path, R, tol):
+    s = mgsetup
+    tm, nb = s["tm"], s["nb"]
+    mg = s["mg_simt"] if path == "simt" else s["mg"]
+    Dnd = _coarse_nd_dense(s, s_odd, NV, s["P"], s["Dcw"], nb)
     rng = np.random.default_rng(5)
-    R = 3
-    xv = rng.standard_normal((R, nb * 2 * n2)) + 1j * rng.standard_normal((R, nb * 2 * n2))
+    xv = rng.standard_normal((R, nb * 4 * NV)) + 1j * rng.standard_normal((R, nb * 4 * NV))
     xin = torch.from_numpy(xv.astype(np.complex64).ravel()).cuda()
     yout = torch.zeros_like(xin)
     tm.mg_coarse_apply(mg, yout, xin, R, s_odd)
     got = yout.cpu().numpy().reshape(R, -1)
     for r in range(R):
         ref = Dnd @ xv[r]
-        assert np.max(np.abs(got[r] - ref)) < 2e-5 * np.abs(ref).max()
+        assert np.max(np.abs(got[r] - ref)) < tol * np.abs(ref).max(), (path, R, r)
+
+
+@pytest.mark.parametrize("s_odd", [0.0, 0.05])
+def test_coarse_apply_tc_production_shape(s_odd):
+    """24 test vectors per chirality (48x48 complex coarse blocks, the production
+    shape: six 8-row groups, K = 96 per direction), 8 right-hand sides, on a
+    4x4x4x8 lattice with 2^4 aggregates: tensor cores vs the oracle, and vs the
+    FP32 CUDA-core path."""
+    tm = require_gpu()
+    nv = 24
+    dims, bdims = (8, 4, 4, 4), (2, 2, 2, 2)
+    U = synth.random_su3_field(dims, 0.5, 98)
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(4)
+    vecs = (rng.standard_normal((nv, V, 12)) + 1j * rng.standard_normal((nv, V, 12))).astype(np.complex64)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    tv = torch.from_numpy(to_mg_layout(dims, vecs, 12)).cuda()
+    mg = tm.tmnd_mg_create(g.handle, bdims, nv, tv)
+    mgs = tm.tmnd_mg_create(g.handle, bdims, nv, tv, coarse_simt=True)
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    P = oracle.mg_prolongator(dims, bdims, vecs.astype(np.complex128).reshape(nv, V, 4, 3))
+    Dcw = oracle.mg_coarse_wilson(act, U, P)
+    nb = P.shape[1] // (2 * nv)
+    Dnd = _coarse_nd_dense(dict(dims=dims), s_odd, nv, P, Dcw, nb)
+    R = 8
+    xv = rng.standard_normal((R, nb * 4 * nv)) + 1j * rng.standard_normal((R, nb * 4 * nv))
+    xin = torch.from_numpy(xv.astype(np.complex64).ravel()).cuda()
+    y_tc, y_simt = torch.zeros_like(xin), torch.zeros_like(xin)
+    tm.mg_coarse_apply(mg, y_tc, xin, R, s_odd)
+    tm.mg_coarse_apply(mgs, y_simt, xin, 2, s_odd)   # CUDA cores: 2 RHS per launch (thread limit)
+    tm.mg_coarse_apply(mgs, y_simt[2 * nb * 4 * nv:], xin[2 * nb * 4 * nv:], 2, s_odd)
+    got = y_tc.cpu().numpy().reshape(R, -1)
+    gs = y_simt.cpu().numpy().reshape(R, -1)
+    for r in range(R):
+        ref = Dnd @ xv[r]
+        assert np.max(np.abs(got[r] - ref)) < 4e-3 * np.abs(ref).max(), r
+        if r < 4:
+            assert np.max(np.abs(gs[r] - ref)) < 2e-5 * np.abs(ref).max(), r
+    tm.tmnd_mg_destroy(mg)
+    tm.tmnd_mg_destroy(mgs)
+    g.close()
