@@ -7,6 +7,25 @@ Gaussian right-hand side, rho = 1e-10.  A step is one complete multi-shift CG
 solve (all shifts, with the FP64 true-residual certification).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tmnd|reference]
+                    [--form fp64|mixed|batched|hybrid|learned]
+
+--form selects one of the solver forms on its own workload (the default, fp64,
+is the headline above); every form certifies each shift at 1e-10 by its FP64
+true residual:
+  mixed    24^3x48, 12 shifts, 2 RHS one at a time: sloppy FP32/16-bit multi-shift
+           CG + FP64 defect correction
+  batched  32^3x64, 12 shifts, 8 RHS: the same with all 8 RHS in every 16-bit
+           stencil launch
+  hybrid   32^3x64, 12 shifts, 8 RHS: mixed multi-shift CG for the 8 largest,
+           Lagrange guesses and case-C two-level MG (4^4 aggregates, 24 vectors
+           per chirality, coarse operator on the tensor cores) for the 4 smallest
+           (the MG setup is built once per gauge field, outside the timed region)
+  learned  24^3x48, 12 shifts, 1 RHS on an unseen field: mixed multi-shift CG for
+           the 8 largest, learned guesses for the 4 smallest finished by defect
+           correction; the network is trained first on solves of other fields
+           (outside the timed region); the same with Lagrange guesses is reported
+Each form's line also times the plain FP64 multi-shift CG on its workload
+("fp64_same_workload") and reports a roofline for its dominant kernel.
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
 this method here) on the host cores, on a bounded sample of the same workload.
@@ -240,6 +259,196 @@ def run_tmnd(args):
     return out
 
 
+
+FORMS = {
+    "mixed": dict(dims=(48, 24, 24, 24), nrhs=2, seeds=(1003, 2003), lattice="24^3x48"),
+    "batched": dict(dims=(64, 32, 32, 32), nrhs=8, seeds=(1004, 2004), lattice="32^3x64"),
+    "hybrid": dict(dims=(64, 32, 32, 32), nrhs=8, seeds=(1004, 2004), lattice="32^3x64"),
+    "learned": dict(dims=(48, 24, 24, 24), nrhs=1, seeds=(1005, 2005), lattice="24^3x48"),
+}
+# 16-bit stencil, algorithmic bytes per odd site: even launch 392 (in 100, 12-real
+# 16-bit links 192, out 100), odd launch 492 (+ psi 100); Qhat^2 + sigma adds aux 100
+S16_Q2_BYTES_PER_SITE = 2 * (392 + 492) + 100
+
+
+def _timed(step, steps, flush, stream):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    e0.record(stream)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        out.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def s16_roofline(tm, g, flush, stream, reps=20):
+    """CUDA-event time of the sloppy Qhat^2 (4 stencil launches) on the form's lattice."""
+    import torch
+    q = g.spinor(1, prec=tm.TMND_S16)
+    tm.tmnd_spinor_convert(g.handle, q, tm.TMND_S16, g.pack(torch.randn(g.vh * 24, dtype=torch.complex128,
+                                                                          device="cuda").view(1, g.vh, 2, 4, 3)),
+                           tm.TMND_F64)
+    o = g.spinor(1, prec=tm.TMND_S16)
+    for _ in range(3):
+        tm.tm_nd_apply(g.handle, o, q, tm.OP_QHAT2 | tm.OP_S16, 0.01, stream=stream)
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tm.tm_nd_apply(g.handle, o, q, tm.OP_QHAT2 | tm.OP_S16, 0.01, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    peak = _peaks().get("hbm_gbs") or 6800.0
+    gbs = S16_Q2_BYTES_PER_SITE * g.vh / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": "k_hop_even_s16/k_hop_odd_s16 (16-bit stencil, Qhat^2 + sigma: 4 launches)",
+            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if _peaks().get("hbm_gbs") else "fallback 6.8 TB/s",
+            "measured": f"median of {reps} CUDA-event timings of tm_nd_apply(Qhat^2, 16-bit), L2 flushed",
+            "ms_per_qhat2": ms}
+
+
+def run_form(args):
+    """One solver form on its own workload (see the module docstring)."""
+    import numpy as np
+    import torch
+
+    import paper_1805_09584_gb300 as tm
+    import synth
+    from paper_1805_09584_gb300 import _build, learned
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        raise SystemExit("--form runs on one GPU")
+    torch.cuda.set_device(local)
+    _build.build()
+    F = FORMS[args.form]
+    dims, nrhs = F["dims"], F["nrhs"]
+    gseed, bseed = F["seeds"]
+    sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
+    U = synth.random_su3_field(dims, ROUGHNESS, gseed)
+    g = tm.Gauge(U, dims, KAPPA, MU_BAR, EPS_BAR)
+    stream = torch.cuda.current_stream()
+    b_host = synth.gaussian_rhs(dims, bseed, nrhs=nrhs)
+    b_dev = g.pack(torch.from_numpy(b_host).cuda(), nrhs=nrhs)
+    xs = [g.spinor(nrhs) for _ in sig]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    extra = {}
+    mg = net = None
+    if args.form == "hybrid":
+        t0 = time.perf_counter()
+        nv = 24
+        tv = torch.randn(nv * 2 * 12 * g.vh, dtype=torch.complex64, device="cuda")
+        tm.tmnd_mg_smooth_vectors(g.handle, tv, nv, 4)
+        mg = tm.tmnd_mg_create(g.handle, (4, 4, 4, 4), nv, tv)
+        torch.cuda.synchronize()
+        extra["mg_setup_s"] = time.perf_counter() - t0
+        del tv
+    if args.form == "learned":
+        t0 = time.perf_counter()
+        Xs, Ss, Hs = [], [], []
+        for fs in range(4):   # training fields (roughness 0.3..0.7), 2 RHS each
+            gt = tm.Gauge(synth.random_su3_field(dims, 0.3 + 0.1 * fs, 100 + fs), dims, KAPPA, MU_BAR, EPS_BAR)
+            for bk in synth.gaussian_rhs(dims, 200 + fs, nrhs=2):
+                bd = gt.pack(torch.from_numpy(bk[None]).cuda())
+                xn, info, hist = learned.solve_nodes(gt, bd, sig, prec=tm.TMND_S16)
+                X, S, H = learned.samples(gt, bd, sig, xn, info, hist)
+                Xs.append(X); Ss.append(S); Hs.append(H)
+                del xn
+            gt.close()
+        net, losses = learned.train(np.concatenate(Xs), np.concatenate(Ss), np.concatenate(Hs), epochs=600)
+        extra["training"] = {"solves": 8, "samples": 32, "fields": 4, "s": time.perf_counter() - t0,
+                             "loss_first_last": [losses[0], losses[-1]]}
+
+    def step():
+        if args.form in ("mixed", "batched"):
+            return tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs, rho=RHO, prec=tm.TMND_S16,
+                                   batch=1 if args.form == "mixed" else 0, stream=stream)
+        if args.form == "hybrid":
+            return tm.tmnd_hybrid_solve(g.handle, mg, b_dev, nrhs, sig, 8, xs, rho=RHO, prec=tm.TMND_S16,
+                                        n_guess=0, guess=1, stream=stream)
+        return tm.tmnd_hybrid_solve(g.handle, None, b_dev, nrhs, sig, 8, xs, rho=RHO, prec=tm.TMND_S16,
+                                    n_guess=0, guess=2, net=net, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(local)
+    ms, infos = _timed(step, args.steps, flush, stream)
+    clocks = sampler.stop()
+    solves = args.steps * NSHIFT * nrhs
+    value = solves / (ms / 1e3)
+    worst = max(max(i["true_res"]) for i in infos)
+    if args.form == "learned":   # the same with Lagrange guesses (the method without the network)
+        def step_lag():
+            return tm.tmnd_hybrid_solve(g.handle, None, b_dev, nrhs, sig, 8, xs, rho=RHO, prec=tm.TMND_S16,
+                                        n_guess=0, guess=1, stream=stream)
+        step_lag()
+        ms_l, inf_l = _timed(step_lag, args.steps, flush, stream)
+        extra["lagrange_guesses"] = {"value": solves / (ms_l / 1e3), "ms_per_step": ms_l / args.steps,
+                                     "guess_res": inf_l[-1]["guess_res"][8:],
+                                     "refine_iters": inf_l[-1]["refine_iters"],
+                                     "fp64_applies": inf_l[-1]["fp64_applies"]}
+        extra["learned_guesses"] = {"guess_res": infos[-1]["guess_res"][8:], "refine_iters": infos[-1]["refine_iters"],
+                                    "fp64_applies": infos[-1]["fp64_applies"]}
+    # e2e: host buffers in and out through the public API
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    x_pin = torch.empty((NSHIFT, nrhs, g.vh, 2, 4, 3), dtype=torch.complex128).pin_memory()
+    b_can = torch.empty((nrhs, g.vh, 2, 4, 3), dtype=torch.complex128, device="cuda")
+    x_can = torch.empty((nrhs, g.vh, 2, 4, 3), dtype=torch.complex128, device="cuda")
+
+    def step_e2e():
+        b_can.copy_(b_pin, non_blocking=True)
+        tm.tmnd_spinor_pack(g.handle, b_dev, b_can, nrhs, stream)
+        step()
+        for i in range(NSHIFT):
+            tm.tmnd_spinor_unpack(g.handle, x_can, xs[i], nrhs, stream)
+            x_pin[i].copy_(x_can, non_blocking=True)
+    e2e_ms, _ = _timed(step_e2e, args.steps, flush, stream)
+    # the plain FP64 multi-shift CG on the same workload (one step)
+    f64 = lambda: tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs, rho=RHO, stream=stream)
+    f64()
+    f64_ms, _ = _timed(f64, 1, flush, stream)
+    roof = s16_roofline(tm, g, flush, stream)
+    if mg is not None:   # the coarse operator on the tensor cores, all 8 RHS at once
+        nb = g.vh * 2 // 256
+        xc = torch.randn(nrhs * nb * 4 * 24, dtype=torch.complex64, device="cuda")
+        yc = torch.empty_like(xc)
+        tm.mg_coarse_apply(mg, yc, xc, nrhs, 0.0, stream=stream)
+        c_ms, _ = _timed(lambda: tm.mg_coarse_apply(mg, yc, xc, nrhs, 0.0, stream=stream), 10, flush, stream)
+        byts = nb * 9 * 48 * 48 * 8 + 2 * nrhs * nb * 4 * 24 * 8
+        extra["coarse_tc"] = {"ms": c_ms / 10, "GBs": byts / (c_ms / 10 / 1e3) / 1e9, "nrhs": nrhs,
+                              "kernel": "k_coarse_apply_tc (tcgen05 TF32, 48x48 blocks)"}
+    launches = sum(i.get("launches", 0) for i in infos) or None
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/16-bit sloppy + f64 defect correction", "data": "synthetic",
+        "config": {"workload": f"{F['lattice']} ND twisted-mass doublet, {args.form} form, 12 shifts 1e-5..2, "
+                               f"{nrhs} RHS, rho 1e-10", "form": args.form, "lattice": F["lattice"],
+                   "nshift": NSHIFT, "nrhs": nrhs, "rho": RHO, "kappa": KAPPA, "mu_bar": MU_BAR,
+                   "eps_bar": EPS_BAR, "roughness": ROUGHNESS, "parallelism": "single GPU",
+                   "l2": "flushed between steps (512 MB write); solve working set > L2"},
+        "max_true_rel_residual": worst,
+        "fp64_same_workload": {"value": nrhs * NSHIFT / (f64_ms / 1e3), "ms_per_step": f64_ms},
+        "e2e": {"value": solves / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": b_host.nbytes,
+                "d2h_bytes_per_step": NSHIFT * b_host.nbytes},
+        "roofline": roof, "gpu_launches": launches, "clocks": clocks, **extra,
+    }
+    if net is not None:
+        tm.tmnd_mlp_destroy(net)
+    if mg is not None:
+        tm.tmnd_mg_destroy(mg)
+    g.close()
+    return out
+
+
 # FP64 peak of a GB300 (sm_103a): 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -312,11 +521,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tmnd", choices=["tmnd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "batched", "hybrid", "learned"])
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
         if out is not None:
             print(json.dumps(out))
+        return
+    if args.form != "fp64":
+        print(json.dumps(run_form(args)))
         return
     out = run_tmnd(args)
     ws, rank, _ = _dist()

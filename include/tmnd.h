@@ -321,10 +321,13 @@ typedef struct {
     int n_guess;           /* shifts after the n_mms largest iterated along in the multi-shift
                               CG as guesses (Sec. 4.2.2; the paper uses 2) */
     int guess;             /* remaining shifts: 1 = Lagrange guess over the nearest <= 8 solved
-                              shifts (Sec. 4.2.1), 0 = zero start */
+                              shifts (Sec. 4.2.1), 0 = zero start, 2 = learned: weights from `net`
+                              over the solutions of the 8 shifts just above (n_mms >= 8; the
+                              network's features use the first RHS's base-recursion history) */
     double mg_tol;         /* relative tolerance of each case-C MG solve (0 = 1e-4; the solve is
                               FP32, the FP64 defect correction finishes the shift) */
     int mg_maxiter, mg_restart, mg_nu;   /* 0 = 100, 8, 4 */
+    const struct tmnd_mlp *net;          /* guess = 2: a trained network (see tmnd_mlp_*), else NULL */
 } tmnd_hybrid_params;
 
 typedef struct {
@@ -339,6 +342,8 @@ typedef struct {
 /* Hybrid solve of (Qhat^2 + sigma_i) x_i = b (Sec. 4.3): multi-shift CG for
  * the n_mms largest shifts, case-C multigrid solves from guesses for the rest
  * (see above), every shift finished by FP64 defect correction to hp->rho.
+ * mg may be NULL: then the remaining shifts go from their guesses straight to the
+ * defect correction (sloppy CG on the FP64 defect).
  * b, x as in mms_cg_solve (FP64 internal odd spinors).  Synchronous. */
 tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void *b, int nrhs, const double *sigma, int nshift,
                               int n_mms, void *const *x, const tmnd_hybrid_params *hp, tmnd_hybrid_info *info,
@@ -366,7 +371,7 @@ tmnd_status tmnd_mg_export(const tmnd_mg *mg, void *P_host, void *Dc_host, void 
 typedef struct tmnd_mlp tmnd_mlp;
 int tmnd_mlp_num_params(int F);
 /* Parameters initialised from `seed` (Gaussian, scale 1/sqrt(fan-in); last layer x0.1;
- * biases 0; mu = 0, isd = 1). */
+ * biases 0 except b3 = 3 (poles near 20: weights close to Lagrange's); mu = 0, isd = 1). */
 tmnd_status tmnd_mlp_create(int F, unsigned long long seed, tmnd_mlp **out);
 void tmnd_mlp_destroy(tmnd_mlp *m);
 /* Copy the FP32 parameters to host_get and/or set them from host_set (either may be NULL). */

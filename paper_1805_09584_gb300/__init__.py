@@ -58,7 +58,7 @@ class HybridParams(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("maxiter", ctypes.c_int), ("prec", ctypes.c_int),
                 ("rho_inner", ctypes.c_double), ("n_guess", ctypes.c_int), ("guess", ctypes.c_int),
                 ("mg_tol", ctypes.c_double), ("mg_maxiter", ctypes.c_int), ("mg_restart", ctypes.c_int),
-                ("mg_nu", ctypes.c_int)]
+                ("mg_nu", ctypes.c_int), ("net", ctypes.c_void_p)]
 
 
 class HybridInfo(ctypes.Structure):
@@ -317,12 +317,14 @@ def tmnd_mg_smooth_vectors(h, vecs, nvec: int, iters: int, stream=None) -> None:
 def tmnd_hybrid_solve(h, mg, b, nrhs: int, sigma, n_mms: int, x, rho: float = 1e-10, maxiter: int = 100000,
                       prec: int = TMND_F64, rho_inner: float = 0.0, n_guess: int = 2, guess: int = 1,
                       mg_tol: float = 0.0, mg_maxiter: int = 0, mg_restart: int = 0, mg_nu: int = 0,
-                      stream=None) -> dict:
+                      net=None, stream=None) -> dict:
+    """mg may be None (no multigrid: guesses go straight to the FP64 defect correction);
+    guess = 2 with a trained network `net` (tmnd_mlp_create) uses learned weights."""
     sig = np.ascontiguousarray(sigma, dtype=np.float64)
     ns = len(sig)
     xs = (ctypes.c_void_p * ns)(*[_ptr(v) for v in x])
     p = HybridParams(float(rho), int(maxiter), int(prec), float(rho_inner), int(n_guess), int(guess), float(mg_tol),
-                     int(mg_maxiter), int(mg_restart), int(mg_nu))
+                     int(mg_maxiter), int(mg_restart), int(mg_nu), net)
     info = HybridInfo()
     st = lib().tmnd_hybrid_solve(h, mg, _ptr(b), int(nrhs), sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns,
                                  int(n_mms), xs, ctypes.byref(p), ctypes.byref(info), _stream(stream))

@@ -297,6 +297,8 @@ extern "C" tmnd_status tmnd_mlp_create(int F, unsigned long long seed, tmnd_mlp 
     for (int i = 0; i < MLP_H * F; i++) h[off_W1(F) + i] = (float)(r.normal() / sqrt((double)F));
     for (int i = 0; i < MLP_H * MLP_H; i++) h[off_W2(F) + i] = (float)(r.normal() / sqrt((double)MLP_H));
     for (int i = 0; i < MLP_P * MLP_H; i++) h[off_W3(F) + i] = (float)(0.1 * r.normal() / sqrt((double)MLP_H));
+    // poles start near e^3 = 20, far above the shifts: the initial weights are close to Lagrange's
+    for (int k = 0; k < MLP_P; k++) h[off_b3(F) + k] = 3.0f;
     if (e == cudaSuccess) e = cudaMemcpy(m->theta, h.data(), b, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->grad, 0, b);
     if (e == cudaSuccess) e = cudaMemset(m->m, 0, b);

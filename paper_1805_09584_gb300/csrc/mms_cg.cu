@@ -1196,7 +1196,10 @@ __global__ void k_g5tau1(int Vh, const double2 *__restrict__ in, double2 *__rest
 extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void *b, int nrhs, const double *sigma,
                                          int nshift, int n_mms, void *const *x, const tmnd_hybrid_params *hp,
                                          tmnd_hybrid_info *hinfo, void *stream) {
-    TMND_ARG_CHECK(g && mg && b && sigma && x && hp, "tmnd_hybrid_solve: NULL argument");
+    TMND_ARG_CHECK(g && b && sigma && x && hp, "tmnd_hybrid_solve: NULL argument");
+    TMND_ARG_CHECK(hp->guess >= 0 && hp->guess <= 2, "tmnd_hybrid_solve: guess = %d not in {0, 1, 2}", hp->guess);
+    TMND_ARG_CHECK(hp->guess != 2 || (hp->net && n_mms >= 8),
+                   "tmnd_hybrid_solve: learned guesses need a network and n_mms >= 8");
     TMND_ARG_CHECK(nshift >= 1 && nshift <= TMND_MAX_SHIFTS && n_mms >= 1 && n_mms <= nshift && nrhs >= 1,
                    "tmnd_hybrid_solve: bad shift counts");
     for (int i = 0; i < nshift; i++)
@@ -1215,6 +1218,13 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
     sp1.nsolve = n_mms;
     sp1.prec = hp->prec;
     sp1.rho_inner = hp->rho_inner;
+    // scalar history of the base recursion (first RHS): the network's Lanczos features
+    std::vector<double> hist;
+    if (hp->guess == 2) {
+        hist.assign(2 * (size_t)(hp->maxiter < 4096 ? hp->maxiter : 4096), 0.0);
+        sp1.ab_hist = hist.data();
+        sp1.ab_hist_len = (int)hist.size();
+    }
     tmnd_solve_info si = {};
     tmnd_status st = mms_cg_solve(g, b, nrhs, sigma, nmms_all, x, &sp1, &si, stream);
     if (st != TMND_OK) return st;
@@ -1226,13 +1236,46 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
         for (int i = 0; i < n_mms; i++) hinfo->true_res[i] = si.true_res[i];
     }
     if (n_mms == nshift) return TMND_OK;
+    // learned weights (one set for all RHS: the features are the shifts and the first RHS's history)
+    std::vector<double> lw;
+    const int n_learn = nshift - nmms_all;
+    if (hp->guess == 2 && n_learn > 0) {
+        // target i: nodes = the 8 shifts just above it (solved before it), features from the
+        // history of the multi-shift solve with base shift sigma[n_mms - 1]
+        std::vector<float> X((size_t)n_learn * 20);
+        std::vector<double> S((size_t)n_learn * 9);
+        for (int q = 0; q < n_learn; q++) {
+            const int i = nmms_all + q;
+            const double *nodes = sigma + (i - 8);
+            st = tmnd_mlp_features(nodes, sigma[i], hist.data(), si.iters, sigma[n_mms - 1], &X[(size_t)q * 20]);
+            if (st != TMND_OK) return st;
+            S[(size_t)q * 9] = sigma[i];
+            for (int j = 0; j < 8; j++) S[(size_t)q * 9 + 1 + j] = nodes[j];
+        }
+        char *dbuf = nullptr;
+        const size_t xb = sizeof(float) * X.size(), sb = sizeof(double) * S.size(), wb = sizeof(double) * 8 * n_learn;
+        TMND_CUDA_TRY(cudaMalloc(&dbuf, xb + sb + wb + 64));
+        double *dS = (double *)(dbuf + ((xb + 15) & ~(size_t)15)), *dW = dS + S.size();
+        lw.resize((size_t)8 * n_learn);
+        cudaError_t ce = cudaMemcpy(dbuf, X.data(), xb, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(dS, S.data(), sb, cudaMemcpyHostToDevice);
+        tmnd_status ps = ce == cudaSuccess ? tmnd_mlp_predict((tmnd_mlp *)hp->net, dbuf, dS, n_learn, dW, nullptr)
+                                           : TMND_ERR_CUDA;
+        if (ps == TMND_OK) ce = cudaMemcpy(lw.data(), dW, wb, cudaMemcpyDeviceToHost);
+        cudaFree(dbuf);
+        if (ps != TMND_OK) return ps;
+        if (ce != cudaSuccess) {
+            tmnd_set_error("tmnd_hybrid_solve: %s", cudaGetErrorString(ce));
+            return TMND_ERR_CUDA;
+        }
+    }
     // 2. the remaining shifts one by one
     const double rho_inner = hp->rho_inner > 0 ? hp->rho_inner : 1e-5;
     st = tmnd_ensure_workspace(g, mixed_work_bytes(Vh, 1));
     if (st != TMND_OK) return st;
     const long nfull = 2 * n;  // full-lattice FP32 doublet (complex numbers)
     const size_t f32b = sizeof(float2) * nfull;
-    const size_t scratch_b = 3 * sp + 4 * f32b + mg_gcr_scratch_bytes(mg, hp->mg_restart > 0 ? hp->mg_restart : 8);
+    const size_t scratch_b = 3 * sp + 4 * f32b + (mg ? mg_gcr_scratch_bytes(mg, hp->mg_restart > 0 ? hp->mg_restart : 8) : 0);
     char *scr = nullptr;
     TMND_CUDA_TRY(cudaMalloc(&scr, scratch_b));
     double2 *tq = (double2 *)scr, *te = (double2 *)(scr + sp), *gb = (double2 *)(scr + 2 * sp);
@@ -1280,7 +1323,12 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
         for (int i = n_mms; i < nshift && res_status == TMND_OK; i++) {
             // guess
             if (i >= nmms_all) {
-                if (hp->guess >= 1) {
+                if (hp->guess == 2) {
+                    const void *xs[8];
+                    for (int j = 0; j < 8; j++) xs[j] = xk[i - 8 + j];
+                    st = tmnd_lincomb(g, &lw[(size_t)8 * (i - nmms_all)], xs, 8, xk[i], 1, s);
+                    if (st != TMND_OK) { res_status = st; break; }
+                } else if (hp->guess == 1) {
                     const int kk = i < 8 ? i : 8;
                     const void *xs[8];
                     for (int j = 0; j < kk; j++) xs[j] = xk[i - kk + j];
@@ -1296,7 +1344,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
             if (hinfo && k == 0) hinfo->guess_res[i] = sqrt(rr0 / bb);
             const double sq = sqrt(sigma[i]);
             int mg_it = 0;
-            if (sqrt(rr0 / bb) > hp->rho) {
+            if (mg && sqrt(rr0 / bb) > hp->rho) {
                 for (int sgn = 1; sgn >= -1; sgn -= 2) {
                     float2 *y = sgn > 0 ? yp : ym;
                     // odd guess (Qhat - sgn i s) x~ ; Qhat = g5 t1 Mhat
@@ -1341,7 +1389,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
     cudaEventDestroy(e0);
     cudaStreamDestroy(s);
     cudaFree(scr);
-    if (res_status == TMND_OK) res_status = tmnd_mg_tc_status(mg);
+    if (res_status == TMND_OK && mg) res_status = tmnd_mg_tc_status(mg);
     if (res_status == TMND_OK && fin != cudaSuccess) {
         tmnd_set_error("tmnd_hybrid_solve: %s", cudaGetErrorString(fin));
         return TMND_ERR_CUDA;

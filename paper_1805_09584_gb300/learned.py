@@ -3,9 +3,9 @@
 Host orchestration only: every arithmetic step runs in libtmnd (multi-shift CG
 with its scalar history, Gram matrices, network features, forward/backward
 kernels, Adam, BF16 inference, linear combinations).  The guess for a target
-shift sigma_t is sum_j w_j x_j over the solutions of the 8 largest shifts
-(solved by the multi-shift CG), with w from Lagrange interpolation (Sec. 4.2.1)
-or from the network, whose two predicted poles p_k give
+shift sigma_t is sum_j w_j x_j over the solutions of the 8 solved shifts just
+above it, with w from Lagrange interpolation (Sec. 4.2.1) or from the network,
+whose two predicted poles p_k give
     w_j = l_j(sigma_t) prod_k (p_k + sigma_j) / (p_k + sigma_t);
 the network is trained on
     loss = mean log(w^T H w + floor),  H = Re(D G D),  G_jk = <x_j, x_k>/|b|^2,
@@ -22,25 +22,36 @@ import paper_1805_09584_gb300 as tm
 NODES = 8
 
 
-def solve_nodes(g, b_dev, sigma, rho=1e-10, maxiter=20000):
-    """Multi-shift CG on the 8 largest shifts; returns (solutions, info, scalar history)."""
+def solve_nodes(g, b_dev, sigma, rho=1e-10, maxiter=20000, prec=None):
+    """Solutions of every shift, the way the hybrid solve produces them: one
+    multi-shift CG on the 8 largest shifts (its scalar history and iteration count
+    are the network's features) and one on the rest.  Returns (solutions of all
+    shifts, info of the first solve, its scalar history).  prec = TMND_S16 gives
+    the history of the sloppy solve, as the mixed hybrid solve sees it."""
     import torch
-    xs = [g.spinor() for _ in range(NODES)]
-    hist = np.zeros(2 * maxiter, np.float64)
-    info = tm.mms_cg_solve(g.handle, b_dev, 1, sigma[:NODES], xs, rho=rho, maxiter=maxiter, ab_hist=hist)
+    pr = tm.TMND_F64 if prec is None else prec
+    xs = [g.spinor() for _ in sigma]
+    hist = np.zeros(2 * min(maxiter, 4096), np.float64)
+    info = tm.mms_cg_solve(g.handle, b_dev, 1, sigma[:NODES], xs[:NODES], rho=rho, maxiter=maxiter, ab_hist=hist,
+                           prec=pr)
+    if len(sigma) > NODES:
+        tm.mms_cg_solve(g.handle, b_dev, 1, sigma[NODES:], xs[NODES:], rho=rho, maxiter=maxiter, prec=pr)
     torch.cuda.synchronize()
     return xs, info, hist
 
 
 def samples(g, b_dev, sigma, xs, info, hist):
     """Network inputs X [T, 20] (float32), shifts S [T, 9] = (sigma_t, nodes) and loss
-    matrices H [T, 8, 8] (float64) for the targets sigma[8:]."""
-    nodes = np.asarray(sigma[:NODES], np.float64)
+    matrices H [T, 8, 8] (float64) for the targets sigma[8:], each over the 8 shifts
+    just above it (the nearest solved ones, as the Lagrange guess of Sec. 4.2.1 uses);
+    the Lanczos features come from the history of the solve with base shift sigma[7]."""
+    sigma = np.asarray(sigma, np.float64)
     bb = float(tm.tmnd_gram(g.handle, [b_dev])[0, 0].real)
-    G = tm.tmnd_gram(g.handle, xs) / bb
     feats, Ss, Hs = [], [], []
-    for t in sigma[NODES:]:
-        feats.append(tm.tmnd_mlp_features(nodes, float(t), hist, info["iters"], float(nodes[-1])))
+    for q, t in enumerate(sigma[NODES:]):
+        nodes = sigma[q:q + NODES]
+        G = tm.tmnd_gram(g.handle, xs[q:q + NODES]) / bb
+        feats.append(tm.tmnd_mlp_features(nodes, float(t), hist, info["iters"], float(sigma[NODES - 1])))
         Ss.append(np.concatenate([[float(t)], nodes]))
         d = float(t) - nodes
         Hs.append(np.real(d[:, None] * G * d[None, :]))

@@ -39,3 +39,39 @@ def test_hybrid_certified(prec):
     assert all(0 < r < 1 for r in info["guess_res"][6:]), info
     tm.tmnd_mg_destroy(mg)
     g.close()
+
+
+def test_hybrid_learned_and_lagrange_guesses_without_mg():
+    """No multigrid: the 4 smallest shifts start from Lagrange (guess 1) or
+    learned (guess 2, a network trained here on solves of other fields) guesses
+    and finish by FP64 defect correction; every shift certified by the oracle."""
+    tm = require_gpu()
+    from paper_1805_09584_gb300 import learned
+    dims = (4, 4, 4, 4)
+    sig = synth.shift_set(12, 1e-5, 2.0)
+    Xs, Ss, Hs = [], [], []
+    for fs in range(4):
+        gauge = tm.Gauge(synth.random_su3_field(dims, 0.3 + 0.1 * fs, 300 + fs), dims, KAPPA, MU, EPS)
+        for k, bk in enumerate(synth.gaussian_rhs(dims, 400 + fs, nrhs=2)):
+            bd = gauge.pack(torch.from_numpy(bk[None]).cuda())
+            xs, info, hist = learned.solve_nodes(gauge, bd, sig, prec=tm.TMND_S16)
+            X, S, H = learned.samples(gauge, bd, sig, xs, info, hist)
+            Xs.append(X); Ss.append(S); Hs.append(H)
+        gauge.close()
+    net, _ = learned.train(np.concatenate(Xs), np.concatenate(Ss), np.concatenate(Hs), epochs=300)
+    U = synth.random_su3_field(dims, 0.45, 333)
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    b = synth.gaussian_rhs(dims, 444, nrhs=2)
+    bi = g.pack(torch.from_numpy(b).cuda(), nrhs=2)
+    for guess, kw in ((1, {}), (2, {"net": net})):
+        xs = [g.spinor(2) for _ in sig]
+        info = tm.tmnd_hybrid_solve(g.handle, None, bi, 2, sig, 8, xs, prec=tm.TMND_S16, n_guess=0, guess=guess, **kw)
+        for i, s in enumerate(sig):
+            x = g.unpack(xs[i], 2).cpu().numpy()
+            for k in range(2):
+                tr = oracle.true_residual(act, U, b[k], x[k], s)
+                assert tr <= 1.01e-10, (guess, i, k, tr, info)
+        assert all(0 < r < 1e-3 for r in info["guess_res"][8:]), (guess, info)
+    tm.tmnd_mlp_destroy(net)
+    g.close()
