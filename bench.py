@@ -27,6 +27,13 @@ true residual:
 Each form's line also times the plain FP64 multi-shift CG on its workload
 ("fp64_same_workload") and reports a roofline for its dominant kernel.
 
+--kernel fp64|s16|coarse times one kernel family alone (CUDA events, L2 flushed
+between applications) and prints its achieved rate against the roofline:
+  fp64    FP64 Qhat^2 + sigma (4 stencil launches), 16^3x32
+  s16     16-bit Qhat^2 + sigma (4 stencil launches), 24^3x48, 1 and 8 RHS per launch
+  coarse  coarse doublet operator, tensor cores and CUDA cores, 24^3x48 with 4^4
+          aggregates and 24 vectors per chirality, 1 and 8 RHS
+
 --impl reference times the FP64 CPU oracle (the only other implementation of
 this method here) on the host cores, on a bounded sample of the same workload.
 Under torchrun (N > 1) every rank solves its own right-hand side (replicas: the
@@ -63,6 +70,13 @@ L2_FLUSH_BYTES = 512 << 20         # > 129 MB L2
 #   odd launch 288 reals (t 48, psi 48, links 144, out 48)
 HOP_FLOP_PER_SITE = 2 * 1320 + 240
 HOP_BYTES_PER_SITE = (240 + 288) / 2 * 8
+# DRAM bytes of one odd-site FP64 stencil launch at 16^3x32, one ncu capture of this kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum: 132.87 MB + 9.04 MB)
+FP64_ODD_LAUNCH_TRAFFIC = 132.866816e6 + 9.036288e6
+# DRAM bytes of the 16-bit stencil at 24^3x48 (V/2 = 331776), one ncu capture: even launch
+# 98.22 + 3.71 MB, odd launch 134.10 + 7.79 MB; Qhat^2 = 2 even + 2 odd launches
+S16_Q2_TRAFFIC_24 = 2 * (98.223360e6 + 3.709952e6) + 2 * (134.103296e6 + 7.787264e6)
+S16_TRAFFIC_VH = 331776
 
 
 def _dist():
@@ -241,7 +255,8 @@ def run_tmnd(args):
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "kernel": "k_hop_even/k_hop_odd (FP64 stencil)",
                          "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / fp64_peak, "traffic": None,
+                         "frac": achieved_tflops / fp64_peak, "traffic": FP64_ODD_LAUNCH_TRAFFIC,
+                         "traffic_note": "DRAM bytes per odd-site launch (ncu capture of this kernel, this workload)",
                          "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
                          "hop_share_of_step": hop_ms / prof_ms,
                          "measured": "CUDA events around every iteration's 4 stencil launches of a profiled "
@@ -308,8 +323,12 @@ def s16_roofline(tm, g, flush, stream, reps=20):
     ms = statistics.median(ts)
     peak = _peaks().get("hbm_gbs") or 6800.0
     gbs = S16_Q2_BYTES_PER_SITE * g.vh / (ms / 1e3) / 1e9
+    scaled = g.vh != S16_TRAFFIC_VH
     return {"bound": "hbm", "kernel": "k_hop_even_s16/k_hop_odd_s16 (16-bit stencil, Qhat^2 + sigma: 4 launches)",
-            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "traffic": S16_Q2_TRAFFIC_24 * g.vh / S16_TRAFFIC_VH,
+            "traffic_note": "DRAM bytes per Qhat^2 from an ncu capture at 24^3x48 (2 even + 2 odd launches)"
+                            + (", scaled by the number of sites" if scaled else ""),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if _peaks().get("hbm_gbs") else "fallback 6.8 TB/s",
             "measured": f"median of {reps} CUDA-event timings of tm_nd_apply(Qhat^2, 16-bit), L2 flushed",
             "ms_per_qhat2": ms}
@@ -449,6 +468,85 @@ def run_form(args):
     return out
 
 
+
+def run_kernel(args):
+    """One kernel family alone on its workload lattice (see the module docstring)."""
+    import torch
+
+    import paper_1805_09584_gb300 as tm
+    import synth
+    from paper_1805_09584_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    peak_hbm = _peaks().get("hbm_gbs") or 6800.0
+    reps = max(args.steps, 10)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    out = {"kernel": args.kernel, "reps": reps, "timing": "median of CUDA-event timings, L2 flushed between"}
+    if args.kernel == "fp64":
+        dims = DIMS
+        g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, GAUGE_SEED), dims, KAPPA, MU_BAR, EPS_BAR)
+        x = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, RHS_SEED)).cuda())
+        y = g.spinor()
+        ms = timed(lambda: tm.tm_nd_apply(g.handle, y, x, tm.OP_QHAT2, 0.01, stream=stream))
+        tf = 4 * HOP_FLOP_PER_SITE * g.vh / (ms / 1e3) / 1e12
+        out.update(lattice="16^3x32", ms_qhat2=ms, tflops=tf, fp64_peak_tflops=FP64_PEAK_TFLOPS,
+                   frac=tf / FP64_PEAK_TFLOPS, gbs=4 * HOP_BYTES_PER_SITE * g.vh / (ms / 1e3) / 1e9)
+    elif args.kernel == "s16":
+        dims = (48, 24, 24, 24)
+        g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
+        for R in (1, 8):
+            b = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, 2003, nrhs=R)).cuda(), nrhs=R)
+            q = g.convert(b, tm.TMND_F64, tm.TMND_S16, nrhs=R)
+            o = g.spinor(R, prec=tm.TMND_S16)
+            del b
+            ms = timed(lambda: tm.tm_nd_apply(g.handle, o, q, tm.OP_QHAT2 | tm.OP_S16, 0.01, nrhs=R, stream=stream))
+            # links are read once per launch for all R right-hand sides
+            byts = g.vh * (R * (2 * (200 + 300) + 100) + 4 * 192)
+            out[f"nrhs{R}"] = {"ms_qhat2": ms, "ms_per_rhs": ms / R, "gbs": byts / (ms / 1e3) / 1e9,
+                               "frac_hbm": byts / (ms / 1e3) / 1e9 / peak_hbm}
+        out.update(lattice="24^3x48", hbm_peak_gbs=peak_hbm)
+    else:
+        dims, nv = (48, 24, 24, 24), 24
+        g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
+        tv = torch.randn(nv * 2 * 12 * g.vh, dtype=torch.complex64, device="cuda")
+        tm.tmnd_mg_smooth_vectors(g.handle, tv, nv, 4)
+        mg = tm.tmnd_mg_create(g.handle, (4, 4, 4, 4), nv, tv)
+        mgs = tm.tmnd_mg_create(g.handle, (4, 4, 4, 4), nv, tv, coarse_simt=True)
+        del tv
+        nb = 2 * g.vh // 256
+        for R in (1, 8):
+            xc = torch.randn(R * nb * 4 * nv, dtype=torch.complex64, device="cuda")
+            yc = torch.empty_like(xc)
+            byts = nb * 9 * (2 * nv) ** 2 * 8 + 2 * R * nb * 4 * nv * 8
+            for name, h in (("tc", mg), ("simt", mgs)):
+                ms = timed(lambda: tm.mg_coarse_apply(h, yc, xc, R, 0.0, stream=stream))
+                out[f"{name}_nrhs{R}"] = {"ms": ms, "gbs": byts / (ms / 1e3) / 1e9,
+                                          "frac_hbm": byts / (ms / 1e3) / 1e9 / peak_hbm}
+        out.update(lattice="24^3x48, 4^4 aggregates, 24 vectors per chirality", hbm_peak_gbs=peak_hbm)
+        tm.tmnd_mg_destroy(mg)
+        tm.tmnd_mg_destroy(mgs)
+    g.close()
+    return out
+
+
 # FP64 peak of a GB300 (sm_103a): 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -522,7 +620,11 @@ def main():
     ap.add_argument("--impl", default="tmnd", choices=["tmnd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "batched", "hybrid", "learned"])
+    ap.add_argument("--kernel", default=None, choices=["fp64", "s16", "coarse"])
     args = ap.parse_args()
+    if args.kernel:
+        print(json.dumps(run_kernel(args)))
+        return
     if args.impl == "reference":
         out = run_reference(args)
         if out is not None:
