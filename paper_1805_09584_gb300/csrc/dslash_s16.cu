@@ -370,7 +370,8 @@ __global__ void __launch_bounds__(S16_THREADS, S16_MINB) k_hop_odd_s16(Geom g, S
         for (int k = 0; k < bt.nrhs; k++) {
             const double yy = block_reduce_partials(ea.part_in + (size_t)(2 * k) * ea.npart_in, ea.npart_in, red);
             const double pp = block_reduce_partials(ea.part_in + (size_t)(2 * k + 1) * ea.npart_in, ea.npart_in, red);
-            if (threadIdx.x == 0) alpha_s[k] = (float)(ea.rr[(size_t)k * ea.rr_stride] / (yy + ea.sigma * pp));
+            const double sg = ea.per_rhs_sigma ? ea.sigma_k[k] : ea.sigma;
+            if (threadIdx.x == 0) alpha_s[k] = (float)(ea.rr[(size_t)k * ea.rr_stride] / (yy + sg * pp));
         }
     }
     if (SUMS)
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(S16_THREADS, S16_MINB) k_hop_odd_s16(Geom g, S
             store_site(out.q, out.nrm, Vh, h, y);
         } else {  // EPI_MMS_R: w = y + sigma aux; r' = r - alpha w (FP32 planes); aux streamed
             const S16In aux = s16_at(ea.aux, k * bt.stride);
-            const float sa = (float)ea.sigma * __ldg(&aux.nrm[h]);
+            const float sa = (float)(ea.per_rhs_sigma ? ea.sigma_k[k] : ea.sigma) * __ldg(&aux.nrm[h]);
             const float alpha = alpha_s[k];
             const float2 *rin = ea.r_in + k * ea.r_stride;
             float2 *rout = ea.r + k * ea.r_stride;

@@ -127,11 +127,26 @@ __global__ void k_init_state(MMSState *st, const double *__restrict__ part, int 
     init_state(st, part, npart, c, red);
 }
 
+// Per-right-hand-side base shift and tolerance (batched single-shift solves, nshift = 1)
+struct BatchConst {
+    int on;
+    double sigma0[TMND_MAX_BATCH], rho2[TMND_MAX_BATCH];
+};
+__device__ __forceinline__ MMSConst const_of(const MMSConst &c, const BatchConst &bc, int k) {
+    MMSConst r = c;
+    if (bc.on) {
+        r.sigma0 = bc.sigma0[k];
+        r.rho2 = bc.rho2[k];
+    }
+    return r;
+}
+
 // batched: block k initialises right-hand side k from partials [k][npart]
 __global__ void k_init_state_b(MMSState *st, size_t st_stride, const double *__restrict__ part, int npart,
-                               MMSConst c) {
+                               MMSConst c, BatchConst bc) {
     __shared__ double red[40];
-    init_state((MMSState *)((char *)st + blockIdx.x * st_stride), part + (size_t)blockIdx.x * npart, npart, c, red);
+    const MMSConst ck = const_of(c, bc, blockIdx.x);
+    init_state((MMSState *)((char *)st + blockIdx.x * st_stride), part + (size_t)blockIdx.x * npart, npart, ck, red);
 }
 
 // Scalar step of the recursion (one block; thread 0 does the arithmetic).
@@ -215,11 +230,12 @@ __global__ void k_scalars(MMSState *st, MMSCoef *cf, const double *__restrict__ 
 // scalar history is kept for k = 0.
 __global__ void k_scalars_b(MMSState *st, MMSCoef *cf, size_t st_stride, size_t cf_stride,
                             const double *__restrict__ part_norm, int nb_hop, const double *__restrict__ part_rr,
-                            MMSConst c, int j, double *hist, int hist_cap) {
+                            MMSConst c, BatchConst bc, int j, double *hist, int hist_cap) {
     __shared__ double red[40];
     const int k = blockIdx.x;
+    const MMSConst ck = const_of(c, bc, k);
     scalars_step((MMSState *)((char *)st + k * st_stride), (MMSCoef *)((char *)cf + k * cf_stride),
-                 part_norm + (size_t)2 * k * nb_hop, nb_hop, part_rr + (size_t)k * nb_hop, c, j,
+                 part_norm + (size_t)2 * k * nb_hop, nb_hop, part_rr + (size_t)k * nb_hop, ck, j,
                  k == 0 ? hist : nullptr, hist_cap, red);
 }
 
@@ -806,9 +822,11 @@ static MixedWork mixed_work(void *base, int Vh, int nshift, int nrhs = 1) {
 // right-hand sides iterate in lockstep: each stencil launch covers all of them,
 // each has its own scalars and stops on its own (later launches skip it), and the
 // loop ends when all are done.  hs receives the final state of each.
+// With sig_k / rho_k (nshift = 1): right-hand side k solves (Qhat^2 + sig_k[k]) e = b_k to rho_k[k].
 static tmnd_status mms_sloppy(tmnd_gauge *g, const MixedWork &m, const double *sigma, int nshift, int nsolve,
                               double rho, int maxiter, int check_every, int profile, cudaStream_t s,
-                              std::vector<MMSState> &hs, LoopOut &lo, double *hist = nullptr, int hist_cap = 0) {
+                              std::vector<MMSState> &hs, LoopOut &lo, double *hist = nullptr, int hist_cap = 0,
+                              const double *sig_k = nullptr, const double *rho_k = nullptr) {
     const int Vh = g->geom.Vh;
     const long n = 24L * Vh;
     const int R = m.nrhs;
@@ -833,6 +851,14 @@ static tmnd_status mms_sloppy(tmnd_gauge *g, const MixedWork &m, const double *s
     c.sigma0 = sigma[nsolve - 1];
     for (int i = 0; i < nshift; i++) c.delta[i] = sigma[i] - c.sigma0;
     c.rho2 = rho * rho;
+    BatchConst bc = {};
+    if (sig_k) {
+        bc.on = 1;
+        for (int k = 0; k < R; k++) {
+            bc.sigma0[k] = sig_k[k];
+            bc.rho2[k] = rho_k[k] * rho_k[k];
+        }
+    }
     SloppyVecs v = m.v;
     v.nshift = nshift;
     const S16Out p16 = v.p16, y16 = s16_out(m.y16, Vh), te16 = s16_out(m.te16, Vh);
@@ -844,7 +870,7 @@ static tmnd_status mms_sloppy(tmnd_gauge *g, const MixedWork &m, const double *s
     bt.rdone_stride = (int)(st_stride / sizeof(int));
 
     k_init_s<<<dim3(nb_site, R), 128, 0, s>>>(Vh, v, part_str);
-    k_init_state_b<<<R, 256, 0, s>>>(st, st_stride, part_str, nb_site, c);
+    k_init_state_b<<<R, 256, 0, s>>>(st, st_stride, part_str, nb_site, c, bc);
     k_all_done<<<1, 1, 0, s>>>(st, st_stride, R, done_all);
     TMND_CUDA_TRY(cudaGetLastError());
 
@@ -869,9 +895,11 @@ static tmnd_status mms_sloppy(tmnd_gauge *g, const MixedWork &m, const double *s
         e2.rr = &st->rr;
         e2.rr_stride = (int)(st_stride / sizeof(double));
         e2.done = done_all;
+        e2.per_rhs_sigma = bc.on;
+        for (int q = 0; q < R && bc.on; q++) e2.sigma_k[q] = bc.sigma0[q];
         launch_hop_odd_s16(g->geom, g->stf, g->links_s16, y16i, te16i, S16Out{}, true, EPI_MMS_R, e2, s, bt);
         mark(1);
-        k_scalars_b<<<R, 256, 0, s>>>(st, cf, st_stride, cf_stride, part_norm, nb_hop, part_rr, c, j, hist,
+        k_scalars_b<<<R, 256, 0, s>>>(st, cf, st_stride, cf_stride, part_norm, nb_hop, part_rr, c, bc, j, hist,
                                       hist_cap);
         k_all_done<<<1, 1, 0, s>>>(st, st_stride, R, done_all);
         k_pupdate_s<<<dim3(nb_site, R), 128, 0, s>>>(Vh, cf, cf_stride, v, j);
@@ -933,69 +961,103 @@ struct RefineStats {
     double hop_ms = 0, upd_ms = 0;
 };
 
-// FP64 defect correction of the shifts in `todo` (Sec. 3.1 stopping rule on
-// the true residual): per round and shift, r = b - (Qhat^2 + sigma_i) x_i in
-// FP64; stop the shift if |r| <= rho |b|, else solve (Qhat^2 + sigma_i) e = r
-// with the sloppy CG to the tolerance the target needs and add e in FP64.
-// res[i] receives the final FP64 relative residuals.
-static tmnd_status defect_correct(tmnd_gauge *g, const MixedWork &m, const double2 *b, double2 *const *xk,
-                                  const double *sigma, std::vector<int> todo, double bb, double rho,
+// FP64 defect correction (Sec. 3.1 stopping rule on the true residual) of a set of
+// (right-hand side, shift) pairs: per round, each pending pair's defect
+// r = b - (Qhat^2 + sigma) x in FP64; a pair stops once |r| <= rho |b|; the others
+// solve (Qhat^2 + sigma) e = r together in one batched sloppy CG (up to
+// TMND_MAX_BATCH pairs per launch, each with its own shift and the tolerance its
+// defect needs) and add e in FP64.  *res receives each pair's final FP64 relative
+// residual.  The sloppy solve's vectors are laid out over the workspace at base.
+struct DCItem {
+    const double2 *b;
+    double2 *x;
+    double sigma, bb;
+    double *res;
+};
+
+static tmnd_status defect_correct(tmnd_gauge *g, void *base, std::vector<DCItem> todo, double rho,
                                   double rho_inner, int maxiter, int check_every, int profile, cudaStream_t s,
-                                  std::vector<double> &res, RefineStats &rs) {
+                                  RefineStats &rs, int max_batch) {
     const int Vh = g->geom.Vh;
     const long n = 24L * Vh;
     const int max_rounds = 8;
     tmnd_status st;
+    if (max_batch < 1) max_batch = 1;
+    if (max_batch > TMND_MAX_BATCH) max_batch = TMND_MAX_BATCH;
     for (int round = 0; !todo.empty(); round++) {
-        std::vector<int> next;
-        for (int i : todo) {
-            double rr = 0;
-            st = fp64_defect(g, m, b, xk[i], sigma[i], s, &rr);
-            if (st != TMND_OK) return st;
-            rs.fp64++;
-            rs.launches += 5;
-            res[i] = sqrt(rr / bb);
-            if (!isfinite(res[i])) {
-                tmnd_set_error("solve: NaN/Inf in the FP64 defect of shift %d", i);
-                return TMND_ERR_NAN;
+        std::vector<DCItem> next;
+        size_t q = 0;
+        while (q < todo.size()) {
+            // defects of up to max_batch pending pairs, each converted into its sloppy slot
+            const MixedWork mw = mixed_work(base, Vh, 1, max_batch);
+            std::vector<DCItem> chunk;
+            std::vector<double> sg, tl;
+            for (; q < todo.size() && (int)chunk.size() < max_batch; q++) {
+                DCItem &it = todo[q];
+                double rr = 0;
+                st = fp64_defect(g, mw, it.b, it.x, it.sigma, s, &rr);
+                if (st != TMND_OK) return st;
+                rs.fp64++;
+                rs.launches += 5;
+                *it.res = sqrt(rr / it.bb);
+                if (!isfinite(*it.res)) {
+                    tmnd_set_error("solve: NaN/Inf in an FP64 defect (shift %g)", it.sigma);
+                    return TMND_ERR_NAN;
+                }
+                if (*it.res <= rho) continue;
+                if (round >= max_rounds) {
+                    tmnd_set_error("solve: shift %g not converged after %d defect-correction rounds (residual %g)",
+                                   it.sigma, max_rounds, *it.res);
+                    return TMND_ERR_NOCONV;
+                }
+                st = convert_spinor(Vh, mw.b32((int)chunk.size()), TMND_F32, mw.r64, TMND_F64, 1, s);
+                if (st != TMND_OK) return st;
+                const double need = 0.3 * rho / *it.res;
+                sg.push_back(it.sigma);
+                tl.push_back(need > rho_inner ? need : rho_inner);
+                chunk.push_back(it);
             }
-            if (res[i] <= rho) continue;
-            if (round >= max_rounds) {
-                next.push_back(i);
-                continue;
-            }
-            const MixedWork m1 = m.single();
-            st = convert_spinor(Vh, m1.b32(0), TMND_F32, m.r64, TMND_F64, 1, s);
-            if (st != TMND_OK) return st;
-            const double need = 0.3 * rho / res[i];
-            const double tol = need > rho_inner ? need : rho_inner;
+            if (chunk.empty()) continue;
+            MixedWork mc = mw;  // the slots the defects were converted into
+            mc.nrhs = (int)chunk.size();
             std::vector<MMSState> hv;
             LoopOut lc;
-            st = mms_sloppy(g, m1, &sigma[i], 1, 1, tol, maxiter, check_every, profile, s, hv, lc);
+            st = mms_sloppy(g, mc, sg.data(), 1, 1, rho_inner, maxiter, check_every, profile, s, hv, lc, nullptr, 0,
+                            sg.data(), tl.data());
             if (st != TMND_OK) return st;
-            const MMSState &hc = hv[0];
-            for (int k = 0; k < hc.iter && k < (int)lc.hop_t.size(); k++) {
+            int maxit = 0;
+            for (const MMSState &h : hv) {
+                rs.iters += h.iter;
+                maxit = h.iter > maxit ? h.iter : maxit;
+            }
+            for (int k = 0; k < maxit && k < (int)lc.hop_t.size(); k++) {
                 rs.hop_ms += lc.hop_t[k];
                 rs.upd_ms += lc.upd_t[k];
             }
-            rs.iters += hc.iter;
-            rs.launches += 2 + lc.nlaunch * ((long long)check_every * 6 + check_every / WIN) + 1;
-            k_add_f32_to_f64<<<stream_blocks(n), UPD_THREADS, 0, s>>>(n, m1.x32(0, 0), xk[i]);
-            TMND_CUDA_TRY(cudaGetLastError());
-            next.push_back(i);
-        }
-        if (round >= max_rounds) {
-            if (!next.empty()) {
-                tmnd_set_error("solve: shift %d not converged after %d defect-correction rounds (residual %g)",
-                               next[0], max_rounds, res[next[0]]);
-                return TMND_ERR_NOCONV;
+            rs.launches += 3 + lc.nlaunch * ((long long)check_every * 7 + check_every / WIN);
+            for (size_t c = 0; c < chunk.size(); c++) {
+                k_add_f32_to_f64<<<stream_blocks(n), UPD_THREADS, 0, s>>>(n, mc.x32((int)c, 0), chunk[c].x);
+                next.push_back(chunk[c]);
             }
-            break;
+            TMND_CUDA_TRY(cudaGetLastError());
         }
         todo = next;
         if (!todo.empty()) rs.rounds = round + 1;
     }
     return TMND_OK;
+}
+
+// (RHS, shift) pairs solved together in one defect-correction round
+static int refine_batch(int R, int nsolve) {
+    const int p = R * nsolve;
+    return p < TMND_MAX_BATCH ? p : TMND_MAX_BATCH;
+}
+
+// workspace of the mixed solve of R right-hand sides: the batched multi-shift vectors, then
+// (same memory) the single-shift vectors of one batch of defect-correction pairs
+static size_t mixed_total_bytes(int Vh, int nshift, int nsolve, int R) {
+    const size_t a = mixed_work_bytes(Vh, nshift, R), b = mixed_work_bytes(Vh, 1, refine_batch(R, nsolve));
+    return a > b ? a : b;
 }
 
 // Mixed-precision solve of right-hand sides k0 .. k0+R-1: one batched sloppy
@@ -1038,6 +1100,8 @@ static tmnd_status mixed_batch(tmnd_gauge *g, const double2 *b, double2 *const *
     }
     tmnd_status conv = TMND_OK;
     int fp64 = 0, rounds = 0, riters = 0;
+    std::vector<std::vector<double>> res(R, std::vector<double>(nshift, 0.0));
+    std::vector<DCItem> items;
     for (int k = 0; k < R; k++) {
         const int rhs = k0 + k;
         double2 *xk[NS];
@@ -1059,25 +1123,25 @@ static tmnd_status mixed_batch(tmnd_gauge *g, const double2 *b, double2 *const *
                 info->zeta[i] = hs[k].zeta[i];
             }
         }
-        // 2. FP64 defect correction, shift by shift, for the shifts that must converge
-        std::vector<double> res(nshift, 0.0);
-        std::vector<int> todo;
-        for (int i = 0; i < nsolve; i++) todo.push_back(i);
-        RefineStats rs;
-        st = defect_correct(g, m, b + (size_t)rhs * n, xk, sigma, todo, bb[k], rho, rho_inner, maxiter,
-                            check_every, profile, s, res, rs);
-        if (st != TMND_OK && st != TMND_ERR_NOCONV) return st;
-        if (st == TMND_ERR_NOCONV) conv = st;
-        fp64 += rs.fp64;
-        riters += rs.iters;
-        rounds = rs.rounds > rounds ? rs.rounds : rounds;
-        launches += rs.launches;
-        hop_ms += rs.hop_ms;
-        upd_ms += rs.upd_ms;
-        if (info)
-            for (int i = 0; i < nshift; i++)
-                if (rhs == 0 || res[i] > info->true_res[i]) info->true_res[i] = res[i];
+        for (int i = 0; i < nsolve; i++)
+            items.push_back(DCItem{b + (size_t)rhs * n, xk[i], sigma[i], bb[k], &res[k][i]});
     }
+    // 2. FP64 defect correction of every (RHS, shift) pair that must converge, batched
+    RefineStats rs;
+    st = defect_correct(g, g->work, items, rho, rho_inner, maxiter, check_every, profile, s, rs,
+                        refine_batch(R, nsolve));
+    if (st != TMND_OK && st != TMND_ERR_NOCONV) return st;
+    if (st == TMND_ERR_NOCONV) conv = st;
+    fp64 += rs.fp64;
+    riters += rs.iters;
+    rounds = rs.rounds;
+    launches += rs.launches;
+    hop_ms += rs.hop_ms;
+    upd_ms += rs.upd_ms;
+    if (info)
+        for (int k = 0; k < R; k++)
+            for (int i = 0; i < nshift; i++)
+                if (k0 + k == 0 || res[k][i] > info->true_res[i]) info->true_res[i] = res[k][i];
     if (info) {
         info->fp64_applies += fp64;
         info->refine_iters += riters;
@@ -1122,13 +1186,16 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
     if (R > nrhs) R = nrhs;
     const size_t sp = tmnd_spinor_bytes(g);
     tmnd_status st = tmnd_ensure_workspace(
-        g, mixed ? mixed_work_bytes(g->geom.Vh, nshift, R) : (WIN + 3 + (size_t)nshift) * sp);
+        g, mixed ? mixed_total_bytes(g->geom.Vh, nshift, nsolve, R) : (WIN + 3 + (size_t)nshift) * sp);
     if (st != TMND_OK) return st;
     const long n = (long)(sp / sizeof(double2));
     const int nbh = hop_blocks(g->geom) > hop_blocks_s16(g->geom) ? hop_blocks(g->geom) : hop_blocks_s16(g->geom);
     const int nbs = stream_blocks(n) > site_blocks(g->geom.Vh) ? stream_blocks(n) : site_blocks(g->geom.Vh);
     size_t pbytes = sizeof(double) * (3 * (size_t)nbh + nbs) + 256 + 2 * 4096 + sizeof(MMSState) + sizeof(MMSCoef);
-    if (mixed && sloppy_partial_bytes(g->geom, R) > pbytes) pbytes = sloppy_partial_bytes(g->geom, R);
+    if (mixed) {
+        const int Rm = R > refine_batch(R, nsolve) ? R : refine_batch(R, nsolve);
+        if (sloppy_partial_bytes(g->geom, Rm) > pbytes) pbytes = sloppy_partial_bytes(g->geom, Rm);
+    }
     st = tmnd_ensure_partials(g, pbytes);
     if (st != TMND_OK) return st;
     if (info) memset(info, 0, sizeof *info);
@@ -1373,8 +1440,8 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
             // FP64 defect correction to rho
             std::vector<double> res(nshift, 0.0);
             RefineStats rs;
-            st = defect_correct(g, m, bk, xk, sigma, std::vector<int>{i}, bb, hp->rho, rho_inner, hp->maxiter, 32,
-                                0, s, res, rs);
+            std::vector<DCItem> one{DCItem{bk, xk[i], sigma[i], bb, &res[i]}};
+            st = defect_correct(g, g->work, one, hp->rho, rho_inner, hp->maxiter, 32, 0, s, rs, 1);
             if (st != TMND_OK) { res_status = st; break; }
             if (hinfo) {
                 hinfo->fp64_applies += rs.fp64 + 1;

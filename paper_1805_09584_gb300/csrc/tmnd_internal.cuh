@@ -186,8 +186,12 @@ __host__ __device__ inline S16Out s16_out(void *base, int Vh) {
     return S16Out{(int4 *)base, (float *)((char *)base + 96 * (size_t)Vh)};
 }
 
+constexpr int TMND_MAX_BATCH = 16;
 struct S16EpiArgs {
     double sigma;
+    // EPI_MMS_R with per_rhs_sigma: right-hand side k uses sigma_k[k] instead of sigma
+    int per_rhs_sigma;
+    double sigma_k[TMND_MAX_BATCH];
     S16In aux;              // EPI_SHIFT / EPI_MMS_R: vector multiplied by sigma
     float2 *r;              // EPI_MMS_R: updated residual (FP32 planes, written)
     const float2 *r_in;     // EPI_MMS_R: residual before the update
@@ -203,7 +207,6 @@ struct S16EpiArgs {
 // Several right-hand sides in one stencil launch (links read once, shared in cache):
 // right-hand side k of every 16-bit vector argument starts k * stride bytes after
 // the first; k is skipped while rdone[k * rdone_stride] is set (rdone may be NULL).
-constexpr int TMND_MAX_BATCH = 16;
 struct S16Batch {
     int nrhs = 1;
     size_t stride = 0;
