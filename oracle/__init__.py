@@ -419,3 +419,59 @@ def guess_quadratic_form(sig_nodes, sig_t, xs, bnorm2):
     G = (X.conj() @ X.T) / bnorm2
     d = float(sig_t) - np.asarray(sig_nodes, np.float64)
     return np.real(d[:, None] * G * d[None, :])
+
+
+# ------------------------------------------------------------ rational approximation
+# Zolotarev's optimal rational approximation of 1/sqrt(y) on eps < y < 1 (Sec. 4.1,
+# Eqs. "rational", "deviation", "zolotarev_shifts"), written from the paper's closed forms
+# with scipy's Jacobi elliptic functions as the library primitive (parameter m = k^2,
+# modulus k = sqrt(1 - eps)):
+#   v = K(k) / (2n + 1),  c_k = cs^2(k v, k),  s_k = sn^2(k v, k),
+#   d = (1 - eps)^((2n+1)/2) prod_j s_(2j-1)^2,  a = 2/(1 + sqrt(1 - d^2)) prod_j s_(2j-1)/s_(2j),
+#   delta = d^2 / (1 + sqrt(1 - d^2))^2
+# (the paper's closed form for delta prints the denominator unsquared, which is twice the
+# maximum of |1 - sqrt(y) R(y)| that defines delta in Eq. "deviation"; the definition decides),
+#   R(y) = a prod_j (y + c_(2j-1)) / (y + c_(2j)) = a (1 + sum_i q_i / (y + c_(2i))),
+#   q_i = (c_(2i-1) - c_(2i)) prod_{j != i} (c_(2j-1) - c_(2i)) / (c_(2j) - c_(2i))   (Eq. "ratapp").
+def zolotarev(n, eps):
+    """(a, c[0..2n-1] = c_1..c_2n, q[0..n-1], delta) for R_{n,eps}."""
+    from scipy.special import ellipj, ellipk
+    m = 1.0 - float(eps)
+    v = ellipk(m) / (2 * n + 1)
+    k = np.arange(1, 2 * n + 1)
+    sn, cn, _, _ = ellipj(k * v, m)
+    c = (cn / sn) ** 2
+    s = sn ** 2
+    d = (1.0 - eps) ** ((2 * n + 1) / 2.0) * np.prod(s[0::2] ** 2)
+    a = 2.0 / (1.0 + np.sqrt(1.0 - d * d)) * np.prod(s[0::2] / s[1::2])
+    delta = d * d / (1.0 + np.sqrt(1.0 - d * d)) ** 2
+    q = np.empty(n)
+    for i in range(n):
+        num, den = c[2 * i], c[2 * i + 1]
+        p = num - den
+        for j in range(n):
+            if j != i:
+                p *= (c[2 * j] - den) / (c[2 * j + 1] - den)
+        q[i] = p
+    return a, c, q, delta
+
+
+def zolotarev_eval(a, c, y):
+    """R(y) in the product form."""
+    y = np.asarray(y, np.float64)
+    r = np.full(y.shape, a)
+    for j in range(len(c) // 2):
+        r = r * (y + c[2 * j]) / (y + c[2 * j + 1])
+    return r
+
+
+def rational_apply(act: Action, links, b, n, lam_min, lam_max, rho=1e-12):
+    """x = R(Qhat^2/lam_max) b / sqrt(lam_max) ~ (Qhat^2)^(-1/2) b via the oracle's multi-shift CG on
+    the shifts lam_max c_(2i) and the partial-fraction form (Eq. "ratapp")."""
+    a, c, q, delta = zolotarev(n, lam_min / lam_max)
+    sig = lam_max * c[1::2]
+    xs = mms_cg(act, links, b, sig, rho=rho)["x"]
+    x = np.asarray(b, np.complex128).copy()
+    for i in range(n):
+        x = x + lam_max * q[i] * xs[i]
+    return a / np.sqrt(lam_max) * x, delta
