@@ -24,6 +24,9 @@ true residual:
            the 8 largest, learned guesses for the 4 smallest finished by defect
            correction; the network is trained first on solves of other fields
            (outside the timed region); the same with Lagrange guesses is reported
+  rational 24^3x48, 2 RHS: x = R(Qhat^2) b ~ (Qhat^2)^(-1/2) b with Zolotarev's n = 10
+           approximation on the spectrum bounds from a Lanczos estimate (mixed
+           multi-shift CG over the 10 Zolotarev shifts + one combination)
 Each form's line also times the plain FP64 multi-shift CG on its workload
 ("fp64_same_workload") and reports a roofline for its dominant kernel.
 
@@ -280,6 +283,7 @@ FORMS = {
     "batched": dict(dims=(64, 32, 32, 32), nrhs=8, seeds=(1004, 2004), lattice="32^3x64"),
     "hybrid": dict(dims=(64, 32, 32, 32), nrhs=8, seeds=(1004, 2004), lattice="32^3x64"),
     "learned": dict(dims=(48, 24, 24, 24), nrhs=1, seeds=(1005, 2005), lattice="24^3x48"),
+    "rational": dict(dims=(48, 24, 24, 24), nrhs=2, seeds=(1003, 2003), lattice="24^3x48"),
 }
 # 16-bit stencil, algorithmic bytes per odd site: even launch 392 (in 100, 12-real
 # 16-bit links 192, out 100), odd launch 492 (+ psi 100); Qhat^2 + sigma adds aux 100
@@ -386,7 +390,24 @@ def run_form(args):
         extra["training"] = {"solves": 8, "samples": 32, "fields": 4, "s": time.perf_counter() - t0,
                              "loss_first_last": [losses[0], losses[-1]]}
 
+    if args.form == "rational":
+        # spectrum bounds of Qhat^2 from the Ritz values of one FP64 CG history (10 % margins)
+        hist = np.zeros(8192)
+        xb = [g.spinor(1)]
+        inf = tm.mms_cg_solve(g.handle, b_dev[: 24 * g.vh], 1, [1e-5], xb, rho=1e-8, ab_hist=hist)
+        f = tm.tmnd_mlp_features(sig[:8], float(sig[8]), hist, inf["iters"], 1e-5)
+        lmin, lmax = 0.9 * 10 ** float(f[17]), 1.1 * 10 ** float(f[18])
+        a_z, c_z, q_z, delta = tm.tmnd_zolotarev(10, lmin / lmax)
+        sig = lmax * c_z[1::2]                 # the shifts the multi-shift solve sees
+        out_r = g.spinor(nrhs)
+        extra["rational"] = {"n": 10, "lambda_min": lmin, "lambda_max": lmax, "delta": delta,
+                             "shifts": [float(v) for v in sig]}
+        del xb
+
     def step():
+        if args.form == "rational":
+            return tm.tmnd_rational_apply(g.handle, b_dev, nrhs, 10, lmin, lmax, out_r, rho=RHO, prec=tm.TMND_S16,
+                                          stream=stream)
         if args.form in ("mixed", "batched"):
             return tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs, rho=RHO, prec=tm.TMND_S16,
                                    batch=1 if args.form == "mixed" else 0, stream=stream)
@@ -401,7 +422,7 @@ def run_form(args):
     sampler = ClockSampler(local)
     ms, infos = _timed(step, args.steps, flush, stream)
     clocks = sampler.stop()
-    solves = args.steps * NSHIFT * nrhs
+    solves = args.steps * len(sig) * nrhs
     value = solves / (ms / 1e3)
     worst = max(max(i["true_res"]) for i in infos)
     if args.form == "learned":   # the same with Lagrange guesses (the method without the network)
@@ -422,16 +443,18 @@ def run_form(args):
     b_can = torch.empty((nrhs, g.vh, 2, 4, 3), dtype=torch.complex128, device="cuda")
     x_can = torch.empty((nrhs, g.vh, 2, 4, 3), dtype=torch.complex128, device="cuda")
 
+    outs = [out_r] if args.form == "rational" else xs
+
     def step_e2e():
         b_can.copy_(b_pin, non_blocking=True)
         tm.tmnd_spinor_pack(g.handle, b_dev, b_can, nrhs, stream)
         step()
-        for i in range(NSHIFT):
-            tm.tmnd_spinor_unpack(g.handle, x_can, xs[i], nrhs, stream)
+        for i, v in enumerate(outs):
+            tm.tmnd_spinor_unpack(g.handle, x_can, v, nrhs, stream)
             x_pin[i].copy_(x_can, non_blocking=True)
     e2e_ms, _ = _timed(step_e2e, args.steps, flush, stream)
     # the plain FP64 multi-shift CG on the same workload (one step)
-    f64 = lambda: tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs, rho=RHO, stream=stream)
+    f64 = lambda: tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs[:len(sig)], rho=RHO, stream=stream)
     f64()
     f64_ms, _ = _timed(f64, 1, flush, stream)
     roof = s16_roofline(tm, g, flush, stream)
@@ -449,15 +472,16 @@ def run_form(args):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32/16-bit sloppy + f64 defect correction", "data": "synthetic",
-        "config": {"workload": f"{F['lattice']} ND twisted-mass doublet, {args.form} form, 12 shifts 1e-5..2, "
-                               f"{nrhs} RHS, rho 1e-10", "form": args.form, "lattice": F["lattice"],
-                   "nshift": NSHIFT, "nrhs": nrhs, "rho": RHO, "kappa": KAPPA, "mu_bar": MU_BAR,
+        "config": {"workload": f"{F['lattice']} ND twisted-mass doublet, {args.form} form, "
+                               + ("Zolotarev n = 10 shifts" if args.form == "rational" else "12 shifts 1e-5..2")
+                               + f", {nrhs} RHS, rho 1e-10", "form": args.form, "lattice": F["lattice"],
+                   "nshift": len(sig), "nrhs": nrhs, "rho": RHO, "kappa": KAPPA, "mu_bar": MU_BAR,
                    "eps_bar": EPS_BAR, "roughness": ROUGHNESS, "parallelism": "single GPU",
                    "l2": "flushed between steps (512 MB write); solve working set > L2"},
         "max_true_rel_residual": worst,
-        "fp64_same_workload": {"value": nrhs * NSHIFT / (f64_ms / 1e3), "ms_per_step": f64_ms},
+        "fp64_same_workload": {"value": nrhs * len(sig) / (f64_ms / 1e3), "ms_per_step": f64_ms},
         "e2e": {"value": solves / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": b_host.nbytes,
-                "d2h_bytes_per_step": NSHIFT * b_host.nbytes},
+                "d2h_bytes_per_step": len(outs) * b_host.nbytes},
         "roofline": roof, "gpu_launches": launches, "clocks": clocks, **extra,
     }
     if net is not None:
@@ -619,7 +643,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tmnd", choices=["tmnd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "batched", "hybrid", "learned"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "batched", "hybrid", "learned", "rational"])
     ap.add_argument("--kernel", default=None, choices=["fp64", "s16", "coarse"])
     args = ap.parse_args()
     if args.kernel:

@@ -401,6 +401,26 @@ tmnd_status tmnd_gram(const tmnd_gauge *g, const void *const *xs, int k, double 
 tmnd_status tmnd_lincomb(const tmnd_gauge *g, const double *w, const void *const *xs, int k, void *out, int nrhs,
                          void *stream);
 
+/* ------------------------------------------------------------ rational approximation
+ * Zolotarev's optimal rational approximation of 1/sqrt(y) on eps < y < 1 (Sec. 4.1,
+ * Eqs. "rational", "deviation", "zolotarev_shifts"):
+ *   R(y) = a prod_{j=1..n} (y + c_{2j-1}) / (y + c_{2j}) = a (1 + sum_i q_i / (y + c_{2i}))
+ * Host function.  c: 2n doubles (c_1 > c_2 > ... > c_2n > 0), q: n residues (Eq. "ratapp"),
+ * *delta = max |1 - sqrt(y) R(y)| on (eps, 1) = d^2 / (1 + sqrt(1 - d^2))^2.
+ * 1 <= n <= TMND_MAX_SHIFTS, 0 < eps < 1. */
+tmnd_status tmnd_zolotarev(int n, double eps, double *a, double *c, double *q, double *delta);
+
+/* out = R(Qhat^2 / lambda_max) b / sqrt(lambda_max) ~ (Qhat^2)^{-1/2} b (Sec. 4.1, Eq. "ratapp")
+ * for a spectrum of Qhat^2 inside [lambda_min, lambda_max] (eps = lambda_min / lambda_max):
+ * one mms_cg_solve of the n shifted systems (Qhat^2 + lambda_max c_{2i}) x_i = b with `params`
+ * (nsolve 0: every shift converges) and one linear combination.  Per eigen-component the
+ * relative error is at most delta (written to *delta_out, may be NULL) plus the solves'.
+ * b, out: device, nrhs internal FP64 spinors.  Allocates n * nrhs spinors for the call.
+ * Synchronous. */
+tmnd_status tmnd_rational_apply(tmnd_gauge *g, const void *b, int nrhs, int n, double lambda_min,
+                                double lambda_max, const tmnd_solve_params *params, void *out,
+                                double *delta_out, tmnd_solve_info *info, void *stream);
+
 /* Message for the last error on this host thread ("" if none). */
 const char *tmnd_last_error(void);
 

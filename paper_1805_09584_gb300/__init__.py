@@ -34,7 +34,7 @@ EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd
            "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export", "tmnd_dnd_full_apply", "tmnd_mg_solve",
            "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve", "tmnd_mlp_num_params", "tmnd_mlp_create",
            "tmnd_mlp_destroy", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad", "tmnd_mlp_train_step", "tmnd_mlp_predict",
-           "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb")
+           "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_zolotarev", "tmnd_rational_apply")
 NOALLOC_MAX_VH = 32768
 
 
@@ -140,8 +140,12 @@ def lib() -> ctypes.CDLL:
         L.tmnd_mlp_features.argtypes = [ctypes.POINTER(d), d, vp, i, d, fp]
         L.tmnd_gram.argtypes = [vp, ctypes.POINTER(vp), i, ctypes.POINTER(d), vp]
         L.tmnd_lincomb.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(vp), i, vp, i, vp]
+        pd = ctypes.POINTER(d)
+        L.tmnd_zolotarev.argtypes = [i, d, pd, pd, pd, pd]
+        L.tmnd_rational_apply.argtypes = [vp, vp, i, i, d, d, ctypes.POINTER(SolveParams), vp, pd,
+                                          ctypes.POINTER(SolveInfo), vp]
         for name in ("tmnd_mlp_create", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad",
-                     "tmnd_mlp_train_step",
+                     "tmnd_mlp_train_step", "tmnd_zolotarev", "tmnd_rational_apply",
                      "tmnd_mlp_predict", "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
@@ -464,3 +468,26 @@ class Gauge:
         out = torch.empty((nrhs, self.vh, 2, 4, 3), dtype=torch.complex128, device=internal.device)
         tmnd_spinor_unpack(self.handle, out, internal, nrhs, stream)
         return out
+
+
+def tmnd_zolotarev(n: int, eps: float):
+    """(a, c[2n], q[n], delta) of Zolotarev's approximation of 1/sqrt(y) on (eps, 1)."""
+    a, delta = ctypes.c_double(), ctypes.c_double()
+    c = np.zeros(2 * n)
+    q = np.zeros(n)
+    pd = ctypes.POINTER(ctypes.c_double)
+    _check(lib().tmnd_zolotarev(int(n), float(eps), ctypes.byref(a), c.ctypes.data_as(pd), q.ctypes.data_as(pd),
+                                ctypes.byref(delta)))
+    return a.value, c, q, delta.value
+
+
+def tmnd_rational_apply(h, b, nrhs: int, n: int, lambda_min: float, lambda_max: float, out, rho: float = 1e-10,
+                        prec: int = TMND_F64, maxiter: int = 100000, stream=None) -> dict:
+    """out = R(Qhat^2/lambda_max) b / sqrt(lambda_max) ~ (Qhat^2)^(-1/2) b."""
+    p = SolveParams(float(rho), int(maxiter), 0, 0, 0, int(prec), 0.0)
+    info = SolveInfo()
+    delta = ctypes.c_double()
+    _check(lib().tmnd_rational_apply(h, _ptr(b), int(nrhs), int(n), float(lambda_min), float(lambda_max),
+                                     ctypes.byref(p), _ptr(out), ctypes.byref(delta), ctypes.byref(info),
+                                     _stream(stream)))
+    return {"delta": delta.value, "iters": info.iters, "true_res": list(info.true_res[:n])}
