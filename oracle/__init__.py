@@ -475,3 +475,52 @@ def rational_apply(act: Action, links, b, n, lam_min, lam_max, rho=1e-12):
     for i in range(n):
         x = x + lam_max * q[i] * xs[i]
     return a / np.sqrt(lam_max) * x, delta
+
+
+# ------------------------------------------------------------ hybrid cost model
+# Sec. 4.3: time-to-solution fits of CG (Eq. "CGtime2") and MG (Eq. "MGtime2") per shift
+# m^2 = sigma, and the hybrid's cost with the n largest shifts by MMS-CG (Eq. "costwo"):
+#   t_CG(s) = a + b / ln(1 - 2 / (sqrt(kappa(s)) + 1)),  kappa(s) = (lmax + s) / (lmin + s)
+#   t_MG(s) = A + B / ln(1 - (C + s) / (L + s))        (L = the spectrum's upper end, 4.7 in the paper)
+#   c_HY(n) = t_CG(s_n) + sum_{i > n} t_MG(s_i),  shifts descending, n = 1..N
+def t_cg(s, a, b, lmin, lmax):
+    s = np.asarray(s, np.float64)
+    kappa = (lmax + s) / (lmin + s)
+    return a + b / np.log(1.0 - 2.0 / (np.sqrt(kappa) + 1.0))
+
+
+def t_mg(s, A, B, C, L):
+    s = np.asarray(s, np.float64)
+    return A + B / np.log(1.0 - (C + s) / (L + s))
+
+
+def hybrid_cost(sig, cg, mg):
+    """c_HY(n) for n = 1..N (list) and the n that minimises it; cg = (a, b, lmin, lmax), mg = (A, B, C, L)."""
+    sig = np.asarray(sig, np.float64)
+    N = len(sig)
+    tm = t_mg(sig, *mg)
+    cost = [float(t_cg(sig[n - 1], *cg) + tm[n:].sum()) for n in range(1, N + 1)]
+    return cost, int(np.argmin(cost)) + 1
+
+
+def fit_cg_time(sig, t, lmin, lmax):
+    """Least-squares (a, b) of Eq. "CGtime2" (linear in a, b)."""
+    x = 1.0 / np.log(1.0 - 2.0 / (np.sqrt((lmax + np.asarray(sig)) / (lmin + np.asarray(sig))) + 1.0))
+    M = np.stack([np.ones_like(x), x], 1)
+    (a, b), *_ = np.linalg.lstsq(M, np.asarray(t, np.float64), rcond=None)
+    return float(a), float(b)
+
+
+def fit_mg_time(sig, t, L, grid=2001):
+    """(A, B, C) of Eq. "MGtime2": least squares in (A, B) for each C on a log grid in (0, L), best C."""
+    sig = np.asarray(sig, np.float64)
+    t = np.asarray(t, np.float64)
+    best = None
+    for C in np.geomspace(1e-8 * L, 0.999 * L, grid):
+        x = 1.0 / np.log(1.0 - (C + sig) / (L + sig))
+        M = np.stack([np.ones_like(x), x], 1)
+        sol, *_ = np.linalg.lstsq(M, t, rcond=None)
+        r = float(np.sum((M @ sol - t) ** 2))
+        if best is None or r < best[0]:
+            best = (r, float(sol[0]), float(sol[1]), float(C))
+    return best[1], best[2], best[3]

@@ -119,3 +119,31 @@ def test_s16_multi_rhs_apply_equals_single():
             tm.tm_nd_apply(g.handle, one, q8[k * nb:(k + 1) * nb], op | tm.OP_S16, 0.0213, nrhs=1)
             assert torch.equal(one.view(torch.uint8), o8[k * nb:(k + 1) * nb]), (op, k)
     g.close()
+
+
+def test_mixed_batch_with_zero_rhs_and_argument_limits():
+    """A zero right-hand side inside a batch gives x = 0 while the others are
+    certified; batch > 16 and 16-bit applies of more than 16 RHS are rejected."""
+    tm = require_gpu()
+    dims = (4, 4, 4, 4)
+    U = synth.random_su3_field(dims, 0.4, 81)
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    b = synth.gaussian_rhs(dims, 82, nrhs=3)
+    b[1] = 0
+    sig = synth.shift_set(6, 1e-3, 1.0)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    bi = g.pack(torch.from_numpy(b).cuda(), nrhs=3)
+    xs = [g.spinor(3) for _ in sig]
+    tm.mms_cg_solve(g.handle, bi, 3, sig, xs, prec=tm.TMND_S16, batch=3)
+    for i, s in enumerate(sig):
+        x = g.unpack(xs[i], 3).cpu().numpy()
+        assert np.all(x[1] == 0)
+        for k in (0, 2):
+            assert oracle.true_residual(act, U, b[k], x[k], s) <= 1.01e-10
+    with pytest.raises(RuntimeError):
+        tm.mms_cg_solve(g.handle, bi, 3, sig, xs, prec=tm.TMND_S16, batch=17)
+    q = g.spinor(17, prec=tm.TMND_S16)
+    o = g.spinor(17, prec=tm.TMND_S16)
+    with pytest.raises(RuntimeError):
+        tm.tm_nd_apply(g.handle, o, q, tm.OP_MHAT | tm.OP_S16, 0.0, nrhs=17)
+    g.close()
