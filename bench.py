@@ -30,6 +30,10 @@ true residual:
 Each form's line also times the plain FP64 multi-shift CG on its workload
 ("fp64_same_workload") and reports a roofline for its dominant kernel.
 
+--study hybrid measures the hybrid cost model of Sec. 4.3 on GB300 (24^3x48):
+per-shift CG and MG times, their fits, the model's optimal n and the measured
+hybrid time for every n, without and with Lagrange guesses.
+
 --kernel fp64|s16|coarse times one kernel family alone (CUDA events, L2 flushed
 between applications) and prints its achieved rate against the roofline:
   fp64    FP64 Qhat^2 + sigma (4 stencil launches), 16^3x32
@@ -571,6 +575,68 @@ def run_kernel(args):
     return out
 
 
+
+def run_study(args):
+    """Hybrid cost model on GB300 (Sec. 4.3): per shift the mixed CG time t_CG and the
+    case-C MG time t_MG (zero start), fits of Eqs. "CGtime2" / "MGtime2", the model's
+    c_HY(n) and n_opt, and the measured hybrid time for every n, without and with guesses."""
+    import numpy as np
+    import torch
+
+    import paper_1805_09584_gb300 as tm
+    import synth
+    from paper_1805_09584_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    dims = (48, 24, 24, 24)
+    g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
+    sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
+    b = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, 2003)).cuda())
+    xs = [g.spinor() for _ in sig]
+    nv = 24
+    tv = torch.randn(nv * 2 * 12 * g.vh, dtype=torch.complex64, device="cuda")
+    tm.tmnd_mg_smooth_vectors(g.handle, tv, nv, 4)
+    mg = tm.tmnd_mg_create(g.handle, (4, 4, 4, 4), nv, tv)
+    del tv
+    hist = np.zeros(8192)
+    inf = tm.mms_cg_solve(g.handle, b, 1, [SIG_LO], xs[:1], rho=1e-8, ab_hist=hist)
+    f = tm.tmnd_mlp_features(sig[:8], float(sig[8]), hist, inf["iters"], SIG_LO)
+    lmin, lmax = 10 ** float(f[17]), 10 ** float(f[18])
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3, out
+
+    wall(lambda: tm.mms_cg_solve(g.handle, b, 1, sig[-1:], xs[:1], rho=RHO, prec=tm.TMND_S16))
+    t_cg = [wall(lambda s=s: tm.mms_cg_solve(g.handle, b, 1, [s], xs[:1], rho=RHO, prec=tm.TMND_S16))[0]
+            for s in sig]
+    hyb = lambda n, guess: tm.tmnd_hybrid_solve(g.handle, mg, b, 1, sig, n, xs, rho=RHO, prec=tm.TMND_S16,
+                                                n_guess=0, guess=guess)
+    hyb(1, 0)
+    _, h0 = wall(lambda: hyb(1, 0))
+    t_mg = h0["shift_ms"][1:]                       # shifts 1..N-1 by MG from zero
+    a, bb = tm.tmnd_fit_cg_time(sig, t_cg, lmin, lmax)
+    A, B, C = tm.tmnd_fit_mg_time(sig[1:], t_mg, lmax)
+    cost, n_opt = tm.tmnd_hybrid_cost(sig, (a, bb, lmin, lmax), (A, B, C, lmax))
+    meas0 = [wall(lambda n=n: hyb(n, 0))[0] for n in range(1, NSHIFT + 1)]
+    meas1 = [wall(lambda n=n: hyb(n, 1))[0] for n in range(1, NSHIFT + 1)]
+    tm.tmnd_mg_destroy(mg)
+    g.close()
+    r = lambda v: [round(float(x), 2) for x in v]
+    return {"study": "hybrid cost model (Sec. 4.3) on GB300", "lattice": "24^3x48", "shifts": r(sig),
+            "spectrum": {"lambda_min": lmin, "lambda_max": lmax, "source": "Ritz values of a CG history"},
+            "t_cg_ms": r(t_cg), "t_mg_ms": r(t_mg),
+            "fit_cg": {"a": a, "b": bb}, "fit_mg": {"A": A, "B": B, "C": C, "L": lmax},
+            "model_cost_ms": r(cost), "model_n_opt": n_opt,
+            "measured_ms_no_guess": r(meas0), "measured_n_opt_no_guess": int(np.argmin(meas0)) + 1,
+            "measured_ms_lagrange": r(meas1), "measured_n_opt_lagrange": int(np.argmin(meas1)) + 1,
+            "note": "n = shifts by the mixed multi-shift CG; the rest by case-C MG + FP64 defect correction"}
+
+
 # FP64 peak of a GB300 (sm_103a): 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -645,7 +711,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "batched", "hybrid", "learned", "rational"])
     ap.add_argument("--kernel", default=None, choices=["fp64", "s16", "coarse"])
+    ap.add_argument("--study", default=None, choices=["hybrid"])
     args = ap.parse_args()
+    if args.study:
+        print(json.dumps(run_study(args)))
+        return
     if args.kernel:
         print(json.dumps(run_kernel(args)))
         return

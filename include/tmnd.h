@@ -337,6 +337,9 @@ typedef struct {
     double true_res[TMND_MAX_SHIFTS];      /* final FP64 relative residuals (max over RHS) */
     int fp64_applies;                      /* FP64 operator applications */
     int refine_iters;                      /* sloppy defect-correction iterations */
+    double shift_ms[TMND_MAX_SHIFTS];      /* wall time of each non-MMS shift's guess, MG and
+                                              defect correction (RHS 0); the MMS part's in mms_ms */
+    double mms_ms;                         /* wall time of the multi-shift part (all RHS) */
 } tmnd_hybrid_info;
 
 /* Hybrid solve of (Qhat^2 + sigma_i) x_i = b (Sec. 4.3): multi-shift CG for
@@ -420,6 +423,22 @@ tmnd_status tmnd_zolotarev(int n, double eps, double *a, double *c, double *q, d
 tmnd_status tmnd_rational_apply(tmnd_gauge *g, const void *b, int nrhs, int n, double lambda_min,
                                 double lambda_max, const tmnd_solve_params *params, void *out,
                                 double *delta_out, tmnd_solve_info *info, void *stream);
+
+/* ------------------------------------------------------------ hybrid cost model (Sec. 4.3)
+ * Host functions.  Per shift s: t_CG(s) = a + b / ln(1 - 2/(sqrt(kappa(s)) + 1)),
+ * kappa(s) = (lmax + s)/(lmin + s) (Eq. "CGtime2"); t_MG(s) = A + B / ln(1 - (C + s)/(L + s))
+ * (Eq. "MGtime2"); the hybrid with the n largest of N descending shifts by multi-shift CG costs
+ * c_HY(n) = t_CG(s_n) + sum_{i > n} t_MG(s_i) (Eq. "costwo").
+ *   cg = {a, b, lmin, lmax}, mg = {A, B, C, L}; cost: N doubles (c_HY(1..N)); *n_opt = argmin. */
+tmnd_status tmnd_hybrid_cost(const double *sigma, int N, const double *cg, const double *mg, double *cost,
+                             int *n_opt);
+/* Least-squares a, b of t_CG for measured times t[i] at shifts sigma[i] (N >= 2). */
+tmnd_status tmnd_fit_cg_time(const double *sigma, const double *t, int N, double lmin, double lmax, double *a,
+                             double *b);
+/* A, B, C of t_MG: C on a log grid of `grid` points in (1e-8 L, 0.999 L), A and B by least
+ * squares for each, the best residual kept (N >= 3). */
+tmnd_status tmnd_fit_mg_time(const double *sigma, const double *t, int N, double L, int grid, double *A, double *B,
+                             double *C);
 
 /* Message for the last error on this host thread ("" if none). */
 const char *tmnd_last_error(void);

@@ -34,7 +34,8 @@ EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd
            "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export", "tmnd_dnd_full_apply", "tmnd_mg_solve",
            "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve", "tmnd_mlp_num_params", "tmnd_mlp_create",
            "tmnd_mlp_destroy", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad", "tmnd_mlp_train_step", "tmnd_mlp_predict",
-           "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_zolotarev", "tmnd_rational_apply")
+           "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_zolotarev", "tmnd_rational_apply",
+           "tmnd_hybrid_cost", "tmnd_fit_cg_time", "tmnd_fit_mg_time")
 NOALLOC_MAX_VH = 32768
 
 
@@ -64,7 +65,8 @@ class HybridParams(ctypes.Structure):
 class HybridInfo(ctypes.Structure):
     _fields_ = [("mms_iters", ctypes.c_int), ("guess_res", ctypes.c_double * MAX_SHIFTS),
                 ("mg_iters", ctypes.c_int * MAX_SHIFTS), ("true_res", ctypes.c_double * MAX_SHIFTS),
-                ("fp64_applies", ctypes.c_int), ("refine_iters", ctypes.c_int)]
+                ("fp64_applies", ctypes.c_int), ("refine_iters", ctypes.c_int),
+                ("shift_ms", ctypes.c_double * MAX_SHIFTS), ("mms_ms", ctypes.c_double)]
 
 
 class SolveParams(ctypes.Structure):
@@ -142,10 +144,14 @@ def lib() -> ctypes.CDLL:
         L.tmnd_lincomb.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(vp), i, vp, i, vp]
         pd = ctypes.POINTER(d)
         L.tmnd_zolotarev.argtypes = [i, d, pd, pd, pd, pd]
+        L.tmnd_hybrid_cost.argtypes = [pd, i, pd, pd, pd, ctypes.POINTER(i)]
+        L.tmnd_fit_cg_time.argtypes = [pd, pd, i, d, d, pd, pd]
+        L.tmnd_fit_mg_time.argtypes = [pd, pd, i, d, i, pd, pd, pd]
         L.tmnd_rational_apply.argtypes = [vp, vp, i, i, d, d, ctypes.POINTER(SolveParams), vp, pd,
                                           ctypes.POINTER(SolveInfo), vp]
         for name in ("tmnd_mlp_create", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad",
-                     "tmnd_mlp_train_step", "tmnd_zolotarev", "tmnd_rational_apply",
+                     "tmnd_mlp_train_step", "tmnd_zolotarev", "tmnd_rational_apply", "tmnd_hybrid_cost",
+                     "tmnd_fit_cg_time", "tmnd_fit_mg_time",
                      "tmnd_mlp_predict", "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
@@ -334,7 +340,8 @@ def tmnd_hybrid_solve(h, mg, b, nrhs: int, sigma, n_mms: int, x, rho: float = 1e
                                  int(n_mms), xs, ctypes.byref(p), ctypes.byref(info), _stream(stream))
     out = {"status": st, "mms_iters": info.mms_iters, "guess_res": list(info.guess_res[:ns]),
            "mg_iters": list(info.mg_iters[:ns]), "true_res": list(info.true_res[:ns]),
-           "fp64_applies": info.fp64_applies, "refine_iters": info.refine_iters}
+           "fp64_applies": info.fp64_applies, "refine_iters": info.refine_iters,
+           "shift_ms": list(info.shift_ms[:ns]), "mms_ms": info.mms_ms}
     _check(st)
     return out
 
@@ -491,3 +498,35 @@ def tmnd_rational_apply(h, b, nrhs: int, n: int, lambda_min: float, lambda_max: 
                                      ctypes.byref(p), _ptr(out), ctypes.byref(delta), ctypes.byref(info),
                                      _stream(stream)))
     return {"delta": delta.value, "iters": info.iters, "true_res": list(info.true_res[:n])}
+
+
+def _pd(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def tmnd_hybrid_cost(sigma, cg, mg):
+    """(c_HY(n) for n = 1..N, n_opt); cg = (a, b, lmin, lmax), mg = (A, B, C, L)."""
+    s = np.ascontiguousarray(sigma, np.float64)
+    c1 = np.ascontiguousarray(cg, np.float64)
+    m1 = np.ascontiguousarray(mg, np.float64)
+    cost = np.zeros(len(s))
+    n = ctypes.c_int()
+    _check(lib().tmnd_hybrid_cost(_pd(s), len(s), _pd(c1), _pd(m1), _pd(cost), ctypes.byref(n)))
+    return cost, n.value
+
+
+def tmnd_fit_cg_time(sigma, t, lmin: float, lmax: float):
+    s = np.ascontiguousarray(sigma, np.float64)
+    tt = np.ascontiguousarray(t, np.float64)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().tmnd_fit_cg_time(_pd(s), _pd(tt), len(s), float(lmin), float(lmax), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def tmnd_fit_mg_time(sigma, t, L: float, grid: int = 2001):
+    s = np.ascontiguousarray(sigma, np.float64)
+    tt = np.ascontiguousarray(t, np.float64)
+    A, B, C = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().tmnd_fit_mg_time(_pd(s), _pd(tt), len(s), float(L), int(grid), ctypes.byref(A), ctypes.byref(B),
+                                  ctypes.byref(C)))
+    return A.value, B.value, C.value

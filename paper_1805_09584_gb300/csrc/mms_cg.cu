@@ -39,6 +39,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <chrono>
 #include <vector>
 
 #include "tmnd_internal.cuh"
@@ -1293,10 +1294,14 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
         sp1.ab_hist_len = (int)hist.size();
     }
     tmnd_solve_info si = {};
+    const auto t_mms = std::chrono::steady_clock::now();
     tmnd_status st = mms_cg_solve(g, b, nrhs, sigma, nmms_all, x, &sp1, &si, stream);
     if (st != TMND_OK) return st;
+    const double mms_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_mms).count();
     if (hinfo) {
         memset(hinfo, 0, sizeof *hinfo);
+        hinfo->mms_ms = mms_ms;
         hinfo->mms_iters = si.iters;
         hinfo->fp64_applies = si.fp64_applies;
         hinfo->refine_iters = si.refine_iters;
@@ -1388,6 +1393,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
         cudaMemsetAsync(rhs, 0, sizeof(float2) * n, s);
         k_to_f32_scaled<<<nbs, 256, 0, s>>>(n, 1.0, gb, rhs + n);
         for (int i = n_mms; i < nshift && res_status == TMND_OK; i++) {
+            const auto t_shift = std::chrono::steady_clock::now();
             // guess
             if (i >= nmms_all) {
                 if (hp->guess == 2) {
@@ -1443,6 +1449,11 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
             std::vector<DCItem> one{DCItem{bk, xk[i], sigma[i], bb, &res[i]}};
             st = defect_correct(g, g->work, one, hp->rho, rho_inner, hp->maxiter, 32, 0, s, rs, 1);
             if (st != TMND_OK) { res_status = st; break; }
+            if (hinfo && k == 0) {
+                cudaStreamSynchronize(s);
+                hinfo->shift_ms[i] =
+                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_shift).count();
+            }
             if (hinfo) {
                 hinfo->fp64_applies += rs.fp64 + 1;
                 hinfo->refine_iters += rs.iters;
