@@ -326,7 +326,8 @@ typedef struct {
                               network's features use the first RHS's base-recursion history) */
     double mg_tol;         /* relative tolerance of each case-C MG solve (0 = 1e-4; the solve is
                               FP32, the FP64 defect correction finishes the shift) */
-    int mg_maxiter, mg_restart, mg_nu;   /* 0 = 100, 8, 4 */
+    int mg_maxiter, mg_restart, mg_nu;   /* 0 = 100, 24, 4 (GCR(8) stagnates on the indefinite
+                                            full-lattice operator at small shifts) */
     const struct tmnd_mlp *net;          /* guess = 2: a trained network (see tmnd_mlp_*), else NULL */
 } tmnd_hybrid_params;
 

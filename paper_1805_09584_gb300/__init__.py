@@ -311,7 +311,7 @@ def tmnd_dnd_full_apply(h, out, inp, s: float = 0.0, stream=None) -> None:
     _check(lib().tmnd_dnd_full_apply(h, _ptr(out), _ptr(inp), float(s), _stream(stream)))
 
 
-def tmnd_mg_solve(mg, x, b, s: float = 0.0, tol: float = 1e-6, maxiter: int = 200, restart: int = 8, nu: int = 4,
+def tmnd_mg_solve(mg, x, b, s: float = 0.0, tol: float = 1e-6, maxiter: int = 200, restart: int = 24, nu: int = 4,
                   stream=None) -> dict:
     it = ctypes.c_int()
     res = ctypes.c_double()

@@ -1347,7 +1347,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
     if (st != TMND_OK) return st;
     const long nfull = 2 * n;  // full-lattice FP32 doublet (complex numbers)
     const size_t f32b = sizeof(float2) * nfull;
-    const size_t scratch_b = 3 * sp + 4 * f32b + (mg ? mg_gcr_scratch_bytes(mg, hp->mg_restart > 0 ? hp->mg_restart : 8) : 0);
+    const size_t scratch_b = 3 * sp + 4 * f32b + (mg ? mg_gcr_scratch_bytes(mg, hp->mg_restart > 0 ? hp->mg_restart : 24) : 0);
     char *scr = nullptr;
     TMND_CUDA_TRY(cudaMalloc(&scr, scratch_b));
     double2 *tq = (double2 *)scr, *te = (double2 *)(scr + sp), *gb = (double2 *)(scr + 2 * sp);
@@ -1434,7 +1434,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
                     double rres = 0;
                     const double tol = hp->mg_tol > 0 ? hp->mg_tol : 1e-4;
                     st = mg_gcr_solve(mg, y, rhs, sgn * sq, tol, hp->mg_maxiter > 0 ? hp->mg_maxiter : 100,
-                                      hp->mg_restart > 0 ? hp->mg_restart : 8, hp->mg_nu > 0 ? hp->mg_nu : 4, s, &it,
+                                      hp->mg_restart > 0 ? hp->mg_restart : 24, hp->mg_nu > 0 ? hp->mg_nu : 4, s, &it,
                                       &rres, gcr);
                     if (st != TMND_OK) { res_status = st; break; }
                     mg_it += it;
