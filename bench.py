@@ -30,6 +30,8 @@ true residual:
 Each form's line also times the plain FP64 multi-shift CG on its workload
 ("fp64_same_workload") and reports a roofline for its dominant kernel.
 
+--study learned runs config 5: train on solves of 20 fields, evaluate on 5 unseen
+fields (CG iterations for the 4 smallest shifts from zero, Lagrange and learned guesses).
 --study hybrid measures the hybrid cost model of Sec. 4.3 on GB300 (24^3x48):
 per-shift CG and MG times, their fits, the model's optimal n and the measured
 hybrid time for every n, without and with Lagrange guesses.
@@ -637,6 +639,72 @@ def run_study(args):
             "note": "n = shifts by the mixed multi-shift CG; the rest by case-C MG + FP64 defect correction"}
 
 
+
+def run_study_learned(args):
+    """Config 5: network trained on solves of 20 seeded fields (roughness 0.3..0.7,
+    RHS_PER_FIELD each), evaluated on 5 unseen fields (roughness 0.3, 0.4, ..., 0.7):
+    CG iterations to 1e-10 for the 4 smallest shifts from the zero vector, from the
+    Lagrange guess (Sec. 4.2.1) and from the learned guess, over the 8 solved shifts
+    just above each target."""
+    import numpy as np
+    import torch
+
+    import paper_1805_09584_gb300 as tm
+    import synth
+    from paper_1805_09584_gb300 import _build, learned
+
+    _build.build()
+    torch.cuda.set_device(0)
+    dims = (48, 24, 24, 24)
+    sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
+    per_field = int(os.environ.get("RHS_PER_FIELD", "10"))
+    t0 = time.perf_counter()
+    Xs, Ss, Hs = [], [], []
+    for f in range(20):
+        r = 0.3 + 0.4 * ((f * 37) % 100) / 100.0
+        g = tm.Gauge(synth.random_su3_field(dims, r, f), dims, KAPPA, MU_BAR, EPS_BAR)
+        for bk in synth.gaussian_rhs(dims, 3000 + 16 * f, nrhs=per_field):
+            bd = g.pack(torch.from_numpy(bk[None]).cuda())
+            xn, info, hist = learned.solve_nodes(g, bd, sig, prec=tm.TMND_S16)
+            X, S, H = learned.samples(g, bd, sig, xn, info, hist)
+            Xs.append(X); Ss.append(S); Hs.append(H)
+            del xn
+        g.close()
+    t_data = time.perf_counter() - t0
+    net, losses = learned.train(np.concatenate(Xs), np.concatenate(Ss), np.concatenate(Hs), epochs=800)
+    t_train = time.perf_counter() - t0 - t_data
+    it = {"zero": np.zeros((5, 4), int), "lagrange": np.zeros((5, 4), int), "learned": np.zeros((5, 4), int)}
+    gres = {"lagrange": np.zeros((5, 4)), "learned": np.zeros((5, 4))}
+    for e in range(5):
+        r = 0.3 + 0.1 * e
+        g = tm.Gauge(synth.random_su3_field(dims, r, 100 + e), dims, KAPPA, MU_BAR, EPS_BAR)
+        b = synth.gaussian_rhs(dims, 5000 + e)
+        bd = g.pack(torch.from_numpy(b).cuda())
+        xn, info, hist = learned.solve_nodes(g, bd, sig, prec=tm.TMND_S16)
+        X, S, H = learned.samples(g, bd, sig, xn, info, hist)
+        w_net = learned.predict(net, X, S)
+        for q in range(4):
+            t = float(sig[8 + q])
+            nodes_x = xn[q:q + 8]
+            wl = learned.lagrange_weights(sig[q:q + 8], t)
+            z = tm.mms_cg_solve(g.handle, bd, 1, [t], [g.spinor()], rho=RHO)
+            it["zero"][e, q] = z["iters"]
+            it["lagrange"][e, q], gres["lagrange"][e, q] = learned.iterations_from_guess(g, bd, nodes_x, wl, t)
+            it["learned"][e, q], gres["learned"][e, q] = learned.iterations_from_guess(g, bd, nodes_x, w_net[q], t)
+        g.close()
+    tm.tmnd_mlp_destroy(net)
+    tot = {k: int(v.sum()) for k, v in it.items()}
+    return {"study": "learned guesses (config 5)", "lattice": "24^3x48",
+            "training": {"fields": 20, "rhs_per_field": per_field, "solves": 20 * per_field,
+                         "samples": int(sum(len(x) for x in Xs)), "data_s": t_data, "train_s": t_train,
+                         "loss_first_last": [losses[0], losses[-1]]},
+            "evaluation": "5 unseen fields (roughness 0.3..0.7), 1 RHS each; FP64 CG iterations to rel. residual "
+                          "1e-10 for shifts 8..11 (the 4 smallest) from each guess",
+            "iterations": {k: v.tolist() for k, v in it.items()}, "iterations_total": tot,
+            "guess_rel_residual": {k: [[float("%.3g" % x) for x in row] for row in v] for k, v in gres.items()},
+            "saved_vs_lagrange": tot["lagrange"] - tot["learned"], "saved_vs_zero": tot["zero"] - tot["learned"]}
+
+
 # FP64 peak of a GB300 (sm_103a): 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -711,10 +779,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "batched", "hybrid", "learned", "rational"])
     ap.add_argument("--kernel", default=None, choices=["fp64", "s16", "coarse"])
-    ap.add_argument("--study", default=None, choices=["hybrid"])
+    ap.add_argument("--study", default=None, choices=["hybrid", "learned"])
     args = ap.parse_args()
     if args.study:
-        print(json.dumps(run_study(args)))
+        print(json.dumps(run_study(args) if args.study == "hybrid" else run_study_learned(args)))
         return
     if args.kernel:
         print(json.dumps(run_kernel(args)))
