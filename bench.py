@@ -540,19 +540,23 @@ def run_kernel(args):
         out.update(lattice="16^3x32", ms_qhat2=ms, tflops=tf, fp64_peak_tflops=FP64_PEAK_TFLOPS,
                    frac=tf / FP64_PEAK_TFLOPS, gbs=4 * HOP_BYTES_PER_SITE * g.vh / (ms / 1e3) / 1e9)
     elif args.kernel == "s16":
-        dims = (48, 24, 24, 24)
-        g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
-        for R in (1, 8):
-            b = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, 2003, nrhs=R)).cuda(), nrhs=R)
-            q = g.convert(b, tm.TMND_F64, tm.TMND_S16, nrhs=R)
-            o = g.spinor(R, prec=tm.TMND_S16)
-            del b
-            ms = timed(lambda: tm.tm_nd_apply(g.handle, o, q, tm.OP_QHAT2 | tm.OP_S16, 0.01, nrhs=R, stream=stream))
-            # links are read once per launch for all R right-hand sides
-            byts = g.vh * (R * (2 * (200 + 300) + 100) + 4 * 192)
-            out[f"nrhs{R}"] = {"ms_qhat2": ms, "ms_per_rhs": ms / R, "gbs": byts / (ms / 1e3) / 1e9,
-                               "frac_hbm": byts / (ms / 1e3) / 1e9 / peak_hbm}
-        out.update(lattice="24^3x48", hbm_peak_gbs=peak_hbm)
+        for dims, name, rs in (((48, 24, 24, 24), "24^3x48", (1, 8)), ((64, 32, 32, 32), "32^3x64", (1,))):
+            g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
+            for R in rs:
+                b = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, 2003, nrhs=R)).cuda(), nrhs=R)
+                q = g.convert(b, tm.TMND_F64, tm.TMND_S16, nrhs=R)
+                o = g.spinor(R, prec=tm.TMND_S16)
+                del b
+                ms = timed(lambda: tm.tm_nd_apply(g.handle, o, q, tm.OP_QHAT2 | tm.OP_S16, 0.01, nrhs=R,
+                                                  stream=stream))
+                # links are read once per launch for all R right-hand sides
+                byts = g.vh * (R * (2 * (200 + 300) + 100) + 4 * 192)
+                out[f"{name}_nrhs{R}"] = {"ms_qhat2": ms, "ms_per_rhs": ms / R, "gbs": byts / (ms / 1e3) / 1e9,
+                                          "frac_hbm": byts / (ms / 1e3) / 1e9 / peak_hbm}
+                del q, o
+            g.close()
+        out.update(hbm_peak_gbs=peak_hbm)
+        return out
     else:
         dims, nv = (48, 24, 24, 24), 24
         g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)

@@ -62,11 +62,12 @@ typedef enum {
 typedef enum {
     TMND_F64 = 0,          /* FP64 storage and arithmetic: 24 complex128 planes per RHS */
     TMND_F32 = 1,          /* FP32 storage: 24 complex64 planes per RHS */
-    TMND_S16 = 2           /* 16-bit fixed-point storage with FP32 arithmetic: 6 planes of
-                              16-byte words over V/2 sites (word = one complex component,
-                              real part in the low 16 bits, imaginary in the high 16 bits,
-                              component c = flavour*12 + spin*3 + colour, plane c/4), then
-                              V/2 floats: the per-site scale max|v|/32767 */
+    TMND_S16 = 2           /* 16-bit fixed-point storage with FP32 arithmetic, in blocks of
+                              8 consecutive sites (800 bytes): 6 planes of 8 16-byte words
+                              (word = one complex component, real part in the low 16 bits,
+                              imaginary in the high 16 bits, component c = flavour*12 +
+                              spin*3 + colour, plane c/4), then the 8 sites' scales
+                              max|v|/32767 as floats; 100 bytes per site */
 } tmnd_prec;
 
 typedef enum {

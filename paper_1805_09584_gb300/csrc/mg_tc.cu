@@ -27,11 +27,13 @@
 //                  such accumulator pairs alternate between sites;
 //   warps 0, 1     epilogue: read rows 0..63 from tensor memory, add the mu_c /
 //                  eps_c terms and i s G_odd x with the flavours swapped, store y.
-// Every wait gives up after ~2^24 polls, sets *err and ends the kernel.  TF32
+// Every wait gives up after ~2 s (or once another warp has given up), sets *err,
+// waits (bounded) for the bulk copies still in flight and ends the kernel.  TF32
 // keeps 10 mantissa bits of each operand (relative error ~1e-3 per product),
 // ample for the coarse correction of the preconditioner.
 #include <stdint.h>
 
+#include "bulk.cuh"
 #include "tmnd_internal.cuh"
 
 namespace {
@@ -77,44 +79,11 @@ struct TCArgs {
     int *err;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
 // shared-memory matrix descriptor, no swizzle, K-major: lbo = byte step between core
 // matrices along K, sbo = byte step between 8-row groups along M (or N)
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
            ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-    for (int i = 0; i < (1 << 24); i++)
-        if (mbar_try(a, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16), counted on mbar
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mbar)
-                 : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -220,7 +189,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MAX_CTAS) k_coarse_apply_tc(TCA
             mbar_init(smem_u32(&acce[j]), 64);
         }
         *sflag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init_fence();
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tholder)),
@@ -236,10 +205,12 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MAX_CTAS) k_coarse_apply_tc(TCA
 
     // warps 2 and 3 run their loops warp-uniformly; lane 0 issues the copies / MMAs
     if (warp == 2) {  // producer
+        int issued = 0;
         for (int q = 0; q < nsite * nsteps; q++) {
             const int b = blockIdx.x + (q / nsteps) * gridDim.x, t = q % nsteps, s = q % S, k = q / S;
-            bool ok = k < 1 || mbar_wait(smem_u32(&empty[s]), (uint32_t)((k - 1) & 1));
+            bool ok = k < 1 || mbar_wait(smem_u32(&empty[s]), (uint32_t)((k - 1) & 1), sflag);
             if (__any_sync(0xffffffffu, !ok || *sflag)) { *sflag = 1; break; }
+            issued = q + 1;
             if (lane == 0) {
                 const uint32_t fb = smem_u32(&full[s]), dst = smem_u32(sm + s * stage);
                 mbar_expect_tx(fb, stage);
@@ -249,19 +220,23 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MAX_CTAS) k_coarse_apply_tc(TCA
             }
             __syncwarp();
         }
+        // after an error, wait (bounded) for the copies still in flight before the block ends
+        if (*sflag && lane == 0)
+            for (int q = issued - S > 0 ? issued - S : 0; q < issued; q++)
+                mbar_wait(smem_u32(&full[q % S]), (uint32_t)((q / S) & 1));
     } else if (warp == 3) {  // MMA issuer
         const uint32_t idesc =
             (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
         bool stop = false;
         for (int i = 0, q = 0; i < nsite && !stop; i++) {
             const int buf = i & 1, u = i >> 1;
-            bool ok = u < 1 || mbar_wait(smem_u32(&acce[buf]), (uint32_t)((u - 1) & 1));
+            bool ok = u < 1 || mbar_wait(smem_u32(&acce[buf]), (uint32_t)((u - 1) & 1), sflag);
             if (__any_sync(0xffffffffu, !ok || *sflag)) { *sflag = 1; break; }
             tc_fence_after();
             const uint32_t dmain = taddr + (uint32_t)(buf * 2 * N), dg = dmain + (uint32_t)N;
             for (int t = 0; t < nsteps; t++, q++) {
                 const int s = q % S, k = q / S;
-                ok = mbar_wait(smem_u32(&full[s]), (uint32_t)(k & 1));
+                ok = mbar_wait(smem_u32(&full[s]), (uint32_t)(k & 1), sflag);
                 if (__any_sync(0xffffffffu, !ok || *sflag)) { *sflag = 1; stop = true; break; }
                 tc_fence_after();
                 if (lane == 0) {
@@ -283,7 +258,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MAX_CTAS) k_coarse_apply_tc(TCA
         float acc[64], gz[64];
         for (int i = 0; i < nsite; i++) {
             const int b = blockIdx.x + i * gridDim.x, buf = i & 1, u = i >> 1;
-            const bool ok = mbar_wait(smem_u32(&accf[buf]), (uint32_t)(u & 1));
+            const bool ok = mbar_wait(smem_u32(&accf[buf]), (uint32_t)(u & 1), sflag);
             if (__any_sync(0xffffffffu, !ok || *sflag)) { *sflag = 1; break; }
             tc_fence_after();
             const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 2 * N);

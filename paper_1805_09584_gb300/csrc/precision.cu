@@ -1,8 +1,8 @@
 // Precision conversions of internal spinors and the 16-bit link packing.
 //   TMND_F64 : 24 planes of complex128 over V/2 sites
 //   TMND_F32 : 24 planes of complex64
-//   TMND_S16 : 6 int4 planes (16-bit fixed point, one word per complex
-//              component) + one float scale per site (see dslash_s16.cu)
+//   TMND_S16 : blocks of 8 sites, each 6 int4 planes (16-bit fixed point, one
+//              word per complex component) + the 8 float scales (tmnd_internal.cuh)
 #include <math.h>
 
 #include "tmnd_internal.cuh"
@@ -32,10 +32,10 @@ __device__ __forceinline__ void read_site(const void *src, int Vh, int h, float 
         }
     } else {
         const S16In s = s16_in(src, Vh);
-        const float sc = s.nrm[h];
+        const float sc = s.nrm[s16_ni(h)];
 #pragma unroll
         for (int j = 0; j < 6; j++) {
-            const int4 w = s.q[(size_t)j * Vh + h];
+            const int4 w = s.q[s16_qi(j, h)];
             const int ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -53,9 +53,9 @@ __global__ void k_s16_to_f64(int Vh, int nrhs, const char *src, char *dst) {
         const int k = (int)(i / Vh), h = (int)(i % Vh);
         const S16In s = s16_in(src + k * sb, Vh);
         double2 *d = (double2 *)(dst + k * db);
-        const double sc = s.nrm[h];
+        const double sc = s.nrm[s16_ni(h)];
         for (int j = 0; j < 6; j++) {
-            const int4 w = s.q[(size_t)j * Vh + h];
+            const int4 w = s.q[s16_qi(j, h)];
             const int ws[4] = {w.x, w.y, w.z, w.w};
             for (int m = 0; m < 4; m++)
                 d[(size_t)(4 * j + m) * Vh + h] = make_double2((double)s16_int_lo(ws[m]) * sc, (double)s16_int_hi(ws[m]) * sc);
@@ -74,11 +74,11 @@ __global__ void k_to_s16(int Vh, int nrhs, const char *src, size_t src_rhs_bytes
         for (int c = 0; c < 24; c++) m = fmaxf(m, fmaxf(fabsf(v[c][0]), fabsf(v[c][1])));
         const float sc = m > 0.0f ? QMAX / m : 0.0f;
         S16Out o = s16_out(dst + k * db, Vh);
-        o.nrm[h] = m / QMAX;
+        o.nrm[s16_ni(h)] = m / QMAX;
         for (int j = 0; j < 6; j++) {
             int w[4];
             for (int q = 0; q < 4; q++) w[q] = s16_pack_fma(v[4 * j + q][0], v[4 * j + q][1], sc);
-            o.q[(size_t)j * Vh + h] = make_int4(w[0], w[1], w[2], w[3]);
+            o.q[s16_qi(j, h)] = make_int4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -92,8 +92,9 @@ __global__ void k_f32_to_f64(long n, const float2 *src, double2 *dst) {
         dst[i] = make_double2(src[i].x, src[i].y);
 }
 
-// links: canonical complex128 [4][T][X][Y][Z][3][3] -> int2 [2 parity][4 mu][3 planes][Vh],
-// rows 0 and 1 rounded to integers at scale 32767, stored in the 16-bit word codec
+// links: canonical complex128 [4][T][X][Y][Z][3][3] -> int2 [2 parity][4 mu][3 Vh]
+// (per parity and direction blocks of 8 sites x 3 planes, s16_li), rows 0 and 1
+// rounded to integers at scale 32767, stored in the 16-bit word codec
 __global__ void k_pack_links_s16(Geom g, const double2 *__restrict__ canon, int2 *__restrict__ out) {
     const long V = 2L * g.Vh;
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;  // over 4 * V links
@@ -113,9 +114,9 @@ __global__ void k_pack_links_s16(Geom g, const double2 *__restrict__ canon, int2
         w[k] = s16_word((int)rint(u[k].x * 32767.0), (int)rint(u[k].y * 32767.0));
     }
     int2 *o = out + ((size_t)par * 4 + mu) * 3 * g.Vh;
-    o[0 * (size_t)g.Vh + h] = make_int2(w[0], w[1]);
-    o[1 * (size_t)g.Vh + h] = make_int2(w[2], w[3]);
-    o[2 * (size_t)g.Vh + h] = make_int2(w[4], w[5]);
+    o[s16_li(0, h)] = make_int2(w[0], w[1]);
+    o[s16_li(1, h)] = make_int2(w[2], w[3]);
+    o[s16_li(2, h)] = make_int2(w[4], w[5]);
 }
 
 int grid_for(long n) {

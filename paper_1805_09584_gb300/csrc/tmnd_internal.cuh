@@ -169,7 +169,12 @@ int hop_blocks(const Geom &g);
 
 // ------------------------------------------------- sloppy (16-bit) path
 
-// 16-bit spinor of one right-hand side: 6 int4 planes over V/2 sites, then V/2 floats (scale).
+// 16-bit spinor of one right-hand side, in blocks of 8 consecutive half-lattice
+// sites (V/2 is a multiple of 8 for even extents): a block is 800 bytes, 6 planes
+// of 8 int4 words (plane j of site h: complex components 4j..4j+3, one 32-bit
+// word each), then the 8 sites' float scales.  A run of consecutive sites that
+// starts and ends on block boundaries is one contiguous byte range.  q and nrm
+// hold the same base address, typed for the two kinds of element.
 struct S16In {
     const int4 *q;
     const float *nrm;
@@ -179,11 +184,20 @@ struct S16Out {
     float *nrm;
 };
 constexpr size_t S16_BYTES_PER_SITE = 6 * 16 + 4;
+constexpr int S16_BLOCK_SITES = 8;
+// int4 index of plane p of site h, float index of the scale of site h
+__host__ __device__ inline size_t s16_qi(int p, size_t h) { return (h >> 3) * 50 + (size_t)p * 8 + (h & 7); }
+__host__ __device__ inline size_t s16_ni(size_t h) { return (h >> 3) * 200 + 192 + (h & 7); }
+// 16-bit links of one (parity, direction), blocks of 8 sites: int2 index of plane j
+// (row-0/row-1 word pair j) of site h; a block is 192 bytes
+__host__ __device__ inline size_t s16_li(int j, size_t h) { return (h >> 3) * 24 + (size_t)j * 8 + (h & 7); }
 __host__ __device__ inline S16In s16_in(const void *base, int Vh) {
-    return S16In{(const int4 *)base, (const float *)((const char *)base + 96 * (size_t)Vh)};
+    (void)Vh;
+    return S16In{(const int4 *)base, (const float *)base};
 }
 __host__ __device__ inline S16Out s16_out(void *base, int Vh) {
-    return S16Out{(int4 *)base, (float *)((char *)base + 96 * (size_t)Vh)};
+    (void)Vh;
+    return S16Out{(int4 *)base, (float *)base};
 }
 
 constexpr int TMND_MAX_BATCH = 16;
@@ -258,10 +272,10 @@ __host__ __device__ inline int s16_word(int re, int im) {
 // Site-level 16-bit (de)quantisation shared by the sloppy solver kernels.
 // v[c][0/1] = real/imaginary part of component c = flavour*12 + spin*3 + colour.
 __device__ __forceinline__ void s16_load_site(S16In in, int Vh, int h, float v[24][2]) {
-    const float sc = in.nrm[h];
+    const float sc = in.nrm[s16_ni(h)];
 #pragma unroll
     for (int j = 0; j < 6; j++) {
-        const int4 w = in.q[(size_t)j * Vh + h];
+        const int4 w = in.q[s16_qi(j, h)];
         const int ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -276,12 +290,12 @@ __device__ __forceinline__ void s16_store_site(S16Out out, int Vh, int h, const 
 #pragma unroll
     for (int c = 0; c < 24; c++) m = fmaxf(m, fmaxf(fabsf(v[c][0]), fabsf(v[c][1])));
     const float sc = m > 0.0f ? S16_QMAX / m : 0.0f;
-    out.nrm[h] = m * (1.0f / S16_QMAX);
+    out.nrm[s16_ni(h)] = m * (1.0f / S16_QMAX);
 #pragma unroll
     for (int j = 0; j < 6; j++) {
         int w[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) w[k] = s16_pack_fma(v[4 * j + k][0], v[4 * j + k][1], sc);
-        out.q[(size_t)j * Vh + h] = make_int4(w[0], w[1], w[2], w[3]);
+        out.q[s16_qi(j, h)] = make_int4(w[0], w[1], w[2], w[3]);
     }
 }

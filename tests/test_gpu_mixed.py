@@ -100,11 +100,11 @@ def test_mixed_batched_rhs_match_one_at_a_time(nrhs, batch):
     g.close()
 
 
-def test_s16_multi_rhs_apply_equals_single():
+@pytest.mark.parametrize("dims", [(8, 6, 6, 6), (6, 4, 8, 16)])
+def test_s16_multi_rhs_apply_equals_single(dims):
     """One 16-bit stencil launch over 3 right-hand sides gives, bit for bit, the
     three single applications (same arithmetic per right-hand side)."""
     tm = require_gpu()
-    dims = (8, 6, 6, 6)
     U = synth.random_su3_field(dims, 0.4, 79)
     g = tm.Gauge(U, dims, KAPPA, MU, EPS)
     b = synth.gaussian_rhs(dims, 103, nrhs=3)

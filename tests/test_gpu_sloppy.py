@@ -43,11 +43,11 @@ def test_s16_roundtrip_bound(dims):
     g.close()
 
 
-# The two larger lattices are big enough for the stencil's column-march launch
-# shape (blocks walking up t over (x, y, z) columns); (58, 16, 16, 16) also has
-# blocks whose run of time slices continues into the next column.
+# Shapes: X = T = 2, Y = 2, rows of Z/2 = 1, 2, 4, 8, 12, 16 sites (parts of, one
+# and several 8-site blocks of the 16-bit layout), 58 time slices.
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 6, 8), (8, 4, 6, 2), (2, 2, 2, 4), (32, 16, 16, 16),
-                                  (58, 16, 16, 16)])
+                                  (58, 16, 16, 16), (4, 4, 32, 32), (4, 2, 48, 24), (4, 2, 40, 32), (4, 4, 2, 8),
+                                  (2, 2, 4, 8)])
 @pytest.mark.parametrize("op,tol", [("mhat", 1e-4), ("mhat_dag", 1e-4), ("qhat2", 2e-4)])
 def test_s16_apply_matches_oracle(dims, op, tol):
     tm, U, g = _gauge(dims)
