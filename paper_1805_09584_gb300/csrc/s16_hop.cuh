@@ -21,6 +21,8 @@ constexpr float INV_QMAX = 1.0f / S16_QMAX;
 using f2 = float2;  // (flavour 0, flavour 1)
 
 __device__ __forceinline__ f2 dup(float a) { return make_float2(a, a); }
+// -a by flipping the sign bit on the integer pipe (keeps the FP32 pipe for products)
+__device__ __forceinline__ float fneg(float a) { return __int_as_float(__float_as_int(a) ^ (int)0x80000000); }
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
@@ -58,13 +60,15 @@ __device__ __forceinline__ f2 comb(f2 u, f2 l) {
 template <int MU, int DIR, bool G5IN, bool FIRST>
 __device__ __forceinline__ void hop_dir(const Raw &r, float sign, f2 acc[4][3][2]) {
     // link rows 0 and 1 (integer-valued floats, scale 32767) and rebuilt row 2 (same scale)
-    float ur[3][3], ui[3][3];
+    // (ni = -ui: each output component below is one fused chain of six products)
+    float ur[3][3], ui[3][3], ni[3][3];
     {
         const int wv[6] = {r.l[0].x, r.l[0].y, r.l[1].x, r.l[1].y, r.l[2].x, r.l[2].y};
 #pragma unroll
         for (int k = 0; k < 6; k++) {
             ur[k / 3][k % 3] = s16_lo(wv[k]);
             ui[k / 3][k % 3] = s16_hi(wv[k]);
+            ni[k / 3][k % 3] = fneg(ui[k / 3][k % 3]);
         }
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -75,6 +79,7 @@ __device__ __forceinline__ void hop_dir(const Raw &r, float sign, f2 acc[4][3][2
             im = fmaf(-ur[0][k2], ui[1][k1], fmaf(-ui[0][k2], ur[1][k1], im));
             ur[2][k] = re * INV_QMAX;
             ui[2][k] = -im * INV_QMAX;
+            ni[2][k] = fneg(ui[2][k]);
         }
     }
     // projection chi = u -+ B l (upper spins 0, 1), exact integers.
@@ -118,33 +123,28 @@ __device__ __forceinline__ void hop_dir(const Raw &r, float sign, f2 acc[4][3][2
     f2 vr[2][3], vi[2][3];
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        f2 wr[3], wi[3];
+        // re = sum_j wr_j chr_j + wa_j chi_j,  im = sum_j wr_j chi_j + wb_j chr_j
+        f2 wr[3], wa[3], wb[3];
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             wr[j] = dup(DIR > 0 ? ur[i][j] : ur[j][i]);
-            wi[j] = dup(DIR > 0 ? ui[i][j] : ui[j][i]);
+            wa[j] = dup(DIR > 0 ? ni[i][j] : ui[j][i]);
+            wb[j] = dup(DIR > 0 ? ui[i][j] : ni[j][i]);
         }
 #pragma unroll
         for (int s = 0; s < 2; s++) {
             f2 a = mul2(wr[0], chr[s][0]);
             a = fma2(wr[1], chr[s][1], a);
             a = fma2(wr[2], chr[s][2], a);
-            f2 b = mul2(wi[0], chi[s][0]);
-            b = fma2(wi[1], chi[s][1], b);
-            b = fma2(wi[2], chi[s][2], b);
-            f2 c = mul2(wr[0], chi[s][0]);
-            c = fma2(wr[1], chi[s][1], c);
-            c = fma2(wr[2], chi[s][2], c);
-            f2 d = mul2(wi[0], chr[s][0]);
-            d = fma2(wi[1], chr[s][1], d);
-            d = fma2(wi[2], chr[s][2], d);
-            if (DIR > 0) {
-                vr[s][i] = fma2(b, dup(-1.0f), a);
-                vi[s][i] = add2(c, d);
-            } else {
-                vr[s][i] = add2(a, b);
-                vi[s][i] = fma2(d, dup(-1.0f), c);
-            }
+            a = fma2(wa[0], chi[s][0], a);
+            a = fma2(wa[1], chi[s][1], a);
+            vr[s][i] = fma2(wa[2], chi[s][2], a);
+            f2 b = mul2(wr[0], chi[s][0]);
+            b = fma2(wr[1], chi[s][1], b);
+            b = fma2(wr[2], chi[s][2], b);
+            b = fma2(wb[0], chr[s][0], b);
+            b = fma2(wb[1], chr[s][1], b);
+            vi[s][i] = fma2(wb[2], chr[s][2], b);
         }
     }
     // accumulate: upper spins += cs v; lower spins += cl B^+ v
