@@ -84,7 +84,9 @@ HOP_BYTES_PER_SITE = (240 + 288) / 2 * 8
 FP64_ODD_LAUNCH_TRAFFIC = 132.866816e6 + 9.036288e6
 # DRAM bytes of the 16-bit stencil at 24^3x48 (V/2 = 331776), one ncu capture: even launch
 # 98.22 + 3.71 MB, odd launch 134.10 + 7.79 MB; Qhat^2 = 2 even + 2 odd launches
-S16_Q2_TRAFFIC_24 = 2 * (98.223360e6 + 3.709952e6) + 2 * (134.103296e6 + 7.787264e6)
+# DRAM bytes (read + write) of one 16-bit Qhat^2 + sigma at 24^3x48: the 4 launches of one ncu capture
+S16_Q2_TRAFFIC_24 = (97.503232e6 + 3.967232e6) + (132.547840e6 + 8.404480e6) + (97.519360e6 + 3.632896e6) \
+    + (169.893632e6 + 15.372288e6)
 S16_TRAFFIC_VH = 331776
 
 
@@ -337,7 +339,8 @@ def s16_roofline(tm, g, flush, stream, reps=20):
     return {"bound": "hbm", "kernel": "k_hop_even_s16/k_hop_odd_s16 (16-bit stencil, Qhat^2 + sigma: 4 launches)",
             "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
             "traffic": S16_Q2_TRAFFIC_24 * g.vh / S16_TRAFFIC_VH,
-            "traffic_note": "DRAM bytes per Qhat^2 from an ncu capture at 24^3x48 (2 even + 2 odd launches)"
+            "traffic_note": "DRAM bytes per Qhat^2 from an ncu capture at 24^3x48 (its 4 launches; below the "
+                            "algorithmic bytes because each launch's output is still in L2 when the next reads it)"
                             + (", scaled by the number of sites" if scaled else ""),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if _peaks().get("hbm_gbs") else "fallback 6.8 TB/s",
             "measured": f"median of {reps} CUDA-event timings of tm_nd_apply(Qhat^2, 16-bit), L2 flushed",
