@@ -30,6 +30,8 @@ true residual:
 Each form's line also times the plain FP64 multi-shift CG on its workload
 ("fp64_same_workload") and reports a roofline for its dominant kernel.
 
+--study errors runs App. A's comparison of equivalent solutions (methods A-F) on the
+16^3x32 field against a known solution, rho = 1e-2 .. 1e-10.
 --study learned runs config 5: train on solves of 20 fields, evaluate on 5 unseen
 fields (CG iterations for the 4 smallest shifts from zero, Lagrange and learned guesses).
 --study hybrid measures the hybrid cost model of Sec. 4.3 on GB300 (24^3x48):
@@ -712,6 +714,58 @@ def run_study_learned(args):
             "saved_vs_lagrange": tot["lagrange"] - tot["learned"], "saved_vs_zero": tot["zero"] - tot["learned"]}
 
 
+
+def run_study_errors(args):
+    """App. A (error and residual of equivalent solutions) on the 16^3x32 field: a known
+    Gaussian x, b = (Qhat^2 + mu^2) x, methods A (direct), B (two consecutive single
+    systems), C (i/(2 mu) (x_+ - x_-)) and, for (Qhat + i mu) x_+ = b, methods D, E, F,
+    each stopped at rho; |r|/|b|, |e|/|b|, the smallest / largest site norm of e and
+    App. A's upper limits (extreme eigenvalues of Qhat^2 from Ritz values)."""
+    import numpy as np
+    import torch
+
+    import paper_1805_09584_gb300 as tm
+    import synth
+    from paper_1805_09584_gb300 import _build, equivalent
+
+    _build.build()
+    torch.cuda.set_device(0)
+    dims = DIMS
+    g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, GAUGE_SEED), dims, KAPPA, MU_BAR, EPS_BAR)
+    x = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, 4000)).cuda())
+    hist = np.zeros(8192)
+    xr = [g.spinor()]
+    inf = tm.mms_cg_solve(g.handle, x, 1, [1e-6], xr, rho=1e-8, ab_hist=hist)
+    f = tm.tmnd_mlp_features(synth.shift_set(8, 1e-4, 1.0), 1e-5, hist, inf["iters"], 1e-6)
+    lmin, lmax = 10 ** float(f[17]), 10 ** float(f[18])
+    t0 = time.perf_counter()
+    rows = []
+    for mu2 in (1e-1, 1e-3, 1e-5):
+        mu = float(np.sqrt(mu2))
+        b = g.spinor()
+        tm.tm_nd_apply(g.handle, b, x, tm.OP_QHAT2, mu2)
+        xp_exact = equivalent.qpm(g, x, mu, -1)          # (Qhat + i mu)^-1 b = (Qhat - i mu) x
+        for rho in (1e-2, 1e-4, 1e-6, 1e-8, 1e-10):
+            sols, one = equivalent.equivalent_solutions(g, b, mu, rho)
+            lim = equivalent.app_a_limits(rho, lmin, lmax, mu)
+            row = {"mu2": mu2, "rho": rho}
+            for c in "ABC":
+                row[c] = equivalent.residual_and_error(g, b, x, sols[c], mu)
+                row[c]["limits"] = list(lim[c])
+            for m in "DEF":
+                row[m] = equivalent.residual_and_error(g, b, xp_exact, one[(m, +1)], mu, +1)
+                row[m]["limits"] = list(lim[m])
+            rows.append(row)
+            del sols, one
+    g.close()
+    return {"study": "App. A equivalent solutions", "lattice": "16^3x32", "kappa": KAPPA, "mu_bar": MU_BAR,
+            "eps_bar": EPS_BAR, "x": "complex Gaussian, seed 4000", "lambda_min": lmin, "lambda_max": lmax,
+            "spectrum": "extreme Ritz values of an FP64 CG history (sigma = 1e-6)",
+            "normalisation": "|r| and |e| divided by |b|; site norms of e divided by the largest site norm of b",
+            "single_systems": "(Qhat + i mu) x_+ = b, exact x_+ = (Qhat - i mu) x", "seconds": time.perf_counter() - t0,
+            "rows": rows}
+
+
 # FP64 peak of a GB300 (sm_103a): 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -786,10 +840,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "batched", "hybrid", "learned", "rational"])
     ap.add_argument("--kernel", default=None, choices=["fp64", "s16", "coarse"])
-    ap.add_argument("--study", default=None, choices=["hybrid", "learned"])
+    ap.add_argument("--study", default=None, choices=["hybrid", "learned", "errors"])
     args = ap.parse_args()
     if args.study:
-        print(json.dumps(run_study(args) if args.study == "hybrid" else run_study_learned(args)))
+        fn = {"hybrid": run_study, "learned": run_study_learned, "errors": run_study_errors}[args.study]
+        print(json.dumps(fn(args)))
         return
     if args.kernel:
         print(json.dumps(run_kernel(args)))

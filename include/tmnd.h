@@ -406,6 +406,25 @@ tmnd_status tmnd_gram(const tmnd_gauge *g, const void *const *xs, int k, double 
 tmnd_status tmnd_lincomb(const tmnd_gauge *g, const double *w, const void *const *xs, int k, void *out, int nrhs,
                          void *stream);
 
+/* ------------------------------------------- equivalent solutions (App. A, error and residual)
+ * The study of App. A compares solutions of (Qhat^2 + mu^2) x = b that agree in exact
+ * arithmetic: A, the direct solve; B, two consecutive solves with (Qhat +- i mu);
+ * C, x_C = i/(2 mu) (x_+ - x_-) (Eq. "linear-combination"), with errors and residuals
+ * against a known solution.  These two calls supply the complex combinations and the
+ * local deviations; the solves are mms_cg_solve and tm_nd_apply (TMND_OP_QHAT).
+ *
+ * tmnd_lincomb_c: out = sum_j w_j xs[j] with complex weights, w = 2k doubles (re, im
+ *   interleaved, host), k <= 8 internal FP64 spinors of nrhs right-hand sides each
+ *   (device, 16-byte aligned); out may be one of the xs (element by element).
+ *   Stream-ordered.  TMND_ERR_ARG for NULL, misaligned or non-finite arguments. */
+tmnd_status tmnd_lincomb_c(const tmnd_gauge *g, const double *w, const void *const *xs, int k, void *out, int nrhs,
+                           void *stream);
+/* tmnd_site_norm_range: smallest and largest site norm |x(site)| (all 24 components of
+ *   one odd site, FP64) over the nrhs internal FP64 spinors at x (device); min_max: 2
+ *   doubles (host).  The "minimal and maximal local deviation" of App. A when x is an
+ *   error vector.  Synchronous. */
+tmnd_status tmnd_site_norm_range(const tmnd_gauge *g, const void *x, int nrhs, double *min_max, void *stream);
+
 /* ------------------------------------------------------------ rational approximation
  * Zolotarev's optimal rational approximation of 1/sqrt(y) on eps < y < 1 (Sec. 4.1,
  * Eqs. "rational", "deviation", "zolotarev_shifts"):

@@ -524,3 +524,67 @@ def fit_mg_time(sig, t, L, grid=2001):
         if best is None or r < best[0]:
             best = (r, float(sol[0]), float(sol[1]), float(C))
     return best[1], best[2], best[3]
+
+
+# ------------------------------------------- equivalent solutions (App. A, squared operator)
+def single_system_solves(act: Action, links, b, mu, rho=1e-10):
+    """Solutions of the single systems (Qhat +- i mu) x_pm = b (App. A, methods E, F and D).
+    Qhat is hermitian, so (Qhat +- i mu)^-1 = (Qhat -+ i mu) (Qhat^2 + mu^2)^-1.
+      E (normal equation, transformed right-hand side): x = CG[(Qhat -+ i mu) b], stopped
+        at rho |(Qhat -+ i mu) b|;
+      F (normal equation, transformed solution): y = CG[b], x = (Qhat -+ i mu) y;
+      D (a solve of the single system to |b - (Qhat +- i mu) x| <= rho |b|): E followed by one
+        F step on its residual, x += (Qhat -+ i mu) CG[r], stopped at rho |b| / |r|.
+    Returns {("E"|"F"|"D", +1|-1): x}; CG is the oracle's plain CG on (Qhat^2 + mu^2)."""
+    b = _c128(b)
+    s2 = float(mu) * float(mu)
+    qb = qhat(act, links, b)
+    y, _ = cg(act, links, b, s2, rho)
+    qy = qhat(act, links, y)
+    out = {}
+    bn = np.linalg.norm(b)
+    for sg in (+1, -1):
+        xe, _ = cg(act, links, qb - sg * 1j * mu * b, s2, rho)
+        out[("E", sg)] = xe
+        out[("F", sg)] = qy - sg * 1j * mu * y
+        r = b - (qhat(act, links, xe) + sg * 1j * mu * xe)
+        rn = np.linalg.norm(r)
+        xd = xe.copy()
+        if rn > rho * bn:
+            d, _ = cg(act, links, r, s2, min(0.5, rho * bn / rn))
+            xd = xd + (qhat(act, links, d) - sg * 1j * mu * d)
+        out[("D", sg)] = xd
+    return out
+
+
+def equivalent_solutions(act: Action, links, b, mu, rho=1e-10):
+    """The three solutions of (Qhat^2 + mu^2) x = b compared in App. A (squared
+    twisted-mass operator):
+      A: x_A = CG[b] (Eq. "direct");
+      B: x_+ = (Qhat + i mu)^-1 b, then x_B = (Qhat - i mu)^-1 x_+, each single system solved
+         as method D above, the second to |x_+ - (Qhat - i mu) x_B| <= rho |x_+| (Eq. "two-step");
+      C: x_C = i/(2 mu) (x_+ - x_-), x_pm by method D (Eq. "linear-combination").
+    Returns {"A", "B", "C", "p", "m"} (p, m = x_+, x_-)."""
+    b = _c128(b)
+    one = single_system_solves(act, links, b, mu, rho)
+    xp, xm = one[("D", +1)], one[("D", -1)]
+    xA, _ = cg(act, links, b, float(mu) * float(mu), rho)
+    xB = single_system_solves(act, links, xp, -mu, rho)[("D", +1)]   # (Qhat - i mu)^-1 x_+
+    xC = 1j / (2.0 * mu) * (xp - xm)
+    return {"A": xA, "B": xB, "C": xC, "p": xp, "m": xm}
+
+
+def equivalent_bounds(rho, bnorm, lmin, lmax, mu):
+    """Upper limits of App. A for |r| and |e| of methods A, B, C (squared operator) and
+    D, E, F (single systems), for sub-solves that meet their stopping criteria; lmin,
+    lmax are the extreme eigenvalues of Qhat^2 (the paper's lambda^2_min, lambda^2_max)."""
+    m2 = float(mu) ** 2
+    lo, hi = lmin + m2, lmax + m2
+    return {
+        "A": (rho * bnorm, rho * bnorm / lo),
+        "B": ((1.0 + np.sqrt(hi / lo)) * rho * bnorm, 2.0 * rho * bnorm / lo),
+        "C": (rho * np.sqrt(hi) * bnorm / abs(mu), rho * bnorm / (abs(mu) * np.sqrt(lo))),
+        "D": (rho * bnorm, rho * bnorm / np.sqrt(lo)),
+        "E": (rho * bnorm * np.sqrt(hi / lo), rho * bnorm * np.sqrt(hi) / lo),
+        "F": (rho * bnorm, rho * bnorm / np.sqrt(lo)),
+    }

@@ -35,7 +35,7 @@ EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd
            "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve", "tmnd_mlp_num_params", "tmnd_mlp_create",
            "tmnd_mlp_destroy", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad", "tmnd_mlp_train_step", "tmnd_mlp_predict",
            "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_zolotarev", "tmnd_rational_apply",
-           "tmnd_hybrid_cost", "tmnd_fit_cg_time", "tmnd_fit_mg_time")
+           "tmnd_hybrid_cost", "tmnd_fit_cg_time", "tmnd_fit_mg_time", "tmnd_lincomb_c", "tmnd_site_norm_range")
 NOALLOC_MAX_VH = 32768
 
 
@@ -142,6 +142,8 @@ def lib() -> ctypes.CDLL:
         L.tmnd_mlp_features.argtypes = [ctypes.POINTER(d), d, vp, i, d, fp]
         L.tmnd_gram.argtypes = [vp, ctypes.POINTER(vp), i, ctypes.POINTER(d), vp]
         L.tmnd_lincomb.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(vp), i, vp, i, vp]
+        L.tmnd_lincomb_c.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(vp), i, vp, i, vp]
+        L.tmnd_site_norm_range.argtypes = [vp, vp, i, ctypes.POINTER(d), vp]
         pd = ctypes.POINTER(d)
         L.tmnd_zolotarev.argtypes = [i, d, pd, pd, pd, pd]
         L.tmnd_hybrid_cost.argtypes = [pd, i, pd, pd, pd, ctypes.POINTER(i)]
@@ -152,7 +154,8 @@ def lib() -> ctypes.CDLL:
         for name in ("tmnd_mlp_create", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad",
                      "tmnd_mlp_train_step", "tmnd_zolotarev", "tmnd_rational_apply", "tmnd_hybrid_cost",
                      "tmnd_fit_cg_time", "tmnd_fit_mg_time",
-                     "tmnd_mlp_predict", "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb"):
+                     "tmnd_mlp_predict", "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_lincomb_c",
+                     "tmnd_site_norm_range"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
                      "tmnd_dnd_full_apply", "tmnd_mg_solve", "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve"):
@@ -416,6 +419,24 @@ def tmnd_lincomb(h, w, xs, out, nrhs: int = 1, stream=None) -> None:
     arr = (ctypes.c_void_p * k)(*[_ptr(v) for v in xs])
     _check(lib().tmnd_lincomb(h, ww.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), arr, k, _ptr(out), int(nrhs),
                               _stream(stream)))
+
+
+def tmnd_lincomb_c(h, w, xs, out, nrhs: int = 1, stream=None) -> None:
+    """out = sum_j w_j xs[j] with complex weights w (App. A combinations)."""
+    w = np.asarray(w, np.complex128)
+    ww = np.ascontiguousarray(np.stack([w.real, w.imag], axis=1).ravel(), np.float64)
+    k = len(xs)
+    arr = (ctypes.c_void_p * k)(*[_ptr(v) for v in xs])
+    _check(lib().tmnd_lincomb_c(h, ww.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), arr, k, _ptr(out),
+                                int(nrhs), _stream(stream)))
+
+
+def tmnd_site_norm_range(h, x, nrhs: int = 1, stream=None):
+    """(smallest, largest) site norm of internal FP64 spinors x (App. A local deviations)."""
+    mm = np.zeros(2, np.float64)
+    _check(lib().tmnd_site_norm_range(h, _ptr(x), int(nrhs), mm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      _stream(stream)))
+    return float(mm[0]), float(mm[1])
 
 
 def _hp(a):

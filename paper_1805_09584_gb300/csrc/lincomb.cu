@@ -3,6 +3,7 @@
 // The weights are k <= 8 FP64 numbers computed on the host; the combination
 // is one bandwidth-bound pass (k reads, one write per element).
 #include <math.h>
+#include <string.h>
 
 #include "tmnd_internal.cuh"
 
@@ -88,5 +89,119 @@ extern "C" tmnd_status tmnd_lincomb(const tmnd_gauge *g, const double *w, const 
     long want = (n + 255) / 256, cap = (long)sms * 8;
     k_lincomb<<<(unsigned)(want < cap ? want : cap), 256, 0, (cudaStream_t)stream>>>(n, a, (double2 *)out);
     TMND_CUDA_TRY(cudaGetLastError());
+    return TMND_OK;
+}
+
+// ------------------------------------------------ complex combinations, site norms
+// Used by the study of equivalent solutions (App. A): x_C = i/(2 mu) (x_+ - x_-),
+// (Qhat -+ i mu) y = Qhat y -+ i mu y, and the smallest / largest local deviation
+// (norm of one site's 24 components) of an error vector.
+namespace {
+
+struct CLinArgs {
+    const double2 *x[MAXK];
+    double2 w[MAXK];
+    int k;
+};
+
+__global__ void k_lincomb_c(long n, CLinArgs a, double2 *__restrict__ out) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int j = 0; j < MAXK; j++) {
+            if (j < a.k) {
+                const double2 v = a.x[j][i];
+                acc.x = fma(a.w[j].x, v.x, fma(-a.w[j].y, v.y, acc.x));
+                acc.y = fma(a.w[j].x, v.y, fma(a.w[j].y, v.x, acc.y));
+            }
+        }
+        out[i] = acc;
+    }
+}
+
+// per-site squared norms folded into a min and a max (non-negative doubles order
+// like their bit patterns, so integer atomics give an exact, order-free result)
+__global__ void k_site_norm_range(int Vh, int nrhs, const double2 *__restrict__ x, unsigned long long *mm) {
+    unsigned long long lo = ~0ull, hi = 0ull;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < (long)Vh * nrhs; i += (long)gridDim.x * blockDim.x) {
+        const long k = i / Vh, h = i % Vh;
+        const double2 *xk = x + (size_t)k * 24 * Vh;
+        double s = 0.0;
+        for (int c = 0; c < 24; c++) {
+            const double2 v = xk[(size_t)c * Vh + h];
+            s = fma(v.x, v.x, fma(v.y, v.y, s));
+        }
+        const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+        lo = b < lo ? b : lo;
+        hi = b > hi ? b : hi;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        lo = l2 < lo ? l2 : lo;
+        hi = h2 > hi ? h2 : hi;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&mm[0], lo);
+        atomicMax(&mm[1], hi);
+    }
+}
+
+}  // namespace
+
+extern "C" tmnd_status tmnd_lincomb_c(const tmnd_gauge *g, const double *w, const void *const *xs, int k, void *out,
+                                      int nrhs, void *stream) {
+    TMND_ARG_CHECK(g && w && xs && out, "tmnd_lincomb_c: NULL argument");
+    TMND_ARG_CHECK(k >= 1 && k <= MAXK && nrhs >= 1, "tmnd_lincomb_c: k = %d not in [1, %d]", k, MAXK);
+    TMND_ARG_CHECK(((uintptr_t)out & 15) == 0, "tmnd_lincomb_c: out misaligned");
+    cudaGetLastError();
+    CLinArgs a = {};
+    a.k = k;
+    for (int j = 0; j < k; j++) {
+        TMND_ARG_CHECK(xs[j] && ((uintptr_t)xs[j] & 15) == 0 && isfinite(w[2 * j]) && isfinite(w[2 * j + 1]),
+                       "tmnd_lincomb_c: bad xs[%d] or weight", j);
+        a.x[j] = (const double2 *)xs[j];
+        a.w[j] = make_double2(w[2 * j], w[2 * j + 1]);
+    }
+    const long n = (long)(tmnd_spinor_bytes(g) / sizeof(double2)) * nrhs;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long want = (n + 255) / 256, cap = (long)sms * 8;
+    k_lincomb_c<<<(unsigned)(want < cap ? want : cap), 256, 0, (cudaStream_t)stream>>>(n, a, (double2 *)out);
+    TMND_CUDA_TRY(cudaGetLastError());
+    return TMND_OK;
+}
+
+extern "C" tmnd_status tmnd_site_norm_range(const tmnd_gauge *g, const void *x, int nrhs, double *min_max,
+                                            void *stream) {
+    TMND_ARG_CHECK(g && x && min_max && nrhs >= 1, "tmnd_site_norm_range: bad arguments");
+    TMND_ARG_CHECK(((uintptr_t)x & 15) == 0, "tmnd_site_norm_range: x misaligned");
+    cudaGetLastError();
+    unsigned long long *mm = nullptr;
+    TMND_CUDA_TRY(cudaMallocAsync((void **)&mm, 2 * sizeof(unsigned long long), (cudaStream_t)stream));
+    const unsigned long long init[2] = {~0ull, 0ull};
+    cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    const int Vh = g->geom.Vh;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long n = (long)Vh * nrhs;
+    long want = (n + 255) / 256, cap = (long)sms * 4;
+    k_site_norm_range<<<(unsigned)(want < cap ? want : cap), 256, 0, (cudaStream_t)stream>>>(Vh, nrhs,
+                                                                                           (const double2 *)x, mm);
+    unsigned long long res[2] = {0, 0};
+    cudaMemcpyAsync(res, mm, sizeof(res), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    cudaFreeAsync(mm, (cudaStream_t)stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        tmnd_set_error("tmnd_site_norm_range: %s", cudaGetErrorString(e));
+        return TMND_ERR_CUDA;
+    }
+    double lo, hi;
+    memcpy(&lo, &res[0], 8);
+    memcpy(&hi, &res[1], 8);
+    min_max[0] = sqrt(lo);
+    min_max[1] = sqrt(hi);
     return TMND_OK;
 }
