@@ -99,6 +99,27 @@ def _dist():
     return ws, rank, local
 
 
+def replica_rhs_seed(rank: int) -> int:
+    """Seed of rank `rank`'s right-hand side: every replica solves its own system."""
+    return RHS_SEED + rank
+
+
+def max_over_ranks(ms: float, ws: int, device="cuda") -> float:
+    """The slowest rank's time (all ranks' work is done only when it is)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, ws: int, ms_max: float) -> float:
+    """Units all ranks processed divided by the max-over-ranks time (per second)."""
+    return units_per_rank * ws / (ms_max / 1e3)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -163,7 +184,7 @@ def run_tmnd(args):
     _build.build()
 
     U = synth.random_su3_field(DIMS, ROUGHNESS, GAUGE_SEED)
-    b_host = synth.gaussian_rhs(DIMS, RHS_SEED + rank)[0]
+    b_host = synth.gaussian_rhs(DIMS, replica_rhs_seed(rank))[0]
     sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
     g = tm.Gauge(U, DIMS, KAPPA, MU_BAR, EPS_BAR)
     stream = torch.cuda.current_stream()
@@ -193,13 +214,9 @@ def run_tmnd(args):
         dist.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    ms_all = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
+    ms_all = max_over_ranks(ms, ws)
     solves = args.steps * NSHIFT * ws
-    value = solves / (ms_all / 1e3)
+    value = whole_job_rate(args.steps * NSHIFT, ws, ms_all)
     worst_res = max(max(i["true_res"]) for i in infos)
     iters = infos[-1]["iters"]
 
@@ -223,12 +240,8 @@ def run_tmnd(args):
             x_pin[i].copy_(x_can[0], non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = solves / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1), ws)
+    e2e_value = whole_job_rate(args.steps * NSHIFT, ws, e2e_ms)
     h2d = b_host.nbytes
     d2h = NSHIFT * b_host.nbytes
 
