@@ -195,10 +195,11 @@ def run_tmnd(args):
     def step(profile=False):
         return tm.mms_cg_solve(g.handle, b_dev, 1, sig, xs, rho=RHO, profile=profile, stream=stream)
 
+    # nvidia-smi starts before the warm-up, so that its start-up does not overlap the timed region
+    sampler = ClockSampler(local)
     for _ in range(args.warmup):
         info = step()
     # ---- timed region: K solves, L2 flushed between solves
-    sampler = ClockSampler(local)
     infos = []
     if ws > 1:
         dist.barrier()
@@ -441,9 +442,9 @@ def run_form(args):
         return tm.tmnd_hybrid_solve(g.handle, None, b_dev, nrhs, sig, 8, xs, rho=RHO, prec=tm.TMND_S16,
                                     n_guess=0, guess=2, net=net, stream=stream)
 
+    sampler = ClockSampler(local)
     for _ in range(args.warmup):
         step()
-    sampler = ClockSampler(local)
     ms, infos = _timed(step, args.steps, flush, stream)
     clocks = sampler.stop()
     solves = args.steps * len(sig) * nrhs
@@ -477,10 +478,16 @@ def run_form(args):
             tm.tmnd_spinor_unpack(g.handle, x_can, v, nrhs, stream)
             x_pin[i].copy_(x_can, non_blocking=True)
     e2e_ms, _ = _timed(step_e2e, args.steps, flush, stream)
-    # the plain FP64 multi-shift CG on the same workload (one step)
+    # the plain FP64 multi-shift CG on the same workload (one step), and each form's solutions
+    # against its solutions: max over shifts of |x_form - x_FP64| / |x_FP64| (all RHS together)
+    keep = [v.clone() for v in xs[:len(sig)]] if args.form != "rational" else None
     f64 = lambda: tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs[:len(sig)], rho=RHO, stream=stream)
     f64()
     f64_ms, _ = _timed(f64, 1, flush, stream)
+    if keep is not None:
+        dx = [float(torch.linalg.vector_norm(k - v) / torch.linalg.vector_norm(v)) for k, v in zip(keep, xs)]
+        extra["rel_diff_vs_fp64"] = {"max": max(dx), "per_shift": [float("%.3g" % d) for d in dx]}
+        del keep
     roof = s16_roofline(tm, g, flush, stream)
     if mg is not None:   # the coarse operator on the tensor cores, all 8 RHS at once
         nb = g.vh * 2 // 256
@@ -797,10 +804,26 @@ def cpu_baseline(iters_full: int, sample_iters: int = 6):
     oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=sample_iters)
     el = time.perf_counter() - t
     per_iter = el / sample_iters
-    return {"value": NSHIFT / (per_iter * iters_full), "unit": "solves/s", "cores": oracle.nthreads(),
-            "kind": "oracle",
-            "sample": f"{sample_iters} MMS-CG iterations of the full 16^3x32 12-shift solve "
-                      f"({el:.1f} s), scaled to the oracle's full solve of {iters_full} iterations"}
+    out = {"value": NSHIFT / (per_iter * iters_full), "unit": "solves/s", "cores": oracle.nthreads(),
+           "kind": "oracle",
+           "sample": f"{sample_iters} MMS-CG iterations of the full 16^3x32 12-shift solve "
+                     f"({el:.1f} s), scaled to the oracle's full solve of {iters_full} iterations"}
+    # the same on one thread (OpenMP fixes its thread count at start-up: a child process)
+    code = ("import sys, time; sys.path.insert(0, %r); import oracle, synth; "
+            "U = synth.random_su3_field(%r, %r, %r); b = synth.gaussian_rhs(%r, %r)[0]; "
+            "sig = synth.shift_set(%r, %r, %r); act = oracle.action(%r, %r, %r, %r); "
+            "t = time.perf_counter(); oracle.mms_cg(act, U, b, sig, rho=%r, maxiter=2); "
+            "print(time.perf_counter() - t)") % (ROOT, DIMS, ROUGHNESS, GAUGE_SEED, DIMS, RHS_SEED, NSHIFT, SIG_LO,
+                                                 SIG_HI, DIMS, KAPPA, MU_BAR, EPS_BAR, RHO)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
+                           capture_output=True, text=True, timeout=300)
+        el1 = float(r.stdout.strip().splitlines()[-1])
+        out["single_thread"] = {"value": NSHIFT / (el1 / 2 * iters_full), "unit": "solves/s", "cores": 1,
+                                "sample": f"2 MMS-CG iterations on one thread ({el1:.1f} s), scaled likewise"}
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        out["single_thread"] = {"value": None, "error": str(e)[:200]}
+    return out
 
 
 def oracle_full_iters():
@@ -847,7 +870,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tmnd", choices=["tmnd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -582,16 +582,16 @@ tmnd_status run_graph_loop(cudaStream_t s, const int *done_dev, int maxiter, int
             return TMND_ERR_CUDA;
         }
     }
-    int *flags = nullptr;  // pinned [2]
-    cudaEvent_t fev[2];
-    cudaError_t err = cudaHostAlloc((void **)&flags, 2 * sizeof(int), cudaHostAllocDefault);
+    int *flags = nullptr;  // pinned [L + 1]
+    const int L = profile ? 1 : 2;  // replays queued ahead of the flag being read
+    cudaEvent_t fev[3];
+    cudaError_t err = cudaHostAlloc((void **)&flags, (L + 1) * sizeof(int), cudaHostAllocDefault);
     if (err != cudaSuccess) {
         cleanup();
         tmnd_set_error("mms_cg_solve: cudaHostAlloc: %s", cudaGetErrorString(err));
         return TMND_ERR_CUDA;
     }
-    cudaEventCreateWithFlags(&fev[0], cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&fev[1], cudaEventDisableTiming);
+    for (int i = 0; i <= L; i++) cudaEventCreateWithFlags(&fev[i], cudaEventDisableTiming);
     auto harvest = [&](long j) {  // read the events of replay j (complete)
         int inst = (int)(j % ninst);
         for (int k = 0; k < check_every; k++) {
@@ -605,23 +605,22 @@ tmnd_status run_graph_loop(cudaStream_t s, const int *done_dev, int maxiter, int
             out.upd_t.push_back(b2);
         }
     };
-    const long max_launch = (long)maxiter / check_every + 3;
+    const long max_launch = (long)maxiter / check_every + 2 + L;
     for (long j = 0; j < max_launch && err == cudaSuccess; j++) {
         err = cudaGraphLaunch(exec[j % ninst], s);
         if (err != cudaSuccess) break;
         out.nlaunch++;
-        cudaMemcpyAsync(&flags[j & 1], done_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
-        cudaEventRecord(fev[j & 1], s);
-        if (j > 0) {
-            err = cudaEventSynchronize(fev[(j - 1) & 1]);
-            if (err == cudaSuccess && profile) harvest(j - 1);
-            if (err == cudaSuccess && flags[(j - 1) & 1]) break;
+        cudaMemcpyAsync(&flags[j % (L + 1)], done_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(fev[j % (L + 1)], s);
+        if (j >= L) {
+            err = cudaEventSynchronize(fev[(j - L) % (L + 1)]);
+            if (err == cudaSuccess && profile) harvest(j - L);
+            if (err == cudaSuccess && flags[(j - L) % (L + 1)]) break;
         }
     }
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err == cudaSuccess && profile && out.nlaunch > 0) harvest(out.nlaunch - 1);
-    cudaEventDestroy(fev[0]);
-    cudaEventDestroy(fev[1]);
+    for (int i = 0; i <= L; i++) cudaEventDestroy(fev[i]);
     cudaFreeHost(flags);
     cleanup();
     if (err != cudaSuccess) {
