@@ -91,3 +91,15 @@ def test_methods_agree_in_the_exact_limit(problem):
     sols = oracle.equivalent_solutions(act, U, b, mu, 1e-13)
     for case in "ABC":
         assert np.linalg.norm(sols[case] - x) <= 1e-8 * np.linalg.norm(x), case
+
+
+def test_library_limits_equal_oracle_limits():
+    """The GPU package restates App. A's limits (relative to |b|) for its study; both
+    restatements agree for a range of spectra and shifts."""
+    from paper_1805_09584_gb300 import equivalent
+    for lmin, lmax, mu, rho in [(1e-3, 2.4, 0.3, 1e-6), (0.011, 2.39, 3.2e-3, 1e-10), (0.0, 5.0, 1e-2, 1e-4)]:
+        mine = equivalent.app_a_limits(rho, lmin, lmax, mu)
+        ref = oracle.equivalent_bounds(rho, 1.0, lmin, lmax, mu)
+        assert set(mine) == set(ref)
+        for k in ref:
+            assert np.allclose(mine[k], ref[k], rtol=1e-14, atol=0), k
