@@ -1,7 +1,7 @@
-"""The N > 1 path of bench.py (replicas: one right-hand side per rank, no data
-exchange) on CPU with two gloo ranks: every rank gets its own right-hand side,
-the timed region is the slowest rank's, and the whole-job rate counts all ranks'
-solves."""
+"""Host logic of bench.py on CPU.  The N > 1 path (replicas: one right-hand side
+per rank, no data exchange) with two gloo ranks: every rank gets its own
+right-hand side, the timed region is the slowest rank's, and the whole-job rate
+counts all ranks' solves.  The reference arm's JSON line (the oracle on the host)."""
 import os
 import socket
 
@@ -57,3 +57,17 @@ def test_single_rank_helpers():
     import bench
     assert bench.max_over_ranks(12.5, 1) == 12.5
     assert bench.whole_job_rate(24, 1, 500.0) == 48.0
+
+
+def test_reference_arm_line(oracle_lib):
+    """bench.py --impl reference times the oracle on the host and prints the contract's keys
+    (one step of two multi-shift CG iterations of the 16^3x32 workload)."""
+    import argparse
+    import bench
+    line = bench.run_reference(argparse.Namespace(steps=1, warmup=0))
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
