@@ -236,6 +236,28 @@ tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, const double *s
 tmnd_status lagrange_guess(const tmnd_gauge *g, const double *nodes, const void *const *xs, int k,
                            double target, void *out, int nrhs, double *lebesgue_out, void *stream);
 
+/* Lagrange weights l_j(target), j < k, over k distinct finite nodes (Sec. 4.2.1), and the
+ * Lebesgue function gamma_k(target) = sum_j |l_j| (App. B; gamma may be NULL).  Host
+ * function, FP64.  w: k doubles.  1 <= k <= 8. */
+tmnd_status tmnd_lagrange_weights(const double *nodes, int k, double target, double *w, double *gamma);
+
+/* Degree truncation of the Lagrange guess (App. B: where the Lebesgue function grows,
+ * lower the degree of the interpolation to keep the residual bound rho gamma_k small).
+ * Host function.  `nodes` lists k candidate shifts in order of preference (nearest to the
+ * target first); *k_used receives the largest k' <= k such that the first k' nodes give
+ * gamma_k'(target) <= gamma_max (k' >= 1: gamma_1 = 1), *gamma (may be NULL) that
+ * gamma_k'(target).  1 <= k <= 8, distinct finite nodes, gamma_max >= 1, else TMND_ERR_ARG. */
+tmnd_status tmnd_lagrange_degree(const double *nodes, int k, double target, double gamma_max, int *k_used,
+                                 double *gamma);
+
+/* Quadratic form of a guess residual (App. B): for solutions x_j of the shifts nodes[j]
+ * with Gram matrix G (host, 2 k k doubles, row-major, re/im interleaved: G_jq = <x_j, x_q>),
+ * H (host, k k doubles) = Re((target - s_j) G_jq (target - s_q)) / bb.  With exact x_j and
+ * weights summing to 1, w^T H w = |b - (Qhat^2 + target) sum_j w_j x_j|^2 / bb, bb = |b|^2.
+ * Host function.  1 <= k <= 8, bb > 0. */
+tmnd_status tmnd_guess_quadratic_form(const double *G, const double *nodes, int k, double target, double bb,
+                                      double *H);
+
 /* ---------------------------------------------------------------- multigrid
  * Aggregation-based two-level multigrid (Sec. 3, DD-alphaAMG; Sec. 3.2 for the
  * doublet), FP32.  Layouts:
@@ -330,6 +352,9 @@ typedef struct {
     int mg_maxiter, mg_restart, mg_nu;   /* 0 = 100, 24, 4 (GCR(8) stagnates on the indefinite
                                             full-lattice operator at small shifts) */
     const struct tmnd_mlp *net;          /* guess = 2: a trained network (see tmnd_mlp_*), else NULL */
+    double lebesgue_max;                 /* guess = 1: the nearest solved shifts (at most 8) are truncated to
+                                            the longest nearest-first run whose Lebesgue function at the
+                                            target is <= lebesgue_max (App. B; tmnd_lagrange_degree); 0 = 4 */
 } tmnd_hybrid_params;
 
 typedef struct {
@@ -342,6 +367,8 @@ typedef struct {
     double shift_ms[TMND_MAX_SHIFTS];      /* wall time of each non-MMS shift's guess, MG and
                                               defect correction (RHS 0); the MMS part's in mms_ms */
     double mms_ms;                         /* wall time of the multi-shift part (all RHS) */
+    int lag_nodes[TMND_MAX_SHIFTS];        /* guess = 1: interpolation nodes used for each shift */
+    double lebesgue[TMND_MAX_SHIFTS];      /* guess = 1: gamma of those nodes at the shift */
 } tmnd_hybrid_info;
 
 /* Hybrid solve of (Qhat^2 + sigma_i) x_i = b (Sec. 4.3): multi-shift CG for

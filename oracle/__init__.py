@@ -190,6 +190,20 @@ def lebesgue(nodes, target) -> float:
     return float(np.sum(np.abs(lagrange_weights(nodes, target))))
 
 
+def lagrange_degree(nodes_nearest_first, target, gamma_max) -> tuple:
+    """Degree truncation of App. B ("in case of diverging growths one can truncate the
+    degree of the interpolation"): the largest k' such that the first k' nodes of the
+    nearest-first list give gamma_k'(target) <= gamma_max, with gamma_1 = 1.  Returns
+    (k', gamma_k'(target))."""
+    nodes = [float(v) for v in nodes_nearest_first]
+    best, gbest = 1, 1.0
+    for k in range(2, len(nodes) + 1):
+        g = lebesgue(nodes[:k], target)
+        if g <= gamma_max:
+            best, gbest = k, g
+    return best, gbest
+
+
 def lagrange_guess(nodes, xs, target) -> np.ndarray:
     """x~(m) = sum_i l_{i,k}(m) x_i (Sec. 4.2.1, Eq. for p(m))."""
     w = lagrange_weights(nodes, target)
@@ -302,6 +316,39 @@ def dnd_odd_shift(act: Action, links, psi_full, s) -> np.ndarray:
     g5 = np.array([1.0, 1.0, -1.0, -1.0])
     term = 1j * s * g5[None, None, :, None] * psi[:, ::-1]   # tau_1 swaps the flavours
     out[odd] += term[odd]
+    return out
+
+
+def mg_coarse_nd_odd_shift(act: Action, links, P, nv: int, s, chunk: int = 256) -> np.ndarray:
+    """Coarse operator of the case-C systems (Sec. 3.1 Eq. "lindif", Sec. 3.2):
+    P_ND^+ D' P_ND with D' = D_ND + i s (gamma_5 (x) tau_1) Pi_odd (dnd_odd_shift)
+    and P_ND = P (x) 1_2, formed by applying D' to every column of P_ND and
+    projecting with P^+ (no block-structure shortcut).  Coarse ND layout as in
+    mg_coarse_nd: index (block, flavour, chirality, k) -> b 4 Nv + f 2 Nv + chi Nv + k."""
+    P = np.asarray(P, np.complex128)
+    V = int(np.prod(act.dims))
+    ncol = P.shape[1]
+    nblock = ncol // (2 * nv)
+    Ph = P.conj().T
+    out = np.zeros((2 * ncol, 2 * ncol), np.complex128)
+
+    def rows(f):
+        b = np.repeat(np.arange(nblock), 2 * nv)
+        r = np.tile(np.arange(2 * nv), nblock)
+        return b * 4 * nv + f * 2 * nv + r
+    for j0 in range(0, 2 * ncol, chunk):
+        js = range(j0, min(j0 + chunk, 2 * ncol))
+        Y = np.empty((2, V * 12, len(js)), np.complex128)
+        for q, j in enumerate(js):
+            b, rem = divmod(j, 4 * nv)
+            f, r = divmod(rem, 2 * nv)
+            fine = np.zeros((V, 2, 4, 3), np.complex128)
+            fine[:, f] = P[:, b * 2 * nv + r].reshape(V, 4, 3)
+            y = dnd_odd_shift(act, links, fine, s)
+            Y[0, :, q] = y[:, 0].ravel()
+            Y[1, :, q] = y[:, 1].ravel()
+        for f in range(2):
+            out[rows(f), j0:j0 + len(js)] = Ph @ Y[f]
     return out
 
 

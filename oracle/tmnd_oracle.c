@@ -444,6 +444,7 @@ int or_mms_cg(const or_action *a, const double *links, const double *b_, int nsh
     cplx *ps = malloc(sizeof(cplx) * n * nshift);
     double *zeta = malloc(sizeof(double) * nshift), *zeta_old = malloc(sizeof(double) * nshift);
     int *active = malloc(sizeof(int) * nshift);
+    double *zeta_new = malloc(sizeof(double) * nshift), *alpha_s = malloc(sizeof(double) * nshift);
     double sigma0 = sigma[nsolve - 1];
     for (long i = 0; i < n; i++) { r[i] = b[i]; p[i] = b[i]; }
     for (int s = 0; s < nshift; s++) {
@@ -458,7 +459,6 @@ int or_mms_cg(const or_action *a, const double *links, const double *b_, int nsh
     while (k < maxiter && active[nsolve - 1]) {
         or_qhat2(a, links, (double *)p, (double *)w, sigma0);
         double alpha = rr / re_dot(n, p, w);
-        double zeta_new[64], alpha_s[64];
         for (int s = 0; s < nshift; s++) {
             if (!active[s]) continue;
             double d = sigma[s] - sigma0;
@@ -490,5 +490,6 @@ int or_mms_cg(const or_action *a, const double *links, const double *b_, int nsh
     for (int s = 0; s < nshift; s++) zeta_out[s] = zeta[s];
     int ok = !active[nsolve - 1];
     free(r); free(p); free(w); free(ps); free(zeta); free(zeta_old); free(active);
+    free(zeta_new); free(alpha_s);
     return ok ? k : -k;
 }

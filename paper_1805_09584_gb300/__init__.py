@@ -35,7 +35,8 @@ EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd
            "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve", "tmnd_mlp_num_params", "tmnd_mlp_create",
            "tmnd_mlp_destroy", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad", "tmnd_mlp_train_step", "tmnd_mlp_predict",
            "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_zolotarev", "tmnd_rational_apply",
-           "tmnd_hybrid_cost", "tmnd_fit_cg_time", "tmnd_fit_mg_time", "tmnd_lincomb_c", "tmnd_site_norm_range")
+           "tmnd_hybrid_cost", "tmnd_fit_cg_time", "tmnd_fit_mg_time", "tmnd_lincomb_c", "tmnd_site_norm_range",
+           "tmnd_lagrange_weights", "tmnd_lagrange_degree", "tmnd_guess_quadratic_form")
 NOALLOC_MAX_VH = 32768
 
 
@@ -59,14 +60,15 @@ class HybridParams(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("maxiter", ctypes.c_int), ("prec", ctypes.c_int),
                 ("rho_inner", ctypes.c_double), ("n_guess", ctypes.c_int), ("guess", ctypes.c_int),
                 ("mg_tol", ctypes.c_double), ("mg_maxiter", ctypes.c_int), ("mg_restart", ctypes.c_int),
-                ("mg_nu", ctypes.c_int), ("net", ctypes.c_void_p)]
+                ("mg_nu", ctypes.c_int), ("net", ctypes.c_void_p), ("lebesgue_max", ctypes.c_double)]
 
 
 class HybridInfo(ctypes.Structure):
     _fields_ = [("mms_iters", ctypes.c_int), ("guess_res", ctypes.c_double * MAX_SHIFTS),
                 ("mg_iters", ctypes.c_int * MAX_SHIFTS), ("true_res", ctypes.c_double * MAX_SHIFTS),
                 ("fp64_applies", ctypes.c_int), ("refine_iters", ctypes.c_int),
-                ("shift_ms", ctypes.c_double * MAX_SHIFTS), ("mms_ms", ctypes.c_double)]
+                ("shift_ms", ctypes.c_double * MAX_SHIFTS), ("mms_ms", ctypes.c_double),
+                ("lag_nodes", ctypes.c_int * MAX_SHIFTS), ("lebesgue", ctypes.c_double * MAX_SHIFTS)]
 
 
 class SolveParams(ctypes.Structure):
@@ -151,11 +153,15 @@ def lib() -> ctypes.CDLL:
         L.tmnd_fit_mg_time.argtypes = [pd, pd, i, d, i, pd, pd, pd]
         L.tmnd_rational_apply.argtypes = [vp, vp, i, i, d, d, ctypes.POINTER(SolveParams), vp, pd,
                                           ctypes.POINTER(SolveInfo), vp]
+        L.tmnd_lagrange_weights.argtypes = [pd, i, d, pd, pd]
+        L.tmnd_lagrange_degree.argtypes = [pd, i, d, d, ctypes.POINTER(i), pd]
+        L.tmnd_guess_quadratic_form.argtypes = [pd, pd, i, d, d, pd]
         for name in ("tmnd_mlp_create", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad",
                      "tmnd_mlp_train_step", "tmnd_zolotarev", "tmnd_rational_apply", "tmnd_hybrid_cost",
                      "tmnd_fit_cg_time", "tmnd_fit_mg_time",
                      "tmnd_mlp_predict", "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_lincomb_c",
-                     "tmnd_site_norm_range"):
+                     "tmnd_site_norm_range", "tmnd_lagrange_weights", "tmnd_lagrange_degree",
+                     "tmnd_guess_quadratic_form"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
                      "tmnd_dnd_full_apply", "tmnd_mg_solve", "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve"):
@@ -330,23 +336,59 @@ def tmnd_mg_smooth_vectors(h, vecs, nvec: int, iters: int, stream=None) -> None:
 def tmnd_hybrid_solve(h, mg, b, nrhs: int, sigma, n_mms: int, x, rho: float = 1e-10, maxiter: int = 100000,
                       prec: int = TMND_F64, rho_inner: float = 0.0, n_guess: int = 2, guess: int = 1,
                       mg_tol: float = 0.0, mg_maxiter: int = 0, mg_restart: int = 0, mg_nu: int = 0,
-                      net=None, stream=None) -> dict:
+                      net=None, lebesgue_max: float = 0.0, stream=None) -> dict:
     """mg may be None (no multigrid: guesses go straight to the FP64 defect correction);
     guess = 2 with a trained network `net` (tmnd_mlp_create) uses learned weights."""
     sig = np.ascontiguousarray(sigma, dtype=np.float64)
     ns = len(sig)
     xs = (ctypes.c_void_p * ns)(*[_ptr(v) for v in x])
     p = HybridParams(float(rho), int(maxiter), int(prec), float(rho_inner), int(n_guess), int(guess), float(mg_tol),
-                     int(mg_maxiter), int(mg_restart), int(mg_nu), net)
+                     int(mg_maxiter), int(mg_restart), int(mg_nu), net, float(lebesgue_max))
     info = HybridInfo()
     st = lib().tmnd_hybrid_solve(h, mg, _ptr(b), int(nrhs), sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns,
                                  int(n_mms), xs, ctypes.byref(p), ctypes.byref(info), _stream(stream))
     out = {"status": st, "mms_iters": info.mms_iters, "guess_res": list(info.guess_res[:ns]),
            "mg_iters": list(info.mg_iters[:ns]), "true_res": list(info.true_res[:ns]),
            "fp64_applies": info.fp64_applies, "refine_iters": info.refine_iters,
-           "shift_ms": list(info.shift_ms[:ns]), "mms_ms": info.mms_ms}
+           "shift_ms": list(info.shift_ms[:ns]), "mms_ms": info.mms_ms,
+           "lag_nodes": list(info.lag_nodes[:ns]), "lebesgue": list(info.lebesgue[:ns])}
     _check(st)
     return out
+
+
+def _pd(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def tmnd_lagrange_weights(nodes, target: float):
+    """(w, gamma): Lagrange weights over `nodes` at `target` and their Lebesgue function."""
+    nd = np.ascontiguousarray(nodes, np.float64)
+    w = np.zeros(len(nd))
+    gam = ctypes.c_double()
+    _check(lib().tmnd_lagrange_weights(_pd(nd), len(nd), float(target), _pd(w), ctypes.byref(gam)))
+    return w, gam.value
+
+
+def tmnd_lagrange_degree(nodes, target: float, gamma_max: float):
+    """(k_used, gamma): the longest prefix of `nodes` (nearest first) with gamma <= gamma_max."""
+    nd = np.ascontiguousarray(nodes, np.float64)
+    ku = ctypes.c_int()
+    gam = ctypes.c_double()
+    _check(lib().tmnd_lagrange_degree(_pd(nd), len(nd), float(target), float(gamma_max), ctypes.byref(ku),
+                                      ctypes.byref(gam)))
+    return ku.value, gam.value
+
+
+def tmnd_guess_quadratic_form(G, nodes, target: float, bb: float) -> np.ndarray:
+    """H [k, k] = Re((t - s_j) G_jq (t - s_q)) / bb for a complex Gram matrix G [k, k]."""
+    nd = np.ascontiguousarray(nodes, np.float64)
+    k = len(nd)
+    Gi = np.empty(2 * k * k)
+    Gc = np.asarray(G, np.complex128).ravel()
+    Gi[0::2], Gi[1::2] = Gc.real, Gc.imag
+    H = np.zeros(k * k)
+    _check(lib().tmnd_guess_quadratic_form(_pd(Gi), _pd(nd), k, float(target), float(bb), _pd(H)))
+    return H.reshape(k, k)
 
 
 def tmnd_mlp_num_params(F: int) -> int:

@@ -205,3 +205,75 @@ extern "C" tmnd_status tmnd_site_norm_range(const tmnd_gauge *g, const void *x, 
     min_max[1] = sqrt(hi);
     return TMND_OK;
 }
+
+// ------------------------------------------------ host helpers of the guesses
+// l_j(target) over nodes[0..k), Sec. 4.2.1; returns gamma_k(target) = sum |l_j| (App. B)
+static double lagrange_w(const double *nodes, int k, double target, double *w) {
+    double leb = 0.0;
+    for (int j = 0; j < k; j++) {
+        double l = 1.0;
+        for (int i = 0; i < k; i++)
+            if (i != j) l *= (target - nodes[i]) / (nodes[j] - nodes[i]);
+        if (w) w[j] = l;
+        leb += fabs(l);
+    }
+    return leb;
+}
+
+static tmnd_status check_nodes(const char *fn, const double *nodes, int k, double target) {
+    TMND_ARG_CHECK(nodes, "%s: NULL nodes", fn);
+    TMND_ARG_CHECK(k >= 1 && k <= MAXK, "%s: k = %d not in [1, %d]", fn, k, MAXK);
+    TMND_ARG_CHECK(isfinite(target), "%s: target must be finite", fn);
+    for (int j = 0; j < k; j++) {
+        TMND_ARG_CHECK(isfinite(nodes[j]), "%s: nodes[%d] not finite", fn, j);
+        for (int i = 0; i < j; i++) TMND_ARG_CHECK(nodes[i] != nodes[j], "%s: nodes %d and %d coincide", fn, i, j);
+    }
+    return TMND_OK;
+}
+
+extern "C" tmnd_status tmnd_lagrange_weights(const double *nodes, int k, double target, double *w, double *gamma) {
+    const tmnd_status st = check_nodes("tmnd_lagrange_weights", nodes, k, target);
+    if (st != TMND_OK) return st;
+    TMND_ARG_CHECK(w, "tmnd_lagrange_weights: NULL w");
+    const double leb = lagrange_w(nodes, k, target, w);
+    if (gamma) *gamma = leb;
+    return TMND_OK;
+}
+
+// App. B: when the Lebesgue function grows, truncate the degree of the interpolation.
+// The nodes come in order of preference (nearest first); keep the longest prefix
+// whose Lebesgue function at the target stays within gamma_max.
+extern "C" tmnd_status tmnd_lagrange_degree(const double *nodes, int k, double target, double gamma_max,
+                                            int *k_used, double *gamma) {
+    const tmnd_status st = check_nodes("tmnd_lagrange_degree", nodes, k, target);
+    if (st != TMND_OK) return st;
+    TMND_ARG_CHECK(k_used, "tmnd_lagrange_degree: NULL k_used");
+    TMND_ARG_CHECK(gamma_max >= 1.0, "tmnd_lagrange_degree: gamma_max = %g < 1", gamma_max);
+    int best = 1;
+    double gbest = 1.0;  // gamma_1 = |l_1| = 1
+    for (int kk = 2; kk <= k; kk++) {
+        const double gk = lagrange_w(nodes, kk, target, nullptr);
+        if (gk <= gamma_max) {
+            best = kk;
+            gbest = gk;
+        }
+    }
+    *k_used = best;
+    if (gamma) *gamma = gbest;
+    return TMND_OK;
+}
+
+// H_jk = Re((t - s_j) G_jk (t - s_k)) / bb: with exact solutions x_j of the shifts s_j and
+// weights summing to 1, w^T H w is the squared relative residual of sum_j w_j x_j at the
+// target shift t (App. B: the residual is - sum_j w_j (t - s_j) x_j); G interleaved re/im.
+extern "C" tmnd_status tmnd_guess_quadratic_form(const double *G, const double *nodes, int k, double target,
+                                                 double bb, double *H) {
+    const tmnd_status st = check_nodes("tmnd_guess_quadratic_form", nodes, k, target);
+    if (st != TMND_OK) return st;
+    TMND_ARG_CHECK(G && H, "tmnd_guess_quadratic_form: NULL argument");
+    TMND_ARG_CHECK(bb > 0 && isfinite(bb), "tmnd_guess_quadratic_form: bb = %g", bb);
+    for (int j = 0; j < k; j++)
+        for (int q = 0; q < k; q++)
+            H[j * k + q] = (target - nodes[j]) * G[2 * (j * k + q)] * (target - nodes[q]) / bb;
+    return TMND_OK;
+}

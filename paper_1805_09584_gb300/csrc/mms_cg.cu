@@ -1265,6 +1265,8 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
                                          tmnd_hybrid_info *hinfo, void *stream) {
     TMND_ARG_CHECK(g && b && sigma && x && hp, "tmnd_hybrid_solve: NULL argument");
     TMND_ARG_CHECK(hp->guess >= 0 && hp->guess <= 2, "tmnd_hybrid_solve: guess = %d not in {0, 1, 2}", hp->guess);
+    TMND_ARG_CHECK(hp->lebesgue_max == 0.0 || hp->lebesgue_max >= 1.0, "tmnd_hybrid_solve: lebesgue_max = %g < 1",
+                   hp->lebesgue_max);
     TMND_ARG_CHECK(hp->guess != 2 || (hp->net && n_mms >= 8),
                    "tmnd_hybrid_solve: learned guesses need a network and n_mms >= 8");
     TMND_ARG_CHECK(nshift >= 1 && nshift <= TMND_MAX_SHIFTS && n_mms >= 1 && n_mms <= nshift && nrhs >= 1,
@@ -1401,11 +1403,24 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
                     st = tmnd_lincomb(g, &lw[(size_t)8 * (i - nmms_all)], xs, 8, xk[i], 1, s);
                     if (st != TMND_OK) { res_status = st; break; }
                 } else if (hp->guess == 1) {
+                    // the nearest solved shifts first, truncated where the Lebesgue function grows (App. B)
                     const int kk = i < 8 ? i : 8;
+                    double cand[8];
                     const void *xs[8];
-                    for (int j = 0; j < kk; j++) xs[j] = xk[i - kk + j];
-                    st = lagrange_guess(g, sigma + (i - kk), xs, kk, sigma[i], xk[i], 1, nullptr, s);
+                    for (int j = 0; j < kk; j++) {
+                        cand[j] = sigma[i - 1 - j];
+                        xs[j] = xk[i - 1 - j];
+                    }
+                    int ku = kk;
+                    double gam = 1.0;
+                    st = tmnd_lagrange_degree(cand, kk, sigma[i], hp->lebesgue_max > 0 ? hp->lebesgue_max : 4.0, &ku,
+                                              &gam);
+                    if (st == TMND_OK) st = lagrange_guess(g, cand, xs, ku, sigma[i], xk[i], 1, nullptr, s);
                     if (st != TMND_OK) { res_status = st; break; }
+                    if (hinfo && k == 0) {
+                        hinfo->lag_nodes[i] = ku;
+                        hinfo->lebesgue[i] = gam;
+                    }
                 } else {
                     cudaMemsetAsync(xk[i], 0, sizeof(double2) * n, s);
                 }

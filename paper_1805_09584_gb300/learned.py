@@ -50,23 +50,16 @@ def samples(g, b_dev, sigma, xs, info, hist):
     feats, Ss, Hs = [], [], []
     for q, t in enumerate(sigma[NODES:]):
         nodes = sigma[q:q + NODES]
-        G = tm.tmnd_gram(g.handle, xs[q:q + NODES]) / bb
+        G = tm.tmnd_gram(g.handle, xs[q:q + NODES])
         feats.append(tm.tmnd_mlp_features(nodes, float(t), hist, info["iters"], float(sigma[NODES - 1])))
         Ss.append(np.concatenate([[float(t)], nodes]))
-        d = float(t) - nodes
-        Hs.append(np.real(d[:, None] * G * d[None, :]))
+        Hs.append(tm.tmnd_guess_quadratic_form(G, nodes, float(t), bb))
     return np.stack(feats), np.stack(Ss), np.stack(Hs)
 
 
 def lagrange_weights(nodes, target):
-    """Host formula of Sec. 4.2.1 (the same one lagrange_guess applies)."""
-    nodes = np.asarray(nodes, np.float64)
-    w = np.ones(len(nodes))
-    for i in range(len(nodes)):
-        for j in range(len(nodes)):
-            if j != i:
-                w[i] *= (target - nodes[j]) / (nodes[i] - nodes[j])
-    return w
+    """Lagrange weights of Sec. 4.2.1 (the library's host function, as lagrange_guess applies them)."""
+    return tm.tmnd_lagrange_weights(nodes, target)[0]
 
 
 def _dev(a, dtype):

@@ -4,6 +4,10 @@ launch configurations, on what the oracle can compute there:
     (shift, RHS) pairs <= 1e-10 (factor 1.01 for summation order);
   * the 16-bit Qhat^2 + sigma at 24^3x48: the oracle's FP64 Qhat^2 of the same field,
     norm-wise 2e-4 (7 roundings of 16-bit data, as in test_gpu_sloppy);
+  * the hybrid solve at 32^3x64 with 8 RHS in the bench's configuration (4^4 aggregates,
+    24 test vectors per chirality, multi-shift CG for the 8 largest shifts, Lagrange guesses
+    and case-C multigrid for the 4 smallest): the oracle's true residual of sampled pairs,
+    two of them on the multigrid branch;
   * the tensor-core coarse operator at 32^3x64 (48x48 blocks, 8 RHS): the FP32
     CUDA-core path, which the oracle pins at small sizes, max-norm 4e-3 (TF32)."""
 import numpy as np
@@ -53,6 +57,29 @@ def test_batched_32_certified_by_oracle():
     for i, k in ((11, 0), (0, 7), (8, 3)):
         x = g.unpack(xs[i], 8)[k].cpu().numpy()
         assert oracle.true_residual(act, U, b[k], x, SIG[i]) <= 1.01e-10, (i, k)
+    g.close()
+
+
+def test_hybrid_32_certified_by_oracle():
+    tm = require_gpu()
+    dims, nv = (64, 32, 32, 32), 24
+    U = synth.random_su3_field(dims, 0.5, 1004)
+    b = synth.gaussian_rhs(dims, 2004, nrhs=8)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    tv = torch.randn(nv * 2 * 12 * g.vh, dtype=torch.complex64, device="cuda", generator=gen)
+    tm.tmnd_mg_smooth_vectors(g.handle, tv, nv, 4)
+    mg = tm.tmnd_mg_create(g.handle, (4, 4, 4, 4), nv, tv)
+    del tv
+    bi = g.pack(torch.from_numpy(b).cuda(), nrhs=8)
+    xs = [g.spinor(8) for _ in SIG]
+    info = tm.tmnd_hybrid_solve(g.handle, mg, bi, 8, SIG, 8, xs, prec=tm.TMND_S16, n_guess=0, guess=1)
+    assert all(it > 0 for it in info["mg_iters"][8:]), info     # the multigrid branch ran
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    for i, k in ((11, 0), (9, 5), (3, 7), (0, 2)):
+        x = g.unpack(xs[i], 8)[k].cpu().numpy()
+        assert oracle.true_residual(act, U, b[k], x, SIG[i]) <= 1.01e-10, (i, k)
+    tm.tmnd_mg_destroy(mg)
     g.close()
 
 

@@ -13,8 +13,8 @@ from test_gpu_mg import to_mg_layout
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [0, 2])
-def test_hybrid_certified(prec):
+@pytest.mark.parametrize("prec,lebesgue_max", [(0, 0.0), (2, 0.0), (2, 1.5)])
+def test_hybrid_certified(prec, lebesgue_max):
     tm = require_gpu()
     dims, bdims, nv = (8, 4, 4, 4), (2, 2, 2, 2), 6
     V = int(np.prod(dims))
@@ -30,7 +30,15 @@ def test_hybrid_certified(prec):
     sig = synth.shift_set(10, 1e-4, 1.0)
     bi = g.pack(torch.from_numpy(b).cuda())
     xs = [g.spinor() for _ in sig]
-    info = tm.tmnd_hybrid_solve(g.handle, mg, bi, 1, sig, 6, xs, prec=prec)
+    info = tm.tmnd_hybrid_solve(g.handle, mg, bi, 1, sig, 6, xs, prec=prec, lebesgue_max=lebesgue_max)
+    # Lagrange nodes of shifts 8, 9 (after 6 multi-shift and 2 guess shifts): the nearest solved
+    # shifts, truncated where the Lebesgue function exceeds lebesgue_max (App. B), as the oracle picks
+    for i in (8, 9):
+        cand = sig[:i][::-1][:8]
+        k_ref, g_ref = oracle.lagrange_degree(cand, sig[i], lebesgue_max or 4.0)
+        assert info["lag_nodes"][i] == k_ref and abs(info["lebesgue"][i] - g_ref) < 1e-12 * g_ref, info
+    if lebesgue_max == 1.5:
+        assert info["lag_nodes"][8] < 8
     for i, s in enumerate(sig):
         x = g.unpack(xs[i])[0].cpu().numpy()
         tr = oracle.true_residual(act, U, b[0], x, s)

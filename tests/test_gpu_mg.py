@@ -147,23 +147,6 @@ def test_restrict_prolong_match_oracle(mgsetup):
             assert np.max(np.abs(back[r, :, f * 12:(f + 1) * 12].ravel() - ref)) < 2e-5 * np.abs(ref).max()
 
 
-def _coarse_nd_dense(s, s_odd, nv, P, Dcw, nb):
-    n2 = 2 * nv
-    Dnd = oracle.mg_coarse_nd(Dcw, nb, nv, 2 * KAPPA * MU, 2 * KAPPA * EPS)
-    if s_odd:
-        V = int(np.prod(s["dims"]))
-        odd = np.zeros(V, bool)
-        odd[synth.odd_sites(s["dims"])] = True
-        g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), V) * np.repeat(odd, 12)
-        G = P.conj().T @ (g5[:, None] * P)
-        for b in range(nb):
-            i0 = b * 2 * n2
-            blk = G[b * n2:(b + 1) * n2, b * n2:(b + 1) * n2]
-            Dnd[i0:i0 + n2, i0 + n2:i0 + 2 * n2] += 1j * s_odd * blk
-            Dnd[i0 + n2:i0 + 2 * n2, i0:i0 + n2] += 1j * s_odd * blk
-    return Dnd
-
-
 @pytest.mark.parametrize("s_odd", [0.0, 0.03])
 @pytest.mark.parametrize("path,R,tol", [("simt", 3, 2e-5), ("tc", 1, 4e-3), ("tc", 3, 4e-3), ("tc", 8, 4e-3),
                                         ("tc", 16, 4e-3)])
@@ -171,7 +154,8 @@ def test_coarse_apply_matches_oracle(mgsetup, s_odd, path, R, tol):
     s = mgsetup
     tm, nb = s["tm"], s["nb"]
     mg = s["mg_simt"] if path == "simt" else s["mg"]
-    Dnd = _coarse_nd_dense(s, s_odd, NV, s["P"], s["Dcw"], nb)
+    # the oracle's P_ND^+ (D_ND + i s gamma_5 tau_1 Pi_odd) P_ND, by column probing
+    Dnd = oracle.mg_coarse_nd_odd_shift(s["act"], s["U"], s["P"], NV, s_odd)
     rng = np.random.default_rng(5)
     xv = rng.standard_normal((R, nb * 4 * NV)) + 1j * rng.standard_normal((R, nb * 4 * NV))
     xin = torch.from_numpy(xv.astype(np.complex64).ravel()).cuda()
@@ -202,9 +186,8 @@ def test_coarse_apply_tc_production_shape(s_odd):
     mgs = tm.tmnd_mg_create(g.handle, bdims, nv, tv, coarse_simt=True)
     act = oracle.action(dims, KAPPA, MU, EPS)
     P = oracle.mg_prolongator(dims, bdims, vecs.astype(np.complex128).reshape(nv, V, 4, 3))
-    Dcw = oracle.mg_coarse_wilson(act, U, P)
     nb = P.shape[1] // (2 * nv)
-    Dnd = _coarse_nd_dense(dict(dims=dims), s_odd, nv, P, Dcw, nb)
+    Dnd = oracle.mg_coarse_nd_odd_shift(act, U, P, nv, s_odd)
     R = 8
     xv = rng.standard_normal((R, nb * 4 * nv)) + 1j * rng.standard_normal((R, nb * 4 * nv))
     xin = torch.from_numpy(xv.astype(np.complex64).ravel()).cuda()

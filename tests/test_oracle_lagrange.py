@@ -76,3 +76,72 @@ def test_residual_interpolation_identity_and_bound(oracle_lib):
     assert np.linalg.norm(r_true) <= term + rho * oracle.lebesgue(sig[:6], tgt) * nb * 1.0001
     # the guess beats the zero start vector (relative residual < 1)
     assert np.linalg.norm(r_true) < nb
+
+
+def test_lebesgue_closed_form_and_degree_truncation():
+    """Equispaced nodes 1..k and the target 0 (extrapolation one step beyond the nearest
+    node): |l_j(0)| = C(k, j), so gamma_k(0) = 2^k - 1 grows exponentially, the case App. B
+    answers by truncating the degree.  The truncation keeps the longest nearest-first run
+    with gamma <= gamma_max: k' = floor(log2(gamma_max + 1))."""
+    from math import comb
+    nodes = np.arange(1.0, 9.0)       # nearest first
+    for k in range(1, 9):
+        w = oracle.lagrange_weights(nodes[:k], 0.0)
+        assert np.allclose(np.abs(w), [comb(k, j) for j in range(1, k + 1)], rtol=1e-13)
+        assert abs(oracle.lebesgue(nodes[:k], 0.0) - (2 ** k - 1)) < 1e-11 * 2 ** k
+    for gmax, kk in ((1.0, 1), (3.0, 2), (4.0, 2), (7.0, 3), (100.0, 6), (1e6, 8)):
+        k_used, g = oracle.lagrange_degree(nodes, 0.0, gmax)
+        assert k_used == kk, (gmax, k_used)
+        assert abs(g - (2 ** kk - 1)) < 1e-11 * 2 ** kk
+
+
+def test_degree_truncation_keeps_the_configured_shift_sets():
+    """On the log-spaced shift sets of the workloads, solved in descending order, the
+    Lebesgue function at the next shift stays below 4 (reading of the paper's
+    gamma_n(m_{n+1}) <= 2 remark: 2.11 and 2.30 here), so the default gamma_max = 4
+    keeps every node."""
+    for sig in (synth.shift_set(12, 1e-5, 2.0), synth.shift_set(10, 1e-4, 1.0)):
+        for i in range(1, len(sig)):
+            cand = sig[max(0, i - 8):i][::-1]          # nearest first
+            k_used, g = oracle.lagrange_degree(cand, sig[i], 4.0)
+            assert k_used == len(cand) and g < 2.31
+
+
+def test_library_guess_helpers_match_oracle():
+    """The library's host helpers (tmnd_lagrange_weights / _degree, tmnd_guess_quadratic_form)
+    against the oracle's Lagrange weights, truncation and the residual quadratic form."""
+    from paper_1805_09584_gb300 import _build
+    _build.build()
+    import paper_1805_09584_gb300 as tm
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        k = int(rng.integers(1, 9))
+        nodes = np.sort(rng.uniform(0.01, 3.0, k))[::-1]
+        t = float(rng.uniform(-0.5, 3.5))
+        w, g = tm.tmnd_lagrange_weights(nodes, t)
+        wr = oracle.lagrange_weights(nodes, t)
+        assert np.allclose(w, wr, rtol=1e-13, atol=1e-13 * np.abs(wr).max())
+        assert abs(g - oracle.lebesgue(nodes, t)) < 1e-12 * g
+        for gmax in (1.0, 2.0, 4.0, 50.0):
+            assert tm.tmnd_lagrange_degree(nodes, t, gmax)[0] == oracle.lagrange_degree(nodes, t, gmax)[0]
+    # quadratic form: exact solutions of a diagonal "operator" A = diag(a) + sigma, so that
+    # w^T H w must equal the squared relative residual of sum_j w_j x_j at the target
+    a = rng.uniform(0.1, 2.0, 40)
+    b = rng.standard_normal(40) + 1j * rng.standard_normal(40)
+    nodes = synth.shift_set(8, 1e-3, 1.0)
+    t = 3e-4
+    xs = [b / (a + s) for s in nodes]
+    G = np.array([[np.vdot(xj, xq) for xq in xs] for xj in xs])
+    H = tm.tmnd_guess_quadratic_form(G, nodes, t, float(np.vdot(b, b).real))
+    Hr = oracle.guess_quadratic_form(nodes, t, xs, float(np.vdot(b, b).real))
+    assert np.allclose(H, Hr, rtol=1e-12, atol=1e-15)
+    w = oracle.lagrange_weights(nodes, t)
+    res = b - (a + t) * sum(wj * xj for wj, xj in zip(w, xs))
+    # w^T H w cancels terms of size (sum_j |w_j (t - s_j)| |x_j| / |b|)^2 down to the residual:
+    # FP64 rounding is relative to that scale
+    scale = (sum(abs(wj * (t - s)) * np.linalg.norm(xj) for wj, s, xj in zip(w, nodes, xs))) ** 2 / np.vdot(b, b).real
+    assert abs(w @ H @ w - np.vdot(res, res).real / np.vdot(b, b).real) < 1e-13 * scale
+    with pytest.raises(tm.TmndError):
+        tm.tmnd_lagrange_degree([0.5, 0.5], 0.1, 4.0)      # coinciding nodes
+    with pytest.raises(tm.TmndError):
+        tm.tmnd_lagrange_degree([0.5, 0.4], 0.1, 0.5)      # gamma_max < 1
