@@ -159,7 +159,10 @@ tmnd_status tm_nd_apply(tmnd_gauge *g, void *out, const void *in, int op, double
  *   - The current device must be the handle's device.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *     before any stream capture begins.  The address is kept for the life of
+ *     the process: after cudaDeviceReset (or any other teardown of the
+ *     device's primary context) it is stale, so do not call this entry point
+ *     again in a process that has reset the device.
  *   - Every call on a device (any handle, stream or host thread) uses the same
  *     array.  Calls whose executions overlap on the GPU race on it and give
  *     wrong results: order them (one stream, or events between streams).
@@ -279,6 +282,13 @@ typedef struct {
     int coarse_simt;           /* 0: mg_coarse_apply on the tensor cores (tcgen05, TF32 operands,
                                   FP32 accumulation) whenever 2 nvec % 4 == 0 and nrhs <= 16,
                                   else FP32 CUDA cores; 1: always FP32 CUDA cores */
+    double wait_limit_s;       /* every wait inside the tensor-core kernel gives up after this many
+                                  seconds (0 = 2 s; at most 60); the kernel then ends with the
+                                  handle's timeout flag set (see tmnd_mg_status) */
+    int stall_test;            /* testing hook, 0 normally: the next stall_test tensor-core applies
+                                  make their MMA warps wait on a barrier that nothing completes, so
+                                  that the wait runs out after wait_limit_s and the error path
+                                  (drain of copies and MMAs in flight, flag, clean exit) runs */
 } tmnd_mg_params;
 
 /* Build the hierarchy from `nvec` caller-provided test vectors (device, FP32
@@ -307,11 +317,16 @@ tmnd_status tmnd_mg_prolong(const tmnd_mg *mg, void *out_fine, const void *in_c,
  * Tensor cores (see tmnd_mg_params.coarse_simt): nrhs <= 16, 2 nvec % 4 == 0; the
  * dense blocks and the vectors enter the products as TF32 (relative error ~1e-3),
  * sums in FP32; a wait that gives up in the kernel is reported as TMND_ERR_TIMEOUT
- * by the next tmnd_mg_solve / tmnd_hybrid_solve.  The handle holds the operand
+ * by the next tmnd_mg_status / tmnd_mg_solve / tmnd_hybrid_solve.  The handle holds the operand
  * tiles of one application: one mg_coarse_apply at a time per handle.  CUDA cores:
  * nrhs * 4 nvec <= 1024, FP32 throughout. */
 tmnd_status mg_coarse_apply(const tmnd_mg *mg, void *out_c, const void *in_c, int nrhs, double odd_shift_s,
                             void *stream);
+
+/* Waits for the device, then reports whether a tensor-core coarse apply on this handle gave
+ * up a bounded wait since the last check: TMND_ERR_TIMEOUT (and the flag is cleared), else
+ * TMND_OK.  The handle stays usable either way.  Synchronous. */
+tmnd_status tmnd_mg_status(const tmnd_mg *mg);
 
 /* out = D' in on the full lattice (fine doublet MG vectors, FP32), with
  *   D' = D_ND + i s (gamma_5 (x) tau_1) Pi_odd

@@ -36,7 +36,7 @@ EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd
            "tmnd_mlp_destroy", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad", "tmnd_mlp_train_step", "tmnd_mlp_predict",
            "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_zolotarev", "tmnd_rational_apply",
            "tmnd_hybrid_cost", "tmnd_fit_cg_time", "tmnd_fit_mg_time", "tmnd_lincomb_c", "tmnd_site_norm_range",
-           "tmnd_lagrange_weights", "tmnd_lagrange_degree", "tmnd_guess_quadratic_form")
+           "tmnd_lagrange_weights", "tmnd_lagrange_degree", "tmnd_guess_quadratic_form", "tmnd_mg_status")
 NOALLOC_MAX_VH = 32768
 
 
@@ -53,7 +53,7 @@ class Action(ctypes.Structure):
 
 class MGParams(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int * 4), ("nvec", ctypes.c_int), ("coarse_mu_factor", ctypes.c_double),
-                ("coarse_simt", ctypes.c_int)]
+                ("coarse_simt", ctypes.c_int), ("wait_limit_s", ctypes.c_double), ("stall_test", ctypes.c_int)]
 
 
 class HybridParams(ctypes.Structure):
@@ -125,6 +125,7 @@ def lib() -> ctypes.CDLL:
         L.tmnd_mg_prolong.argtypes = [vp, vp, vp, i, vp]
         L.mg_coarse_apply.argtypes = [vp, vp, vp, i, d, vp]
         L.tmnd_mg_export.argtypes = [vp, vp, vp, vp]
+        L.tmnd_mg_status.argtypes = [vp]
         L.tmnd_dnd_full_apply.argtypes = [vp, vp, vp, d, vp]
         L.tmnd_mg_solve.argtypes = [vp, vp, vp, d, d, i, i, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]
         L.tmnd_mg_smooth_vectors.argtypes = [vp, vp, i, i, vp]
@@ -164,6 +165,7 @@ def lib() -> ctypes.CDLL:
                      "tmnd_guess_quadratic_form"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
+                     "tmnd_mg_status",
                      "tmnd_dnd_full_apply", "tmnd_mg_solve", "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_gauge_create", "tmnd_spinor_pack", "tmnd_spinor_unpack", "tm_nd_apply",
@@ -282,11 +284,13 @@ def lagrange_guess(h, nodes, xs, target: float, out, nrhs: int = 1, stream=None)
     return leb.value
 
 
-def tmnd_mg_create(h, block, nvec: int, test_vectors, coarse_mu_factor: float = 1.0, coarse_simt: bool = False):
+def tmnd_mg_create(h, block, nvec: int, test_vectors, coarse_mu_factor: float = 1.0, coarse_simt: bool = False,
+                   wait_limit_s: float = 0.0, stall_test: int = 0):
     p = MGParams()
     for k in range(4):
         p.block[k] = int(block[k])
     p.nvec, p.coarse_mu_factor, p.coarse_simt = int(nvec), float(coarse_mu_factor), int(bool(coarse_simt))
+    p.wait_limit_s, p.stall_test = float(wait_limit_s), int(stall_test)
     out = ctypes.c_void_p()
     _check(lib().tmnd_mg_create(h, ctypes.byref(p), _ptr(test_vectors), ctypes.byref(out)))
     return out
@@ -310,6 +314,11 @@ def tmnd_mg_prolong(mg, out_fine, in_c, nrhs: int = 1, stream=None) -> None:
 
 def mg_coarse_apply(mg, out_c, in_c, nrhs: int = 1, odd_shift_s: float = 0.0, stream=None) -> None:
     _check(lib().mg_coarse_apply(mg, _ptr(out_c), _ptr(in_c), int(nrhs), float(odd_shift_s), _stream(stream)))
+
+
+def tmnd_mg_status(mg) -> None:
+    """Raise TmndError(TMND_ERR_TIMEOUT) if a tensor-core apply gave up a wait since the last check."""
+    _check(lib().tmnd_mg_status(mg))
 
 
 def tmnd_mg_export(mg, P_host=None, Dc_host=None, Godd_host=None) -> None:

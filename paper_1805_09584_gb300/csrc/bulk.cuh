@@ -32,16 +32,18 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 
 // Wait for the phase of the given parity to complete.  Returns false if the wait
-// gave up: after ~2 s, after 2^24 polls, or when *stop becomes non-zero.
+// gave up: after limit_ns (default ~2 s), after 2^24 polls, or when *stop becomes
+// non-zero.
 constexpr uint64_t MBAR_WAIT_NS = 2000000000ull;
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, const volatile int *stop = nullptr) {
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, const volatile int *stop = nullptr,
+                                          uint64_t limit_ns = MBAR_WAIT_NS) {
     if (mbar_try(a, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (int i = 1; i < (1 << 24); i++) {
         if (mbar_try(a, parity)) return true;
         if ((i & 255) == 0) {
             if (stop && *stop) return false;
-            if (globaltimer_ns() - t0 > MBAR_WAIT_NS) return false;
+            if (globaltimer_ns() - t0 > limit_ns) return false;
         }
     }
     return false;

@@ -35,6 +35,8 @@ struct tmnd_mg {
     size_t work_bytes;
     int tc;             // coarse apply on the tensor cores where the shape allows
     int *tc_err;        // device flag: a tensor-core kernel gave up waiting
+    uint64_t wait_ns;   // limit of the tensor-core kernel's bounded waits
+    mutable int stall_next;  // test hook: tensor-core launches still to run with the stall barrier
     void *Dt, *Gt;      // D_W,c and G_odd again, in the tensor-core operand-tile layout
     void *Bt;           // B operand tiles of one application (up to 16 right-hand sides)
 };
@@ -45,7 +47,7 @@ size_t coarse_tc_btile_bytes(int nblock, int nv, int nrhs);
 tmnd_status coarse_tc_make_atiles(const float2 *src, void *dst, long nmat, int nv, cudaStream_t s);
 tmnd_status launch_coarse_apply_tc(const void *Dt, const void *Gt, void *btiles, const float2 *x, float2 *y,
                                    int nblock, const int nbd[4], int nv, int nrhs, float mu_c, float eps_c,
-                                   float s_odd, int *err, cudaStream_t s);
+                                   float s_odd, int *err, uint64_t wait_ns, int stall, cudaStream_t s);
 
 namespace {
 
@@ -381,6 +383,8 @@ extern "C" tmnd_status tmnd_mg_create(tmnd_gauge *g, const tmnd_mg_params *p, co
     TMND_ARG_CHECK(g && p && test_vectors && out, "tmnd_mg_create: NULL argument");
     *out = nullptr;
     TMND_ARG_CHECK(p->nvec >= 1 && p->nvec <= MG_MAXV, "tmnd_mg_create: nvec = %d not in [1, %d]", p->nvec, MG_MAXV);
+    TMND_ARG_CHECK(p->wait_limit_s >= 0 && p->wait_limit_s <= 60 && p->stall_test >= 0,
+                   "tmnd_mg_create: wait_limit_s = %g not in [0, 60] or stall_test < 0", p->wait_limit_s);
     for (int i = 0; i < 4; i++)
         TMND_ARG_CHECK(p->block[i] >= 1 && g->act.dims[i] % p->block[i] == 0,
                        "tmnd_mg_create: block[%d] = %d does not divide dims[%d] = %d", i, p->block[i], i,
@@ -396,9 +400,10 @@ extern "C" tmnd_status tmnd_mg_create(tmnd_gauge *g, const tmnd_mg_params *p, co
         mg->nsb *= mg->bd[i];
         mg->nblock *= mg->nbd[i];
     }
-    TMND_ARG_CHECK(mg->nsb * 6 >= 2 * p->nvec || true, "");
     mg->nv = p->nvec;
     mg->tc = p->coarse_simt ? 0 : 1;
+    mg->wait_ns = p->wait_limit_s > 0 ? (uint64_t)(p->wait_limit_s * 1e9) : 2000000000ull;
+    mg->stall_next = p->stall_test;
     const double d = p->coarse_mu_factor > 0 ? p->coarse_mu_factor : 1.0;
     mg->mu_c = 2 * g->act.kappa * g->act.mu_bar * d;
     mg->eps_c = 2 * g->act.kappa * g->act.eps_bar;
@@ -546,10 +551,13 @@ extern "C" tmnd_status mg_coarse_apply(const tmnd_mg *mg, void *out_c, const voi
     TMND_ARG_CHECK(((uintptr_t)out_c & 15) == 0 && ((uintptr_t)in_c & 15) == 0,
                    "mg_coarse_apply: vectors must be 16-byte aligned");
     cudaGetLastError();
-    if (mg->tc && mg->Dt && coarse_tc_smem(n2, nrhs) > 0)
+    if (mg->tc && mg->Dt && coarse_tc_smem(n2, nrhs) > 0) {
+        const int stall = mg->stall_next > 0;
+        if (stall) mg->stall_next--;
         return launch_coarse_apply_tc(mg->Dt, mg->Gt, mg->Bt, (const float2 *)in_c, (float2 *)out_c, mg->nblock,
                                       mg->nbd, mg->nv, nrhs, (float)mg->mu_c, (float)mg->eps_c, (float)odd_shift_s,
-                                      mg->tc_err, (cudaStream_t)stream);
+                                      mg->tc_err, mg->wait_ns, stall, (cudaStream_t)stream);
+    }
     TMND_ARG_CHECK(n2 * 2 * nrhs <= 1024, "mg_coarse_apply: nrhs = %d too large for 2*nvec = %d", nrhs, n2);
     MGGeom m = mg_geom(mg);
     const size_t smem = sizeof(float2) * 9 * n2 * 2 * nrhs;
@@ -565,6 +573,7 @@ extern "C" tmnd_status mg_coarse_apply(const tmnd_mg *mg, void *out_c, const voi
 
 // reads and clears the tensor-core timeout flag (synchronous)
 tmnd_status tmnd_mg_tc_status(const tmnd_mg *mg) {
+    TMND_ARG_CHECK(mg, "tmnd_mg_status: NULL handle");
     int h = 0;
     TMND_CUDA_TRY(cudaMemcpy(&h, mg->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h) {
@@ -589,6 +598,8 @@ extern "C" tmnd_status tmnd_mg_export(const tmnd_mg *mg, void *P_host, void *Dc_
                                  cudaMemcpyDeviceToHost));
     return TMND_OK;
 }
+
+extern "C" tmnd_status tmnd_mg_status(const tmnd_mg *mg) { return tmnd_mg_tc_status(mg); }
 
 // accessors for the solver translation unit
 size_t tmnd_mg_nblock_nv(const tmnd_mg *mg, int *nv) {

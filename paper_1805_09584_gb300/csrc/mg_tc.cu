@@ -27,8 +27,11 @@
 //                  such accumulator pairs alternate between sites;
 //   warps 0, 1     epilogue: read rows 0..63 from tensor memory, add the mu_c /
 //                  eps_c terms and i s G_odd x with the flavours swapped, store y.
-// Every wait gives up after ~2 s (or once another warp has given up), sets *err,
-// waits (bounded) for the bulk copies still in flight and ends the kernel.  TF32
+// Every wait gives up after a limit (~2 s by default, or once another warp has given
+// up), sets *err, waits (bounded) for the bulk copies and the MMAs still in flight
+// and ends the kernel.  For tests of that path, `stall` makes the MMA issuer of
+// every block wait, after its first MMAs, on a barrier that nothing completes, so
+// that the wait runs out and the error path runs (no fault, no hang).  TF32
 // keeps 10 mantissa bits of each operand (relative error ~1e-3 per product),
 // ample for the coarse correction of the preconditioner.
 #include <stdint.h>
@@ -77,6 +80,8 @@ struct TCArgs {
     float2 *y;
     float mu_c, eps_c, s_odd;
     int *err;
+    uint64_t wait_ns;  // limit of every bounded wait
+    int stall;         // test hook: the MMA issuer waits on a barrier nothing completes
 };
 
 // shared-memory matrix descriptor, no swizzle, K-major: lbo = byte step between core
@@ -173,7 +178,8 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MAX_CTAS) k_coarse_apply_tc(TCA
     const int S = a.stages;
     uint64_t *bar = (uint64_t *)(sm + S * stage + TC_SLACK);
     uint64_t *full = bar, *empty = bar + TC_MAX_STAGES, *accf = bar + 2 * TC_MAX_STAGES, *acce = accf + 2;
-    uint32_t *tholder = (uint32_t *)(acce + 2);
+    uint64_t *drain = acce + 2, *never = drain + 1;  // MMA drain on the error path; the stall hook's barrier
+    uint32_t *tholder = (uint32_t *)(never + 1);
     volatile int *sflag = (volatile int *)(tholder + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint32_t ncols = 32;
@@ -188,6 +194,8 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MAX_CTAS) k_coarse_apply_tc(TCA
             mbar_init(smem_u32(&accf[j]), 1);
             mbar_init(smem_u32(&acce[j]), 64);
         }
+        mbar_init(smem_u32(drain), 1);
+        mbar_init(smem_u32(never), 1);
         *sflag = 0;
         mbar_init_fence();
     }
@@ -208,7 +216,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MAX_CTAS) k_coarse_apply_tc(TCA
         int issued = 0;
         for (int q = 0; q < nsite * nsteps; q++) {
             const int b = blockIdx.x + (q / nsteps) * gridDim.x, t = q % nsteps, s = q % S, k = q / S;
-            bool ok = k < 1 || mbar_wait(smem_u32(&empty[s]), (uint32_t)((k - 1) & 1), sflag);
+            bool ok = k < 1 || mbar_wait(smem_u32(&empty[s]), (uint32_t)((k - 1) & 1), sflag, a.wait_ns);
             if (__any_sync(0xffffffffu, !ok || *sflag)) { *sflag = 1; break; }
             issued = q + 1;
             if (lane == 0) {
@@ -230,13 +238,17 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MAX_CTAS) k_coarse_apply_tc(TCA
         bool stop = false;
         for (int i = 0, q = 0; i < nsite && !stop; i++) {
             const int buf = i & 1, u = i >> 1;
-            bool ok = u < 1 || mbar_wait(smem_u32(&acce[buf]), (uint32_t)((u - 1) & 1), sflag);
+            bool ok = u < 1 || mbar_wait(smem_u32(&acce[buf]), (uint32_t)((u - 1) & 1), sflag, a.wait_ns);
             if (__any_sync(0xffffffffu, !ok || *sflag)) { *sflag = 1; break; }
             tc_fence_after();
             const uint32_t dmain = taddr + (uint32_t)(buf * 2 * N), dg = dmain + (uint32_t)N;
             for (int t = 0; t < nsteps; t++, q++) {
                 const int s = q % S, k = q / S;
-                ok = mbar_wait(smem_u32(&full[s]), (uint32_t)(k & 1), sflag);
+                if (a.stall && q == 1) {  // test hook: a wait that runs out (MMAs of step 0 are in flight)
+                    ok = mbar_wait(smem_u32(never), 0u, sflag, a.wait_ns);
+                    if (__any_sync(0xffffffffu, !ok || *sflag)) { *sflag = 1; stop = true; break; }
+                }
+                ok = mbar_wait(smem_u32(&full[s]), (uint32_t)(k & 1), sflag, a.wait_ns);
                 if (__any_sync(0xffffffffu, !ok || *sflag)) { *sflag = 1; stop = true; break; }
                 tc_fence_after();
                 if (lane == 0) {
@@ -253,12 +265,19 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MAX_CTAS) k_coarse_apply_tc(TCA
             if (lane == 0) mma_commit(smem_u32(&accf[buf]));
             __syncwarp();
         }
+        // after an error, wait (bounded) until every MMA this thread issued has completed, so that
+        // none still reads shared memory or writes tensor memory when the block frees them
+        if (*sflag && lane == 0) {
+            mma_commit(smem_u32(drain));
+            mbar_wait(smem_u32(drain), 0u);
+        }
+        __syncwarp();
     } else {  // warps 0, 1: epilogue, rows 0..63 (tensor-memory lanes 32 w + lane)
         const int row = warp * 32 + lane;
         float acc[64], gz[64];
         for (int i = 0; i < nsite; i++) {
             const int b = blockIdx.x + i * gridDim.x, buf = i & 1, u = i >> 1;
-            const bool ok = mbar_wait(smem_u32(&accf[buf]), (uint32_t)(u & 1), sflag);
+            const bool ok = mbar_wait(smem_u32(&accf[buf]), (uint32_t)(u & 1), sflag, a.wait_ns);
             if (__any_sync(0xffffffffu, !ok || *sflag)) { *sflag = 1; break; }
             tc_fence_after();
             const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 2 * N);
@@ -333,7 +352,7 @@ size_t coarse_tc_btile_bytes(int nblock, int nv, int nrhs) {
 
 tmnd_status launch_coarse_apply_tc(const void *Dt, const void *Gt, void *btiles, const float2 *x, float2 *y,
                                    int nblock, const int nbd[4], int nv, int nrhs, float mu_c, float eps_c,
-                                   float s_odd, int *err, cudaStream_t s) {
+                                   float s_odd, int *err, uint64_t wait_ns, int stall, cudaStream_t s) {
     const size_t smem = coarse_tc_smem(2 * nv, nrhs);
     TMND_ARG_CHECK(smem > 0, "mg_coarse_apply: tensor-core path needs 2 nvec % 4 == 0, <= 64 and nrhs <= 16");
     TCArgs a;
@@ -344,6 +363,8 @@ tmnd_status launch_coarse_apply_tc(const void *Dt, const void *Gt, void *btiles,
     a.Bt = (const unsigned char *)btiles;
     a.x = x; a.y = y;
     a.mu_c = mu_c; a.eps_c = eps_c; a.s_odd = s_odd; a.err = err;
+    a.wait_ns = wait_ns;
+    a.stall = stall;
     k_coarse_btiles<<<nblock, 256, 0, s>>>(a.g, x, (unsigned char *)btiles);
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);

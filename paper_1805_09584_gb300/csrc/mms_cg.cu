@@ -638,7 +638,8 @@ tmnd_status run_graph_loop(cudaStream_t s, const int *done_dev, int maxiter, int
 // or b at the start).
 static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *x, const double *sigma, int nshift,
                                int nsolve, double rho, int maxiter, int check_every, int profile,
-                               tmnd_solve_info *info, cudaStream_t s, int rhs_index, double *hist, int hist_cap) {
+                               tmnd_solve_info *info, cudaStream_t s, int rhs_index, double *hist, int hist_cap,
+                               bool certify = true) {
     const size_t sp = tmnd_spinor_bytes(g);
     const long n = (long)(sp / sizeof(double2));
     char *w = (char *)g->work;
@@ -715,10 +716,19 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
 
     MMSState hs;
     TMND_CUDA_TRY(cudaMemcpy(&hs, st, sizeof hs, cudaMemcpyDeviceToHost));
+    if (!certify) {  // a correction solve: its caller certifies the corrected solution
+        if (info) info->iters = hs.iter;
+        if (hs.status == TMND_ERR_NAN) {
+            tmnd_set_error("mms_cg_solve: NaN/Inf in a reduction of a defect correction at iteration %d", hs.iter);
+            return TMND_ERR_NAN;
+        }
+        return TMND_OK;
+    }
 
-    // true residuals |b - (Qhat^2 + sigma_i) x_i| / |b| with the operator
-    double *hpart = new double[nb_str];
-    for (int i = 0; i < nshift; i++) {
+    // true residual |b - (Qhat^2 + sigma_i) x_i| / |b| with the operator; leaves the defect
+    // b - (Qhat^2 + sigma_i) x_i in r
+    std::vector<double> hpart(nb_str);
+    auto true_res_of = [&](int i, double *tr) -> tmnd_status {
         HopEpiArgs ea = {};
         launch_hop_even_f64(g->geom, g->st, g->links, ptrs.x[i], te, false, nullptr, s);
         launch_hop_odd_f64(g->geom, g->st, g->links, ptrs.x[i], te, r, false, EPI_STORE, ea, s);
@@ -727,20 +737,57 @@ static tmnd_status mms_one_rhs(tmnd_gauge *g, const double2 *b, double2 *const *
         e2.aux = ptrs.x[i];
         launch_hop_even_f64(g->geom, g->st, g->links, r, te, true, nullptr, s);
         launch_hop_odd_f64(g->geom, g->st, g->links, r, te, y, true, EPI_SHIFT, e2, s);
-        k_diff_norm<<<nb_str, UPD_THREADS, 0, s>>>(n, b, y, part_str);
-        cudaError_t e3 = cudaMemcpyAsync(hpart, part_str, sizeof(double) * nb_str, cudaMemcpyDeviceToHost, s);
+        k_resid<<<nb_str, UPD_THREADS, 0, s>>>(n, b, y, r, part_str);
+        cudaError_t e3 = cudaMemcpyAsync(hpart.data(), part_str, sizeof(double) * nb_str, cudaMemcpyDeviceToHost, s);
         if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(s);
         if (e3 != cudaSuccess) {
-            delete[] hpart;
             tmnd_set_error("mms_cg_solve: %s", cudaGetErrorString(e3));
             return TMND_ERR_CUDA;
         }
         double acc = 0;
         for (int k = 0; k < nb_str; k++) acc += hpart[k];
-        double tr = hs.bb > 0 ? sqrt(acc / hs.bb) : 0.0;
-        if (info && (rhs_index == 0 || tr > info->true_res[i])) info->true_res[i] = tr;
+        *tr = hs.bb > 0 ? sqrt(acc / hs.bb) : 0.0;
+        return TMND_OK;
+    };
+    // A required shift whose true residual drifted above rho (the recursively updated residual
+    // drifts from the true one by rounding) is finished by FP64 defect correction (Sec. 3.1
+    // stopping rule on the true residual): (Qhat^2 + sigma_i) e = d by a single-shift FP64 CG to
+    // |d - (Qhat^2 + sigma_i) e| <= rho |b| / 2, x_i += e, the true residual again.
+    double2 *corr = nullptr;  // d, e: two spinors, allocated the first time a shift needs them
+    tmnd_status cst = TMND_OK;
+    for (int i = 0; i < nshift && cst == TMND_OK; i++) {
+        double tr = 0;
+        cst = true_res_of(i, &tr);
+        const bool nan = !isfinite(tr);
+        for (int round = 0; cst == TMND_OK && !nan && i < nsolve && hs.status == TMND_OK && tr > rho && round < 4;
+             round++) {
+            if (!corr && cudaMalloc(&corr, 2 * sizeof(double2) * n) != cudaSuccess) {
+                corr = nullptr;
+                tmnd_set_error("mms_cg_solve: no device memory for the defect correction");
+                cst = TMND_ERR_OOM;
+                break;
+            }
+            double2 *d = corr, *e = corr + n;
+            TMND_CUDA_TRY(cudaMemcpyAsync(d, r, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
+            const double rel = fmin(0.5, 0.5 * rho / tr);  // relative to |d| = tr |b|
+            tmnd_solve_info sub = {};
+            double2 *ev[1] = {e};
+            cst = mms_one_rhs(g, d, ev, sigma + i, 1, 1, rel, maxiter, check_every, 0, &sub, s, 0, nullptr, 0,
+                              false);
+            if (cst != TMND_OK) break;
+            k_zaxpy64<<<nb_str, UPD_THREADS, 0, s>>>(n, 1.0, 0.0, e, ptrs.x[i]);
+            cst = true_res_of(i, &tr);
+            if (info) {
+                info->refine_iters += sub.iters;
+                info->fp64_applies += 1;
+                info->launches += sub.launches + 6;
+                if (round + 1 > info->refine_rounds) info->refine_rounds = round + 1;
+            }
+        }
+        if (info && (rhs_index == 0 || tr > info->true_res[i] || nan)) info->true_res[i] = tr;
     }
-    delete[] hpart;
+    if (corr) cudaFree(corr);
+    if (cst != TMND_OK) return cst;
     if (info && profile) {
         // only the iterations that did work (later ones returned at once)
         for (int k = 0; k < hs.iter && k < (int)hop_t.size(); k++) {
