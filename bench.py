@@ -1,25 +1,30 @@
-"""Benchmark: shift-system solves/s at relative residual 1e-10 on one GB300.
+"""Benchmark: shift-system solves/s at relative residual 1e-10 on one GB300, and the
+16-bit Dslash's GB/s against the measured HBM peak.
 
-Workload (N = 1): the 16^3x32 FP64 multi-shift solve of the ND twisted-mass
-doublet (kappa 0.16, mu_bar 0.1, eps_bar 0.11, antiperiodic time, seeded
-SU(3) links with roughness 0.5), 12 shifts log-spaced in 1e-5..2, one
-Gaussian right-hand side, rho = 1e-10.  A step is one complete multi-shift CG
-solve (all shifts, with the FP64 true-residual certification).
+Workload (N = 1, the default): the 32^3x64 hybrid solve of the ND twisted-mass
+doublet (kappa 0.16, mu_bar 0.1, eps_bar 0.11, antiperiodic time, seeded SU(3)
+links with roughness 0.5), 12 shifts log-spaced in 1e-5..2, 8 Gaussian
+right-hand sides, rho = 1e-10: mixed-precision multi-shift CG (FP32 arithmetic on
+16-bit stencil data, all 8 right-hand sides in every stencil launch) for the 8
+largest shifts, Lagrange guesses and case-C two-level multigrid (4^4 aggregates,
+24 test vectors per chirality, coarse operator on the tensor cores) for the 4
+smallest, every (shift, right-hand side) pair finished by FP64 defect correction
+and certified by its FP64 true residual.  A step is one complete solve of the 96
+systems (the multigrid setup is built once per gauge field, outside the timed
+region).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tmnd|reference]
-                    [--form fp64|mixed|batched|hybrid|learned]
+                    [--form hybrid|fp64|mixed|batched|learned|rational]
 
---form selects one of the solver forms on its own workload (the default, fp64,
-is the headline above); every form certifies each shift at 1e-10 by its FP64
-true residual:
+--form selects a solver form on its own workload (every form certifies each shift
+at 1e-10 by its FP64 true residual):
+  hybrid   the headline above
+  fp64     16^3x32, 12 shifts, 1 RHS: plain FP64 multi-shift CG (its oracle baseline is
+           the oracle's full solve of the same system, timed)
   mixed    24^3x48, 12 shifts, 2 RHS one at a time: sloppy FP32/16-bit multi-shift
            CG + FP64 defect correction
   batched  32^3x64, 12 shifts, 8 RHS: the same with all 8 RHS in every 16-bit
-           stencil launch
-  hybrid   32^3x64, 12 shifts, 8 RHS: mixed multi-shift CG for the 8 largest,
-           Lagrange guesses and case-C two-level MG (4^4 aggregates, 24 vectors
-           per chirality, coarse operator on the tensor cores) for the 4 smallest
-           (the MG setup is built once per gauge field, outside the timed region)
+           stencil launch, no multigrid
   learned  24^3x48, 12 shifts, 1 RHS on an unseen field: mixed multi-shift CG for
            the 8 largest, learned guesses for the 4 smallest finished by defect
            correction; the network is trained first on solves of other fields
@@ -28,7 +33,7 @@ true residual:
            approximation on the spectrum bounds from a Lanczos estimate (mixed
            multi-shift CG over the 10 Zolotarev shifts + one combination)
 Each form's line also times the plain FP64 multi-shift CG on its workload
-("fp64_same_workload") and reports a roofline for its dominant kernel.
+("fp64_same_workload") and reports the rooflines of its stencils.
 
 --study errors runs App. A's comparison of equivalent solutions (methods A-F) on the
 16^3x32 field against a known solution, rho = 1e-2 .. 1e-10.
@@ -41,13 +46,14 @@ hybrid time for every n, without and with Lagrange guesses.
 --kernel fp64|s16|coarse times one kernel family alone (CUDA events, L2 flushed
 between applications) and prints its achieved rate against the roofline:
   fp64    FP64 Qhat^2 + sigma (4 stencil launches), 16^3x32
-  s16     16-bit Qhat^2 + sigma (4 stencil launches), 24^3x48, 1 and 8 RHS per launch
+  s16     16-bit Qhat^2 + sigma (4 stencil launches), 24^3x48 (1 and 8 RHS per launch)
+          and 32^3x64 (1 and 8 RHS)
   coarse  coarse doublet operator, tensor cores and CUDA cores, 24^3x48 with 4^4
           aggregates and 24 vectors per chirality, 1 and 8 RHS
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
 this method here) on the host cores, on a bounded sample of the same workload.
-Under torchrun (N > 1) every rank solves its own right-hand side (replicas: the
+Under torchrun (N > 1) every rank solves its own right-hand sides (replicas: the
 path has no data exchange between independent solves); value = all ranks'
 solves / max-over-ranks time.  Rank 0 prints one JSON line.
 """
@@ -65,17 +71,18 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DIMS = (32, 16, 16, 16)            # T, X, Y, Z
 KAPPA, MU_BAR, EPS_BAR = 0.16, 0.1, 0.11
 ROUGHNESS = 0.5
-GAUGE_SEED, RHS_SEED = 1002, 2032
 NSHIFT, SIG_LO, SIG_HI = 12, 1e-5, 2.0
 RHO = 1e-10
-METRIC = "shift-system solves/sec at rel. residual 1e-10"
-WORKLOAD = "16^3x32 ND twisted-mass doublet, FP64 multi-shift CG, 12 shifts 1e-5..2, 1 RHS, rho 1e-10"
+METRIC = "shift-system solves/sec at rel. residual 1e-10; Dslash GB/s vs HBM peak"
 L2_FLUSH_BYTES = 512 << 20         # > 129 MB L2
 
-# Algorithmic counts per odd site for ONE stencil launch (both flavours):
+# 16^3x32 workload of the plain FP64 form (and of --kernel fp64, --study errors)
+DIMS = (32, 16, 16, 16)            # T, X, Y, Z
+GAUGE_SEED, RHS_SEED = 1002, 2032
+
+# Algorithmic counts per odd site for ONE FP64 stencil launch (both flavours):
 #   flops: 2 x 1320 (Wilson hop with spin projection, 8 directions) + 240 (A^-1 or A site term)
 #   bytes (FP64, 18-real links): even launch 240 reals (in 48, links 144, out 48),
 #   odd launch 288 reals (t 48, psi 48, links 144, out 48)
@@ -84,12 +91,17 @@ HOP_BYTES_PER_SITE = (240 + 288) / 2 * 8
 # DRAM bytes of one odd-site FP64 stencil launch at 16^3x32, one ncu capture of this kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum: 132.87 MB + 9.04 MB)
 FP64_ODD_LAUNCH_TRAFFIC = 132.866816e6 + 9.036288e6
-# DRAM bytes of the 16-bit stencil at 24^3x48 (V/2 = 331776), one ncu capture: even launch
-# 98.22 + 3.71 MB, odd launch 134.10 + 7.79 MB; Qhat^2 = 2 even + 2 odd launches
-# DRAM bytes (read + write) of one 16-bit Qhat^2 + sigma at 24^3x48: the 4 launches of one ncu capture
-S16_Q2_TRAFFIC_24 = (97.503232e6 + 3.967232e6) + (132.547840e6 + 8.404480e6) + (97.519360e6 + 3.632896e6) \
-    + (169.893632e6 + 15.372288e6)
-S16_TRAFFIC_VH = 331776
+FP64_TRAFFIC_VH = 65536
+# 16-bit stencil, algorithmic bytes per odd site and right-hand side: even launch 200 (in 100,
+# out 100) + 192 links, odd launch 300 (+ psi 100) + 192 links; a Qhat^2 + sigma is 2 even +
+# 2 odd launches and the sigma term's 100; with R right-hand sides per launch the links
+# (4 x 192) are read once: R (2 (200 + 300) + 100) + 4 x 192 bytes per odd site
+S16_SPINOR_BYTES_PER_SITE = 2 * (200 + 300) + 100
+S16_LINK_BYTES_PER_SITE = 4 * 192
+# DRAM bytes (read + write) of one 16-bit Qhat^2 + sigma, one ncu capture of its 4 launches:
+# {(lattice V/2, RHS per launch): bytes}
+S16_Q2_TRAFFIC = {(331776, 1): (97.503232e6 + 3.967232e6) + (132.547840e6 + 8.404480e6)
+                  + (97.519360e6 + 3.632896e6) + (169.893632e6 + 15.372288e6)}
 
 
 def _dist():
@@ -99,9 +111,10 @@ def _dist():
     return ws, rank, local
 
 
-def replica_rhs_seed(rank: int) -> int:
-    """Seed of rank `rank`'s right-hand side: every replica solves its own system."""
-    return RHS_SEED + rank
+def replica_rhs_seed(rank: int, base: int = 2004, nrhs: int = 8) -> int:
+    """Seed of rank `rank`'s right-hand sides: every replica solves its own systems
+    (right-hand side k of the rank draws from seed + k)."""
+    return base + 1000 * rank
 
 
 def max_over_ranks(ms: float, ws: int, device="cuda") -> float:
@@ -126,6 +139,12 @@ def _peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of this machine, else the fallback."""
+    v = _peaks().get("hbm_gbs")
+    return (float(v), "MEASURED_PEAKS.json hbm_gbs (measured)") if v else (6800.0, "fallback 6.8 TB/s")
 
 
 class ClockSampler:
@@ -168,150 +187,149 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_tmnd(args):
-    import numpy as np
+def count_kernels(fn, prefix=("k_",)):
+    """Kernels of this library that one call of fn launches, counted from the CUDA
+    activity trace of torch's profiler (CUPTI; kernels replayed inside CUDA graphs
+    included), and their names.  None if the profiler is unavailable."""
     import torch
-    import torch.distributed as dist
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        n, names = 0, {}
+        for ev in prof.events():
+            nm = ev.name or ""
+            dev = str(getattr(ev, "device_type", ""))
+            base = nm.split("(")[0].split("<")[0].split(" ")[-1]
+            if "CUDA" in dev and any(base.startswith(p) for p in prefix):
+                n += 1
+                names[base] = names.get(base, 0) + 1
+        return n, names
+    except Exception as e:  # noqa: BLE001
+        return None, {"error": str(e)[:200]}
 
-    import paper_1805_09584_gb300 as tm
-    import synth
-    from paper_1805_09584_gb300 import _build
 
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    if ws > 1:
-        dist.init_process_group("nccl")
-    _build.build()
+def fp64_peak_measured():
+    """FP64 throughput of this GPU measured in this run: cuBLAS DGEMM 8192^3 through torch
+    (best of 5, CUDA events) -- the denominator of the FP64 stencil's roofline."""
+    import torch
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    bm = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = a @ bm
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c = a @ bm
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, bm, c
+    torch.cuda.empty_cache()
+    return 2 * n ** 3 / (best / 1e3) / 1e12
 
-    U = synth.random_su3_field(DIMS, ROUGHNESS, GAUGE_SEED)
-    b_host = synth.gaussian_rhs(DIMS, replica_rhs_seed(rank))[0]
-    sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
-    g = tm.Gauge(U, DIMS, KAPPA, MU_BAR, EPS_BAR)
-    stream = torch.cuda.current_stream()
-    b_dev = g.pack(torch.from_numpy(b_host).cuda())
-    xs = [g.spinor() for _ in sig]
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def step(profile=False):
-        return tm.mms_cg_solve(g.handle, b_dev, 1, sig, xs, rho=RHO, profile=profile, stream=stream)
-
-    # nvidia-smi starts before the warm-up, so that its start-up does not overlap the timed region
-    sampler = ClockSampler(local)
-    for _ in range(args.warmup):
-        info = step()
-    # ---- timed region: K solves, L2 flushed between solves
-    infos = []
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+def _median_ms(fn, flush, stream, reps):
+    import torch
+    for _ in range(3):
+        fn()
+    ts = []
+    for _ in range(reps):
         flush.fill_(1.0)
-        infos.append(step())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    ms_all = max_over_ranks(ms, ws)
-    solves = args.steps * NSHIFT * ws
-    value = whole_job_rate(args.steps * NSHIFT, ws, ms_all)
-    worst_res = max(max(i["true_res"]) for i in infos)
-    iters = infos[-1]["iters"]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
 
-    # ---- e2e: the public API with host buffers (pinned b in, all x_i out, per step)
-    b_pin = torch.from_numpy(b_host).pin_memory()
-    x_pin = torch.empty((NSHIFT, g.vh, 2, 4, 3), dtype=torch.complex128).pin_memory()
-    b_can = torch.empty((1, g.vh, 2, 4, 3), dtype=torch.complex128, device="cuda")
-    x_can = torch.empty((1, g.vh, 2, 4, 3), dtype=torch.complex128, device="cuda")
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        b_can.copy_(b_pin, non_blocking=True)
-        tm.tmnd_spinor_pack(g.handle, b_dev, b_can, 1, stream)
-        tm.mms_cg_solve(g.handle, b_dev, 1, sig, xs, rho=RHO, stream=stream)
-        for i in range(NSHIFT):
-            tm.tmnd_spinor_unpack(g.handle, x_can, xs[i], 1, stream)
-            x_pin[i].copy_(x_can[0], non_blocking=True)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(f0.elapsed_time(f1), ws)
-    e2e_value = whole_job_rate(args.steps * NSHIFT, ws, e2e_ms)
-    h2d = b_host.nbytes
-    d2h = NSHIFT * b_host.nbytes
 
-    # ---- roofline of the dominant kernel (the FP64 stencil launches): one more
-    # solve, identical to the timed ones, with CUDA events recorded around the
-    # stencil and update launches of every iteration (event nodes in the graph;
-    # kept out of the timed region so that they do not slow the headline number)
-    flush.fill_(1.0)
-    torch.cuda.synchronize()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    pinfo = step(profile=True)
-    p1.record(stream)
-    torch.cuda.synchronize()
-    prof_ms = p0.elapsed_time(p1)
-    hop_ms = pinfo["hop_ms"]
-    n_hop_launch = 4 * pinfo["iters"]
-    hop_avg_s = hop_ms / 1e3 / n_hop_launch
-    flop_per_launch = HOP_FLOP_PER_SITE * g.vh
-    achieved_tflops = flop_per_launch / hop_avg_s / 1e12
-    fp64_peak = FP64_PEAK_TFLOPS
-    upd_ms = pinfo["update_ms"]
-    launches = sum(i["launches"] for i in infos)
+def s16_roofline(tm, g, flush, stream, nrhs=1, reps=20):
+    """The 16-bit stencil of the sloppy solves: median CUDA-event time of one 16-bit
+    Qhat^2 + sigma (its 4 stencil launches, nrhs right-hand sides per launch, as the
+    solve launches them) on the form's lattice, L2 flushed, against the HBM peak."""
+    import torch
+    src = g.pack(torch.randn(nrhs * g.vh * 24, dtype=torch.complex128, device="cuda").view(nrhs, g.vh, 2, 4, 3),
+                 nrhs=nrhs)
+    q = g.convert(src, tm.TMND_F64, tm.TMND_S16, nrhs=nrhs)
+    del src
+    o = g.spinor(nrhs, prec=tm.TMND_S16)
+    ms = _median_ms(lambda: tm.tm_nd_apply(g.handle, o, q, tm.OP_QHAT2 | tm.OP_S16, 0.01, nrhs=nrhs, stream=stream),
+                    flush, stream, reps)
+    peak, src_peak = hbm_peak()
+    byts = g.vh * (nrhs * S16_SPINOR_BYTES_PER_SITE + S16_LINK_BYTES_PER_SITE)
+    gbs = byts / (ms / 1e3) / 1e9
+    tr = None
+    note = "no ncu capture of this launch shape"
+    for (vh, r), t in S16_Q2_TRAFFIC.items():
+        if r == nrhs:
+            tr = t * g.vh / vh
+            note = (f"DRAM bytes of one Qhat^2 from an ncu capture of its 4 launches at V/2 = {vh}, {r} RHS per launch"
+                    + (", scaled by the number of sites" if vh != g.vh else ""))
+            break
+    del q, o
+    return {"bound": "hbm", "kernel": f"k_hop_even_s16/k_hop_odd_s16 (16-bit stencil, Qhat^2 + sigma: 4 launches, "
+                                      f"{nrhs} RHS per launch)",
+            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": tr,
+            "traffic_note": note, "algorithmic_bytes": byts, "peak_source": src_peak,
+            "measured": f"median of {reps} CUDA-event timings of tm_nd_apply(Qhat^2 + sigma, 16-bit), L2 flushed",
+            "ms_per_qhat2": ms, "nrhs": nrhs}
 
-    out = None
-    if rank == 0:
-        out = {
-            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": "16^3x32", "nshift": NSHIFT, "nrhs": 1,
-                       "rho": RHO, "kappa": KAPPA, "mu_bar": MU_BAR, "eps_bar": EPS_BAR, "roughness": ROUGHNESS,
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "l2": "flushed between steps (512 MB write); solve working set > L2"},
-            "iters": iters, "max_true_rel_residual": worst_res,
-            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "roofline": {"bound": "alu", "kernel": "k_hop_even/k_hop_odd (FP64 stencil)",
-                         "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / fp64_peak, "traffic": FP64_ODD_LAUNCH_TRAFFIC,
-                         "traffic_note": "DRAM bytes per odd-site launch (ncu capture of this kernel, this workload)",
-                         "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                         "hop_share_of_step": hop_ms / prof_ms,
-                         "measured": "CUDA events around every iteration's 4 stencil launches of a profiled "
-                                     "solve run right after the timed steps",
-                         "hop_achieved_gbs": HOP_BYTES_PER_SITE * g.vh / hop_avg_s / 1e9,
-                         "hbm_peak_gbs": _peaks().get("hbm_gbs")},
-            "update_share_of_step": upd_ms / prof_ms,
-            "gpu_launches": launches,
-            "clocks": clocks,
-        }
-    g.close()
-    if ws > 1:
-        dist.barrier()
-        dist.destroy_process_group()
-    return out
 
+def fp64_roofline(tm, g, flush, stream, peak_tflops, reps=10):
+    """The FP64 stencil of the true residuals and defect corrections: median CUDA-event
+    time of one FP64 Qhat^2 + sigma (4 launches, 1 RHS) on the form's lattice, against
+    the FP64 throughput measured in this run (FP64-pipe bound on GB300)."""
+    import torch
+    x = g.pack(torch.randn(g.vh * 24, dtype=torch.complex128, device="cuda").view(1, g.vh, 2, 4, 3))
+    y = g.spinor()
+    ms = _median_ms(lambda: tm.tm_nd_apply(g.handle, y, x, tm.OP_QHAT2, 0.01, stream=stream), flush, stream, reps)
+    tf = 4 * HOP_FLOP_PER_SITE * g.vh / (ms / 1e3) / 1e12
+    del x, y
+    return {"bound": "alu", "kernel": "k_hop_even/k_hop_odd (FP64 stencil, Qhat^2 + sigma: 4 launches)",
+            "achieved": tf, "peak": peak_tflops, "unit": "TFLOP/s", "frac": tf / peak_tflops,
+            "traffic": FP64_ODD_LAUNCH_TRAFFIC * g.vh / FP64_TRAFFIC_VH,
+            "traffic_note": "DRAM bytes of one odd-site launch from an ncu capture at 16^3x32, scaled by the "
+                            "number of sites",
+            "peak_source": "cuBLAS DGEMM 8192^3 (torch, best of 5) measured in this run",
+            "algorithmic_flop_per_launch": HOP_FLOP_PER_SITE * g.vh,
+            "measured": f"median of {reps} CUDA-event timings of tm_nd_apply(Qhat^2 + sigma, FP64), L2 flushed",
+            "ms_per_qhat2": ms, "gbs": 4 * HOP_BYTES_PER_SITE * g.vh / (ms / 1e3) / 1e9}
 
 
 FORMS = {
-    "mixed": dict(dims=(48, 24, 24, 24), nrhs=2, seeds=(1003, 2003), lattice="24^3x48"),
-    "batched": dict(dims=(64, 32, 32, 32), nrhs=8, seeds=(1004, 2004), lattice="32^3x64"),
-    "hybrid": dict(dims=(64, 32, 32, 32), nrhs=8, seeds=(1004, 2004), lattice="32^3x64"),
-    "learned": dict(dims=(48, 24, 24, 24), nrhs=1, seeds=(1005, 2005), lattice="24^3x48"),
-    "rational": dict(dims=(48, 24, 24, 24), nrhs=2, seeds=(1003, 2003), lattice="24^3x48"),
+    "fp64": dict(dims=(32, 16, 16, 16), nrhs=1, seeds=(1002, 2032), lattice="16^3x32", batch=1),
+    "mixed": dict(dims=(48, 24, 24, 24), nrhs=2, seeds=(1003, 2003), lattice="24^3x48", batch=1),
+    "batched": dict(dims=(64, 32, 32, 32), nrhs=8, seeds=(1004, 2004), lattice="32^3x64", batch=8),
+    "hybrid": dict(dims=(64, 32, 32, 32), nrhs=8, seeds=(1004, 2004), lattice="32^3x64", batch=8),
+    "learned": dict(dims=(48, 24, 24, 24), nrhs=1, seeds=(1005, 2005), lattice="24^3x48", batch=1),
+    "rational": dict(dims=(48, 24, 24, 24), nrhs=2, seeds=(1003, 2003), lattice="24^3x48", batch=2),
 }
-# 16-bit stencil, algorithmic bytes per odd site: even launch 392 (in 100, 12-real
-# 16-bit links 192, out 100), odd launch 492 (+ psi 100); Qhat^2 + sigma adds aux 100
-S16_Q2_BYTES_PER_SITE = 2 * (392 + 492) + 100
+# the multigrid of the hybrid form: 4^4 aggregates, 24 test vectors per chirality relaxed by
+# 4 minimal-residual steps on D_TM(mu_bar) x = 0
+MG_BLOCK, MG_NV, MG_RELAX = (4, 4, 4, 4), 24, 4
+N_MMS = 8
+
+
+def workload_name(form, F, nrhs):
+    desc = {
+        "fp64": "plain FP64 multi-shift CG",
+        "mixed": "mixed-precision multi-shift CG (FP32 on 16-bit data + FP64 defect correction), RHS one at a time",
+        "batched": "mixed-precision multi-shift CG with all RHS in every 16-bit stencil launch + batched FP64 "
+                   "defect correction",
+        "hybrid": "hybrid solve: batched mixed multi-shift CG for the 8 largest shifts, Lagrange guesses and case-C "
+                  "two-level multigrid (4^4 aggregates, 24 vectors per chirality, tensor-core coarse operator) for "
+                  "the 4 smallest, batched FP64 defect correction",
+        "learned": "mixed multi-shift CG for the 8 largest shifts, learned guesses for the 4 smallest",
+        "rational": "Zolotarev n = 10 rational approximation of (Qhat^2)^(-1/2) over a mixed multi-shift solve",
+    }[form]
+    shifts = "Zolotarev shifts" if form == "rational" else "12 shifts 1e-5..2"
+    return f"{F['lattice']} ND twisted-mass doublet, {desc}, {shifts}, {nrhs} RHS, rho 1e-10"
 
 
 def _timed(step, steps, flush, stream):
@@ -328,54 +346,21 @@ def _timed(step, steps, flush, stream):
     return e0.elapsed_time(e1), out
 
 
-def s16_roofline(tm, g, flush, stream, reps=20):
-    """CUDA-event time of the sloppy Qhat^2 (4 stencil launches) on the form's lattice."""
-    import torch
-    q = g.spinor(1, prec=tm.TMND_S16)
-    tm.tmnd_spinor_convert(g.handle, q, tm.TMND_S16, g.pack(torch.randn(g.vh * 24, dtype=torch.complex128,
-                                                                          device="cuda").view(1, g.vh, 2, 4, 3)),
-                           tm.TMND_F64)
-    o = g.spinor(1, prec=tm.TMND_S16)
-    for _ in range(3):
-        tm.tm_nd_apply(g.handle, o, q, tm.OP_QHAT2 | tm.OP_S16, 0.01, stream=stream)
-    ts = []
-    for _ in range(reps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        tm.tm_nd_apply(g.handle, o, q, tm.OP_QHAT2 | tm.OP_S16, 0.01, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    ms = statistics.median(ts)
-    peak = _peaks().get("hbm_gbs") or 6800.0
-    gbs = S16_Q2_BYTES_PER_SITE * g.vh / (ms / 1e3) / 1e9
-    scaled = g.vh != S16_TRAFFIC_VH
-    return {"bound": "hbm", "kernel": "k_hop_even_s16/k_hop_odd_s16 (16-bit stencil, Qhat^2 + sigma: 4 launches)",
-            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-            "traffic": S16_Q2_TRAFFIC_24 * g.vh / S16_TRAFFIC_VH,
-            "traffic_note": "DRAM bytes per Qhat^2 from an ncu capture at 24^3x48 (its 4 launches; below the "
-                            "algorithmic bytes because each launch's output is still in L2 when the next reads it)"
-                            + (", scaled by the number of sites" if scaled else ""),
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if _peaks().get("hbm_gbs") else "fallback 6.8 TB/s",
-            "measured": f"median of {reps} CUDA-event timings of tm_nd_apply(Qhat^2, 16-bit), L2 flushed",
-            "ms_per_qhat2": ms}
-
-
 def run_form(args):
-    """One solver form on its own workload (see the module docstring)."""
+    """One solver form on its own workload (see the module docstring); the default form,
+    hybrid, is the headline.  Under torchrun every rank solves its own right-hand sides."""
     import numpy as np
     import torch
+    import torch.distributed as dist
 
     import paper_1805_09584_gb300 as tm
     import synth
     from paper_1805_09584_gb300 import _build, learned
 
     ws, rank, local = _dist()
-    if ws > 1:
-        raise SystemExit("--form runs on one GPU")
     torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
     _build.build()
     F = FORMS[args.form]
     dims, nrhs = F["dims"], F["nrhs"]
@@ -383,8 +368,9 @@ def run_form(args):
     sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
     U = synth.random_su3_field(dims, ROUGHNESS, gseed)
     g = tm.Gauge(U, dims, KAPPA, MU_BAR, EPS_BAR)
+    del U
     stream = torch.cuda.current_stream()
-    b_host = synth.gaussian_rhs(dims, bseed, nrhs=nrhs)
+    b_host = synth.gaussian_rhs(dims, bseed if ws == 1 else replica_rhs_seed(rank, bseed, nrhs), nrhs=nrhs)
     b_dev = g.pack(torch.from_numpy(b_host).cuda(), nrhs=nrhs)
     xs = [g.spinor(nrhs) for _ in sig]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -392,17 +378,16 @@ def run_form(args):
     mg = net = None
     if args.form == "hybrid":
         t0 = time.perf_counter()
-        nv = 24
-        tv = torch.randn(nv * 2 * 12 * g.vh, dtype=torch.complex64, device="cuda")
-        tm.tmnd_mg_smooth_vectors(g.handle, tv, nv, 4)
-        mg = tm.tmnd_mg_create(g.handle, (4, 4, 4, 4), nv, tv)
+        tv = torch.randn(MG_NV * 2 * 12 * g.vh, dtype=torch.complex64, device="cuda")
+        tm.tmnd_mg_smooth_vectors(g.handle, tv, MG_NV, MG_RELAX)
+        mg = tm.tmnd_mg_create(g.handle, MG_BLOCK, MG_NV, tv)
         torch.cuda.synchronize()
         extra["mg_setup_s"] = time.perf_counter() - t0
         del tv
     if args.form == "learned":
         t0 = time.perf_counter()
         Xs, Ss, Hs = [], [], []
-        for fs in range(4):   # training fields (roughness 0.3..0.7), 2 RHS each
+        for fs in range(4):   # training fields (roughness 0.3..0.6), 2 RHS each
             gt = tm.Gauge(synth.random_su3_field(dims, 0.3 + 0.1 * fs, 100 + fs), dims, KAPPA, MU_BAR, EPS_BAR)
             for bk in synth.gaussian_rhs(dims, 200 + fs, nrhs=2):
                 bd = gt.pack(torch.from_numpy(bk[None]).cuda())
@@ -414,7 +399,6 @@ def run_form(args):
         net, losses = learned.train(np.concatenate(Xs), np.concatenate(Ss), np.concatenate(Hs), epochs=600)
         extra["training"] = {"solves": 8, "samples": 32, "fields": 4, "s": time.perf_counter() - t0,
                              "loss_first_last": [losses[0], losses[-1]]}
-
     if args.form == "rational":
         # spectrum bounds of Qhat^2 from the Ritz values of one FP64 CG history (10 % margins)
         hist = np.zeros(8192)
@@ -430,29 +414,37 @@ def run_form(args):
         del xb
 
     def step():
+        if args.form == "fp64":
+            return tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs, rho=RHO, stream=stream)
         if args.form == "rational":
             return tm.tmnd_rational_apply(g.handle, b_dev, nrhs, 10, lmin, lmax, out_r, rho=RHO, prec=tm.TMND_S16,
                                           stream=stream)
         if args.form in ("mixed", "batched"):
             return tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs, rho=RHO, prec=tm.TMND_S16,
-                                   batch=1 if args.form == "mixed" else 0, stream=stream)
+                                   batch=F["batch"], stream=stream)
         if args.form == "hybrid":
-            return tm.tmnd_hybrid_solve(g.handle, mg, b_dev, nrhs, sig, 8, xs, rho=RHO, prec=tm.TMND_S16,
+            return tm.tmnd_hybrid_solve(g.handle, mg, b_dev, nrhs, sig, N_MMS, xs, rho=RHO, prec=tm.TMND_S16,
                                         n_guess=0, guess=1, stream=stream)
-        return tm.tmnd_hybrid_solve(g.handle, None, b_dev, nrhs, sig, 8, xs, rho=RHO, prec=tm.TMND_S16,
+        return tm.tmnd_hybrid_solve(g.handle, None, b_dev, nrhs, sig, N_MMS, xs, rho=RHO, prec=tm.TMND_S16,
                                     n_guess=0, guess=2, net=net, stream=stream)
 
+    # nvidia-smi starts before the warm-up, so that its start-up does not overlap the timed region
     sampler = ClockSampler(local)
     for _ in range(args.warmup):
         step()
+    if ws > 1:
+        dist.barrier()
     ms, infos = _timed(step, args.steps, flush, stream)
+    if ws > 1:
+        dist.barrier()
     clocks = sampler.stop()
+    ms_all = max_over_ranks(ms, ws)
     solves = args.steps * len(sig) * nrhs
-    value = solves / (ms / 1e3)
+    value = whole_job_rate(args.steps * len(sig) * nrhs, ws, ms_all)
     worst = max(max(i["true_res"]) for i in infos)
     if args.form == "learned":   # the same with Lagrange guesses (the method without the network)
         def step_lag():
-            return tm.tmnd_hybrid_solve(g.handle, None, b_dev, nrhs, sig, 8, xs, rho=RHO, prec=tm.TMND_S16,
+            return tm.tmnd_hybrid_solve(g.handle, None, b_dev, nrhs, sig, N_MMS, xs, rho=RHO, prec=tm.TMND_S16,
                                         n_guess=0, guess=1, stream=stream)
         step_lag()
         ms_l, inf_l = _timed(step_lag, args.steps, flush, stream)
@@ -462,66 +454,94 @@ def run_form(args):
                                      "fp64_applies": inf_l[-1]["fp64_applies"]}
         extra["learned_guesses"] = {"guess_res": infos[-1]["guess_res"][8:], "refine_iters": infos[-1]["refine_iters"],
                                     "fp64_applies": infos[-1]["fp64_applies"]}
-    # e2e: host buffers in and out through the public API
+    # solver statistics of the last timed step
+    last = infos[-1]
+    stats = {k: last[k] for k in ("iters", "mms_iters", "refine_iters", "fp64_applies", "refine_rounds", "mg_iters",
+                                  "guess_res", "lag_nodes") if k in last}
+    # e2e: host buffers in and out through the public API: the canonical right-hand sides
+    # from pinned host memory, packed, solved, and every shift's solutions unpacked and read
+    # back into pinned host memory (one buffer, reused shift by shift)
+    e2e_steps = min(args.steps, 3)
+    outs = [out_r] if args.form == "rational" else xs
     b_pin = torch.from_numpy(b_host).pin_memory()
-    x_pin = torch.empty((NSHIFT, nrhs, g.vh, 2, 4, 3), dtype=torch.complex128).pin_memory()
+    x_pin = torch.empty((nrhs, g.vh, 2, 4, 3), dtype=torch.complex128).pin_memory()
     b_can = torch.empty((nrhs, g.vh, 2, 4, 3), dtype=torch.complex128, device="cuda")
     x_can = torch.empty((nrhs, g.vh, 2, 4, 3), dtype=torch.complex128, device="cuda")
-
-    outs = [out_r] if args.form == "rational" else xs
 
     def step_e2e():
         b_can.copy_(b_pin, non_blocking=True)
         tm.tmnd_spinor_pack(g.handle, b_dev, b_can, nrhs, stream)
-        step()
-        for i, v in enumerate(outs):
+        r = step()
+        for v in outs:
             tm.tmnd_spinor_unpack(g.handle, x_can, v, nrhs, stream)
-            x_pin[i].copy_(x_can, non_blocking=True)
-    e2e_ms, _ = _timed(step_e2e, args.steps, flush, stream)
+            x_pin.copy_(x_can, non_blocking=True)
+        return r
+    if ws > 1:
+        dist.barrier()
+    e2e_ms, _ = _timed(step_e2e, e2e_steps, flush, stream)
+    e2e_all = max_over_ranks(e2e_ms, ws)
+    del b_pin, x_pin, b_can, x_can
+    # kernels launched per step (torch profiler's CUDA activity trace of one more step)
+    nk, knames = count_kernels(step)
     # the plain FP64 multi-shift CG on the same workload (one step), and each form's solutions
     # against its solutions: max over shifts of |x_form - x_FP64| / |x_FP64| (all RHS together)
-    keep = [v.clone() for v in xs[:len(sig)]] if args.form != "rational" else None
-    f64 = lambda: tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs[:len(sig)], rho=RHO, stream=stream)
-    f64()
-    f64_ms, _ = _timed(f64, 1, flush, stream)
-    if keep is not None:
-        dx = [float(torch.linalg.vector_norm(k - v) / torch.linalg.vector_norm(v)) for k, v in zip(keep, xs)]
-        extra["rel_diff_vs_fp64"] = {"max": max(dx), "per_shift": [float("%.3g" % d) for d in dx]}
-        del keep
-    roof = s16_roofline(tm, g, flush, stream)
-    if mg is not None:   # the coarse operator on the tensor cores, all 8 RHS at once
+    if args.form != "fp64":
+        keep = [v.clone() for v in xs[:len(sig)]] if args.form != "rational" else None
+        f64 = lambda: tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs[:len(sig)], rho=RHO, stream=stream)
+        f64()
+        f64_ms, f64_inf = _timed(f64, 1, flush, stream)
+        extra["fp64_same_workload"] = {"value": nrhs * len(sig) / (f64_ms / 1e3), "ms_per_step": f64_ms,
+                                       "iters": f64_inf[0]["iters"]}
+        if keep is not None:
+            dx = [float(torch.linalg.vector_norm(k - v) / torch.linalg.vector_norm(v)) for k, v in zip(keep, xs)]
+            extra["rel_diff_vs_fp64"] = {"max": max(dx), "per_shift": [float("%.3g" % d) for d in dx]}
+            del keep
+    # rooflines of the two stencils on this lattice
+    fp64_peak = fp64_peak_measured()
+    roof = s16_roofline(tm, g, flush, stream, nrhs=F["batch"])
+    roof64 = fp64_roofline(tm, g, flush, stream, fp64_peak)
+    if mg is not None:   # the coarse operator on the tensor cores, all RHS at once
         nb = g.vh * 2 // 256
-        xc = torch.randn(nrhs * nb * 4 * 24, dtype=torch.complex64, device="cuda")
+        xc = torch.randn(nrhs * nb * 4 * MG_NV, dtype=torch.complex64, device="cuda")
         yc = torch.empty_like(xc)
-        tm.mg_coarse_apply(mg, yc, xc, nrhs, 0.0, stream=stream)
-        c_ms, _ = _timed(lambda: tm.mg_coarse_apply(mg, yc, xc, nrhs, 0.0, stream=stream), 10, flush, stream)
-        byts = nb * 9 * 48 * 48 * 8 + 2 * nrhs * nb * 4 * 24 * 8
-        extra["coarse_tc"] = {"ms": c_ms / 10, "GBs": byts / (c_ms / 10 / 1e3) / 1e9, "nrhs": nrhs,
+        c_ms = _median_ms(lambda: tm.mg_coarse_apply(mg, yc, xc, nrhs, 0.0, stream=stream), flush, stream, 10)
+        byts = nb * 9 * (2 * MG_NV) ** 2 * 8 + 2 * nrhs * nb * 4 * MG_NV * 8
+        extra["coarse_tc"] = {"ms": c_ms, "GBs": byts / (c_ms / 1e3) / 1e9, "nrhs": nrhs,
+                              "frac_hbm": byts / (c_ms / 1e3) / 1e9 / hbm_peak()[0],
                               "kernel": "k_coarse_apply_tc (tcgen05 TF32, 48x48 blocks)"}
-    launches = sum(i.get("launches", 0) for i in infos) or None
-    out = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32/16-bit sloppy + f64 defect correction", "data": "synthetic",
-        "config": {"workload": f"{F['lattice']} ND twisted-mass doublet, {args.form} form, "
-                               + ("Zolotarev n = 10 shifts" if args.form == "rational" else "12 shifts 1e-5..2")
-                               + f", {nrhs} RHS, rho 1e-10", "form": args.form, "lattice": F["lattice"],
-                   "nshift": len(sig), "nrhs": nrhs, "rho": RHO, "kappa": KAPPA, "mu_bar": MU_BAR,
-                   "eps_bar": EPS_BAR, "roughness": ROUGHNESS, "parallelism": "single GPU",
-                   "l2": "flushed between steps (512 MB write); solve working set > L2"},
-        "max_true_rel_residual": worst,
-        "fp64_same_workload": {"value": nrhs * len(sig) / (f64_ms / 1e3), "ms_per_step": f64_ms},
-        "e2e": {"value": solves / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": b_host.nbytes,
-                "d2h_bytes_per_step": len(outs) * b_host.nbytes},
-        "roofline": roof, "gpu_launches": launches, "clocks": clocks, **extra,
-    }
+    launches_claim = nk * args.steps if nk else (sum(i.get("launches", 0) for i in infos) or None)
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64" if args.form == "fp64" else "f32 (16-bit storage) + f64 (true residuals, defect correction)",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.form, F, nrhs), "form": args.form, "lattice": F["lattice"],
+                       "nshift": len(sig), "nrhs": nrhs, "rho": RHO, "kappa": KAPPA, "mu_bar": MU_BAR,
+                       "eps_bar": EPS_BAR, "roughness": ROUGHNESS,
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "flushed between steps (512 MB write); solve working set > L2"},
+            "max_true_rel_residual": worst,
+            "e2e": {"value": whole_job_rate(e2e_steps * len(sig) * nrhs, ws, e2e_all), "unit": "solves/s",
+                    "h2d_bytes_per_step": b_host.nbytes, "d2h_bytes_per_step": len(outs) * b_host.nbytes,
+                    "steps": e2e_steps},
+            "roofline": roof, "roofline_fp64": roof64, "solver": stats,
+            "gpu_launches": launches_claim,
+            "gpu_launches_note": ("kernels per step counted from torch.profiler's CUDA activity trace of one "
+                                  "step, times the timed steps" if nk else "the library's own launch count"),
+            "kernels_per_step": knames, "clocks": clocks, **extra,
+        }
     if net is not None:
         tm.tmnd_mlp_destroy(net)
     if mg is not None:
         tm.tmnd_mg_destroy(mg)
     g.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
     return out
-
 
 
 def run_kernel(args):
@@ -565,7 +585,7 @@ def run_kernel(args):
         out.update(lattice="16^3x32", ms_qhat2=ms, tflops=tf, fp64_peak_tflops=FP64_PEAK_TFLOPS,
                    frac=tf / FP64_PEAK_TFLOPS, gbs=4 * HOP_BYTES_PER_SITE * g.vh / (ms / 1e3) / 1e9)
     elif args.kernel == "s16":
-        for dims, name, rs in (((48, 24, 24, 24), "24^3x48", (1, 8)), ((64, 32, 32, 32), "32^3x64", (1,))):
+        for dims, name, rs in (((48, 24, 24, 24), "24^3x48", (1, 8)), ((64, 32, 32, 32), "32^3x64", (1, 8))):
             g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
             for R in rs:
                 b = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, 2003, nrhs=R)).cuda(), nrhs=R)
@@ -786,48 +806,16 @@ def run_study_errors(args):
             "rows": rows}
 
 
-# FP64 peak of a GB300 (sm_103a): 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
+
+
+# nominal FP64 rate of a GB300 (sm_103a): 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz;
+# the headline's FP64 roofline uses the DGEMM rate measured in the run instead
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def cpu_baseline(iters_full: int, sample_iters: int = 6):
-    """The oracle, as it stands, on the host cores: `sample_iters` MMS-CG
-    iterations of the same workload, scaled to a full solve of `iters_full`
-    iterations (the oracle's own count for this workload, tests/golden)."""
-    import oracle
-    import synth
-    U = synth.random_su3_field(DIMS, ROUGHNESS, GAUGE_SEED)
-    b = synth.gaussian_rhs(DIMS, RHS_SEED)[0]
-    sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
-    act = oracle.action(DIMS, KAPPA, MU_BAR, EPS_BAR)
-    t = time.perf_counter()
-    oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=sample_iters)
-    el = time.perf_counter() - t
-    per_iter = el / sample_iters
-    out = {"value": NSHIFT / (per_iter * iters_full), "unit": "solves/s", "cores": oracle.nthreads(),
-           "kind": "oracle",
-           "sample": f"{sample_iters} MMS-CG iterations of the full 16^3x32 12-shift solve "
-                     f"({el:.1f} s), scaled to the oracle's full solve of {iters_full} iterations"}
-    # the same on one thread (OpenMP fixes its thread count at start-up: a child process)
-    code = ("import sys, time; sys.path.insert(0, %r); import oracle, synth; "
-            "U = synth.random_su3_field(%r, %r, %r); b = synth.gaussian_rhs(%r, %r)[0]; "
-            "sig = synth.shift_set(%r, %r, %r); act = oracle.action(%r, %r, %r, %r); "
-            "t = time.perf_counter(); oracle.mms_cg(act, U, b, sig, rho=%r, maxiter=2); "
-            "print(time.perf_counter() - t)") % (ROOT, DIMS, ROUGHNESS, GAUGE_SEED, DIMS, RHS_SEED, NSHIFT, SIG_LO,
-                                                 SIG_HI, DIMS, KAPPA, MU_BAR, EPS_BAR, RHO)
-    try:
-        r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
-                           capture_output=True, text=True, timeout=300)
-        el1 = float(r.stdout.strip().splitlines()[-1])
-        out["single_thread"] = {"value": NSHIFT / (el1 / 2 * iters_full), "unit": "solves/s", "cores": 1,
-                                "sample": f"2 MMS-CG iterations on one thread ({el1:.1f} s), scaled likewise"}
-    except (subprocess.SubprocessError, ValueError, IndexError) as e:
-        out["single_thread"] = {"value": None, "error": str(e)[:200]}
-    return out
-
-
-def oracle_full_iters():
-    p = os.path.join(ROOT, "tests", "golden", "mms_16x16x16x32.json")
+def oracle_full_iters(name):
+    """The oracle's own iteration count for a workload (tests/golden/make_golden.py)."""
+    p = os.path.join(ROOT, "tests", "golden", name + ".json")
     try:
         with open(p) as f:
             return int(json.load(f)["iters"])
@@ -835,46 +823,109 @@ def oracle_full_iters():
         return None
 
 
-def run_reference(args):
+GOLDEN = {"fp64": "mms_16x16x16x32", "hybrid": "mms_32x32x32x64", "batched": "mms_32x32x32x64"}
+
+
+def _oracle_inputs(form):
+    import oracle
+    import synth
+    F = FORMS[form]
+    dims = F["dims"]
+    U = synth.random_su3_field(dims, ROUGHNESS, F["seeds"][0])
+    b = synth.gaussian_rhs(dims, F["seeds"][1], nrhs=F["nrhs"])[0]
+    act = oracle.action(dims, KAPPA, MU_BAR, EPS_BAR)
+    return oracle, U, b, synth.shift_set(NSHIFT, SIG_LO, SIG_HI), act
+
+
+def cpu_baseline(form, sample_iters=3):
+    """The oracle, as it stands, on the host cores (all of them: OpenMP over sites).
+    fp64 form: the oracle's complete 12-shift solve of the same system, timed.
+    32^3x64 forms: one right-hand side, a bounded sample -- the solve's set-up alone
+    (maxiter 0) and `sample_iters` iterations -- scaled to the oracle's own iteration
+    count for that system (tests/golden) and to the workload's 8 right-hand sides."""
+    oracle, U, b, sig, act = _oracle_inputs(form)
+    nrhs = FORMS[form]["nrhs"]
+    if form == "fp64":
+        t = time.perf_counter()
+        res = oracle.mms_cg(act, U, b, sig, rho=RHO)
+        el = time.perf_counter() - t
+        return {"value": NSHIFT / el, "unit": "solves/s", "cores": oracle.nthreads(), "kind": "oracle",
+                "sample": f"the oracle's complete 16^3x32 12-shift solve ({res['iters']} iterations, {el:.1f} s)"}
+    iters_full = oracle_full_iters(GOLDEN[form])
+    if iters_full is None:
+        return {"value": None, "unavailable": "the oracle's iteration count for this workload is not recorded"}
+    t = time.perf_counter()
+    oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=0)
+    t_setup = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=sample_iters)
+    t_k = time.perf_counter() - t
+    per_iter = max(t_k - t_setup, 1e-9) / sample_iters
+    full = t_setup + iters_full * per_iter
+    return {"value": NSHIFT * nrhs / (nrhs * full), "unit": "solves/s", "cores": oracle.nthreads(), "kind": "oracle",
+            "sample": f"1 of the {nrhs} right-hand sides: the oracle's set-up ({t_setup:.1f} s) and {sample_iters} "
+                      f"multi-shift CG iterations ({t_k:.1f} s with set-up) of its 12-shift FP64 solve, scaled to "
+                      f"the oracle's {iters_full}-iteration solve of that system and to {nrhs} right-hand sides",
+            "projected_s_per_step": nrhs * full}
+
+
+def run_reference(args, form=None):
+    """--impl reference: the FP64 oracle on the host cores, on the default form's workload
+    (rank 0 only).  Each step is one call of the oracle's multi-shift CG on one of the
+    right-hand sides, stopped after one iteration; the warm-up steps time the solve's
+    set-up alone (maxiter 0).  The value scales the median step to the oracle's full
+    iteration count for that system and to all right-hand sides of the workload."""
     ws, rank, _ = _dist()
     if rank != 0:
         return None
-    iters_full = oracle_full_iters()
+    form = form or args.form
+    if form not in GOLDEN:
+        form = "hybrid"
+    iters_full = oracle_full_iters(GOLDEN[form])
     if iters_full is None:
         return {"impl": "reference", "unavailable": "oracle iteration count for the workload not recorded"}
-    import oracle
-    import synth
-    U = synth.random_su3_field(DIMS, ROUGHNESS, GAUGE_SEED)
-    b = synth.gaussian_rhs(DIMS, RHS_SEED)[0]
-    sig = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
-    act = oracle.action(DIMS, KAPPA, MU_BAR, EPS_BAR)
-    sample = 2
-    for _ in range(args.warmup):
-        oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=1)
-    t = time.perf_counter()
+    oracle, U, b, sig, act = _oracle_inputs(form)
+    F = FORMS[form]
+    nrhs = F["nrhs"]
+    setup = []
+    for _ in range(max(args.warmup, 1)):
+        t = time.perf_counter()
+        oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=0)
+        setup.append(time.perf_counter() - t)
+    steps = []
+    t_all = time.perf_counter()
     for _ in range(args.steps):
-        oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=sample)
-    el = time.perf_counter() - t
-    per_iter = el / (args.steps * sample)
-    value = NSHIFT / (per_iter * iters_full)
+        t = time.perf_counter()
+        oracle.mms_cg(act, U, b, sig, rho=RHO, maxiter=1)
+        steps.append(time.perf_counter() - t)
+    el = time.perf_counter() - t_all
+    t_setup = statistics.median(setup)
+    per_iter = max(statistics.median(steps) - t_setup, 1e-9)
+    full = t_setup + iters_full * per_iter          # one right-hand side, seconds
+    value = NSHIFT / full
+    sample = (f"each step: one oracle multi-shift CG call on 1 of the {nrhs} right-hand sides, stopped after 1 "
+              f"iteration (median {statistics.median(steps):.2f} s; set-up alone {t_setup:.2f} s), scaled to the "
+              f"oracle's {iters_full}-iteration solve of that system; value = {NSHIFT * nrhs} solves / "
+              f"({nrhs} x that time)")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * iters_full * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / max(args.steps, 1) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": "16^3x32", "nshift": NSHIFT, "nrhs": 1, "rho": RHO},
+            "config": {"workload": workload_name(form, F, nrhs), "form": form, "lattice": F["lattice"],
+                       "nshift": NSHIFT, "nrhs": nrhs, "rho": RHO},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle.nthreads(), "kind": "oracle",
-                             "sample": f"each step: {sample} MMS-CG iterations of the full workload, scaled to "
-                                       f"the oracle's {iters_full}-iteration solve"},
+                             "sample": sample},
+            "projected_s_per_workload": nrhs * full,
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tmnd", choices=["tmnd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "batched", "hybrid", "learned", "rational"])
+    ap.add_argument("--form", default="hybrid", choices=list(FORMS))
     ap.add_argument("--kernel", default=None, choices=["fp64", "s16", "coarse"])
     ap.add_argument("--study", default=None, choices=["hybrid", "learned", "errors"])
     args = ap.parse_args()
@@ -890,15 +941,13 @@ def main():
         if out is not None:
             print(json.dumps(out))
         return
-    if args.form != "fp64":
-        print(json.dumps(run_form(args)))
-        return
-    out = run_tmnd(args)
+    out = run_form(args)
     ws, rank, _ = _dist()
     if rank == 0 and out is not None:
-        if ws == 1 and not args.no_cpu_baseline:
-            itf = oracle_full_iters() or out["iters"]
-            out["cpu_baseline"] = cpu_baseline(itf)
+        if args.form == "fp64":
+            out["roofline"], out["roofline_s16"] = out.pop("roofline_fp64"), out.pop("roofline")
+        if ws == 1 and not args.no_cpu_baseline and args.form in GOLDEN:
+            out["cpu_baseline"] = cpu_baseline(args.form)
         print(json.dumps(out))
 
 

@@ -374,23 +374,31 @@ typedef struct {
 
 typedef struct {
     int mms_iters;                         /* base iterations of the multi-shift part */
-    double guess_res[TMND_MAX_SHIFTS];     /* relative residual of each MG shift's initial guess (RHS 0) */
-    int mg_iters[TMND_MAX_SHIFTS];         /* outer MG iterations of the two case-C solves (RHS 0) */
+    double guess_res[TMND_MAX_SHIFTS];     /* FP64 relative residual of each remaining shift's initial
+                                              guess (RHS 0) */
+    int mg_iters[TMND_MAX_SHIFTS];         /* outer MG iterations of the two case-C solves (RHS 0); the
+                                              GCR stops at once when the guess already meets mg_tol */
     double true_res[TMND_MAX_SHIFTS];      /* final FP64 relative residuals (max over RHS) */
     int fp64_applies;                      /* FP64 operator applications */
     int refine_iters;                      /* sloppy defect-correction iterations */
-    double shift_ms[TMND_MAX_SHIFTS];      /* wall time of each non-MMS shift's guess, MG and
-                                              defect correction (RHS 0); the MMS part's in mms_ms */
+    double shift_ms[TMND_MAX_SHIFTS];      /* wall time of each non-MMS shift's guesses, MG solves and
+                                              batched defect correction (all RHS); the MMS part's in
+                                              mms_ms */
     double mms_ms;                         /* wall time of the multi-shift part (all RHS) */
     int lag_nodes[TMND_MAX_SHIFTS];        /* guess = 1: interpolation nodes used for each shift */
     double lebesgue[TMND_MAX_SHIFTS];      /* guess = 1: gamma of those nodes at the shift */
+    long long launches;                    /* kernels launched by the multi-shift part and the defect
+                                              corrections (the multigrid's own launches not counted) */
 } tmnd_hybrid_info;
 
 /* Hybrid solve of (Qhat^2 + sigma_i) x_i = b (Sec. 4.3): multi-shift CG for
  * the n_mms largest shifts, case-C multigrid solves from guesses for the rest
  * (see above), every shift finished by FP64 defect correction to hp->rho.
  * mg may be NULL: then the remaining shifts go from their guesses straight to the
- * defect correction (sloppy CG on the FP64 defect).
+ * defect correction (sloppy CG on the FP64 defect).  The remaining shifts are taken in
+ * descending order; for each, every right-hand side gets its guess (and case-C solves),
+ * then the defect corrections of all right-hand sides of that shift run as one batched
+ * sloppy solve (up to 16 per stencil launch).
  * b, x as in mms_cg_solve (FP64 internal odd spinors).  Synchronous. */
 tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void *b, int nrhs, const double *sigma, int nshift,
                               int n_mms, void *const *x, const tmnd_hybrid_params *hp, tmnd_hybrid_info *info,

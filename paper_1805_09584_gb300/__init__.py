@@ -68,7 +68,8 @@ class HybridInfo(ctypes.Structure):
                 ("mg_iters", ctypes.c_int * MAX_SHIFTS), ("true_res", ctypes.c_double * MAX_SHIFTS),
                 ("fp64_applies", ctypes.c_int), ("refine_iters", ctypes.c_int),
                 ("shift_ms", ctypes.c_double * MAX_SHIFTS), ("mms_ms", ctypes.c_double),
-                ("lag_nodes", ctypes.c_int * MAX_SHIFTS), ("lebesgue", ctypes.c_double * MAX_SHIFTS)]
+                ("lag_nodes", ctypes.c_int * MAX_SHIFTS), ("lebesgue", ctypes.c_double * MAX_SHIFTS),
+                ("launches", ctypes.c_longlong)]
 
 
 class SolveParams(ctypes.Structure):
@@ -360,7 +361,8 @@ def tmnd_hybrid_solve(h, mg, b, nrhs: int, sigma, n_mms: int, x, rho: float = 1e
            "mg_iters": list(info.mg_iters[:ns]), "true_res": list(info.true_res[:ns]),
            "fp64_applies": info.fp64_applies, "refine_iters": info.refine_iters,
            "shift_ms": list(info.shift_ms[:ns]), "mms_ms": info.mms_ms,
-           "lag_nodes": list(info.lag_nodes[:ns]), "lebesgue": list(info.lebesgue[:ns])}
+           "lag_nodes": list(info.lag_nodes[:ns]), "lebesgue": list(info.lebesgue[:ns]),
+           "launches": info.launches}
     _check(st)
     return out
 

@@ -1020,6 +1020,7 @@ struct DCItem {
     double2 *x;
     double sigma, bb;
     double *res;
+    double *res0 = nullptr;  // optional: the relative residual of the first round (before any correction)
 };
 
 static tmnd_status defect_correct(tmnd_gauge *g, void *base, std::vector<DCItem> todo, double rho,
@@ -1047,6 +1048,7 @@ static tmnd_status defect_correct(tmnd_gauge *g, void *base, std::vector<DCItem>
                 rs.fp64++;
                 rs.launches += 5;
                 *it.res = sqrt(rr / it.bb);
+                if (round == 0 && it.res0) *it.res0 = *it.res;
                 if (!isfinite(*it.res)) {
                     tmnd_set_error("solve: NaN/Inf in an FP64 defect (shift %g)", it.sigma);
                     return TMND_ERR_NAN;
@@ -1350,6 +1352,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
     if (hinfo) {
         memset(hinfo, 0, sizeof *hinfo);
         hinfo->mms_ms = mms_ms;
+        hinfo->launches = si.launches;
         hinfo->mms_iters = si.iters;
         hinfo->fp64_applies = si.fp64_applies;
         hinfo->refine_iters = si.refine_iters;
@@ -1389,9 +1392,11 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
             return TMND_ERR_CUDA;
         }
     }
-    // 2. the remaining shifts one by one
+    // 2. the remaining shifts in descending order; per shift every right-hand side's guess and
+    // case-C multigrid solve, then one batched FP64 defect correction of all its (RHS, shift) pairs
     const double rho_inner = hp->rho_inner > 0 ? hp->rho_inner : 1e-5;
-    st = tmnd_ensure_workspace(g, mixed_work_bytes(Vh, 1));
+    const int dc_batch = nrhs < TMND_MAX_BATCH ? nrhs : TMND_MAX_BATCH;
+    st = tmnd_ensure_workspace(g, mixed_work_bytes(Vh, 1, dc_batch));
     if (st != TMND_OK) return st;
     const long nfull = 2 * n;  // full-lattice FP32 doublet (complex numbers)
     const size_t f32b = sizeof(float2) * nfull;
@@ -1417,32 +1422,36 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
     const int nbs = stream_blocks(n);
     MixedWork m = mixed_work(g->work, Vh, 1);
     tmnd_status res_status = TMND_OK;
+    // |b_k|^2 in FP64
+    std::vector<double> bbk(nrhs, 0.0);
     for (int k = 0; k < nrhs && res_status == TMND_OK; k++) {
-        const double2 *bk = (const double2 *)b + (size_t)k * n;
-        double2 *xk[NS];
-        for (int i = 0; i < nshift; i++) xk[i] = (double2 *)x[i] + (size_t)k * n;
-        double bb = 0;
-        {
-            double *part = (double *)g->partials;
-            cudaMemsetAsync(m.y64, 0, sizeof(double2) * n, s);
-            k_diff_norm<<<nbs, UPD_THREADS, 0, s>>>(n, bk, m.y64, part);
-            std::vector<double> h(nbs);
-            cudaMemcpyAsync(h.data(), part, sizeof(double) * nbs, cudaMemcpyDeviceToHost, s);
-            cudaError_t e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) {
-                tmnd_set_error("tmnd_hybrid_solve: %s", cudaGetErrorString(e));
-                res_status = TMND_ERR_CUDA;
-                break;
-            }
-            for (int q = 0; q < nbs; q++) bb += h[q];
+        double *part = (double *)g->partials;
+        cudaMemsetAsync(m.y64, 0, sizeof(double2) * n, s);
+        k_diff_norm<<<nbs, UPD_THREADS, 0, s>>>(n, (const double2 *)b + (size_t)k * n, m.y64, part);
+        std::vector<double> h(nbs);
+        cudaMemcpyAsync(h.data(), part, sizeof(double) * nbs, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            tmnd_set_error("tmnd_hybrid_solve: %s", cudaGetErrorString(e));
+            res_status = TMND_ERR_CUDA;
+            break;
         }
-        // case-C right-hand side (0, gamma_5 tau_1 b) in FP32 full layout (parity 0 even, 1 odd)
-        k_g5tau1<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Vh, bk, gb);
-        cudaMemsetAsync(rhs, 0, sizeof(float2) * n, s);
-        k_to_f32_scaled<<<nbs, 256, 0, s>>>(n, 1.0, gb, rhs + n);
-        for (int i = n_mms; i < nshift && res_status == TMND_OK; i++) {
-            const auto t_shift = std::chrono::steady_clock::now();
-            // guess
+        for (int q = 0; q < nbs; q++) bbk[k] += h[q];
+    }
+    for (int i = n_mms; i < nshift && res_status == TMND_OK; i++) {
+        const auto t_shift = std::chrono::steady_clock::now();
+        const double sq = sqrt(sigma[i]);
+        std::vector<double> res(nrhs, 0.0), res0(nrhs, 0.0);
+        std::vector<DCItem> items;
+        for (int k = 0; k < nrhs && res_status == TMND_OK; k++) {
+            const double2 *bk = (const double2 *)b + (size_t)k * n;
+            double2 *xk[NS];
+            for (int q = 0; q < nshift; q++) xk[q] = (double2 *)x[q] + (size_t)k * n;
+            if (bbk[k] == 0.0) {  // b = 0: x = 0 is exact
+                cudaMemsetAsync(xk[i], 0, sizeof(double2) * n, s);
+                continue;
+            }
+            // guess (the guess shifts of the multi-shift solve already hold theirs)
             if (i >= nmms_all) {
                 if (hp->guess == 2) {
                     const void *xs[8];
@@ -1472,13 +1481,21 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
                     cudaMemsetAsync(xk[i], 0, sizeof(double2) * n, s);
                 }
             }
-            double rr0 = 0;
-            st = fp64_defect(g, m, bk, xk[i], sigma[i], s, &rr0);
-            if (st != TMND_OK) { res_status = st; break; }
-            if (hinfo && k == 0) hinfo->guess_res[i] = sqrt(rr0 / bb);
-            const double sq = sqrt(sigma[i]);
             int mg_it = 0;
-            if (mg && sqrt(rr0 / bb) > hp->rho) {
+            if (mg) {
+                if (k == 0) {  // the guess's FP64 residual (RHS 0), before the multigrid
+                    double rr0 = 0;
+                    st = fp64_defect(g, m, bk, xk[i], sigma[i], s, &rr0);
+                    if (st != TMND_OK) { res_status = st; break; }
+                    if (hinfo) {
+                        hinfo->guess_res[i] = bbk[0] > 0 ? sqrt(rr0 / bbk[0]) : 0.0;
+                        hinfo->fp64_applies += 1;
+                    }
+                }
+                // case-C right-hand side (0, gamma_5 tau_1 b) in FP32 full layout (parity 0 even, 1 odd)
+                k_g5tau1<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Vh, bk, gb);
+                cudaMemsetAsync(rhs, 0, sizeof(float2) * n, s);
+                k_to_f32_scaled<<<nbs, 256, 0, s>>>(n, 1.0, gb, rhs + n);
                 for (int sgn = 1; sgn >= -1; sgn -= 2) {
                     float2 *y = sgn > 0 ? yp : ym;
                     // odd guess (Qhat - sgn i s) x~ ; Qhat = g5 t1 Mhat
@@ -1504,22 +1521,23 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
                 k_casec_combine<<<nbs, 256, 0, s>>>(n, sq, yp + n, ym + n, xk[i]);
             }
             if (hinfo && k == 0) hinfo->mg_iters[i] = mg_it;
-            // FP64 defect correction to rho
-            std::vector<double> res(nshift, 0.0);
-            RefineStats rs;
-            std::vector<DCItem> one{DCItem{bk, xk[i], sigma[i], bb, &res[i]}};
-            st = defect_correct(g, g->work, one, hp->rho, rho_inner, hp->maxiter, 32, 0, s, rs, 1);
-            if (st != TMND_OK) { res_status = st; break; }
-            if (hinfo && k == 0) {
-                cudaStreamSynchronize(s);
-                hinfo->shift_ms[i] =
-                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_shift).count();
-            }
-            if (hinfo) {
-                hinfo->fp64_applies += rs.fp64 + 1;
-                hinfo->refine_iters += rs.iters;
-                if (k == 0 || res[i] > hinfo->true_res[i]) hinfo->true_res[i] = res[i];
-            }
+            items.push_back(DCItem{bk, xk[i], sigma[i], bbk[k], &res[k], &res0[k]});
+        }
+        if (res_status != TMND_OK) break;
+        // FP64 defect correction of this shift's pairs to rho, all right-hand sides together
+        RefineStats rs;
+        st = defect_correct(g, g->work, items, hp->rho, rho_inner, hp->maxiter, 32, 0, s, rs, dc_batch);
+        if (st != TMND_OK) { res_status = st; break; }
+        if (hinfo) {
+            if (!mg) hinfo->guess_res[i] = res0[0];  // the guess's residual: the first FP64 defect
+            cudaStreamSynchronize(s);
+            hinfo->shift_ms[i] =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_shift).count();
+            hinfo->fp64_applies += rs.fp64;
+            hinfo->refine_iters += rs.iters;
+            hinfo->launches += rs.launches;
+            for (int k = 0; k < nrhs; k++)
+                if (k == 0 || res[k] > hinfo->true_res[i]) hinfo->true_res[i] = res[k];
         }
     }
     cudaEventRecord(e0, s);

@@ -59,12 +59,15 @@ def test_single_rank_helpers():
     assert bench.whole_job_rate(24, 1, 500.0) == 48.0
 
 
-def test_reference_arm_line(oracle_lib):
+def test_reference_arm_line(oracle_lib, monkeypatch):
     """bench.py --impl reference times the oracle on the host and prints the contract's keys
-    (one step of two multi-shift CG iterations of the 16^3x32 workload)."""
+    (the default form's workload shrunk to 4^3x8 with 2 right-hand sides, one step)."""
     import argparse
     import bench
-    line = bench.run_reference(argparse.Namespace(steps=1, warmup=0))
+    monkeypatch.setitem(bench.FORMS, "hybrid", dict(dims=(8, 4, 4, 4), nrhs=2, seeds=(11, 12), lattice="4^3x8",
+                                                    batch=2))
+    monkeypatch.setattr(bench, "oracle_full_iters", lambda name: 50)
+    line = bench.run_reference(argparse.Namespace(steps=1, warmup=1, form="hybrid"))
     for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in line, k

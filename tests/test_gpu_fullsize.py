@@ -73,8 +73,11 @@ def test_hybrid_32_certified_by_oracle():
     del tv
     bi = g.pack(torch.from_numpy(b).cuda(), nrhs=8)
     xs = [g.spinor(8) for _ in SIG]
-    info = tm.tmnd_hybrid_solve(g.handle, mg, bi, 8, SIG, 8, xs, prec=tm.TMND_S16, n_guess=0, guess=1)
-    assert all(it > 0 for it in info["mg_iters"][8:]), info     # the multigrid branch ran
+    # mg_tol 3e-7 of |b|: the Lagrange guess of shift 8 (residual ~3e-6) leaves the case-C
+    # multigrid real work; the smaller shifts' guesses may already be below it
+    info = tm.tmnd_hybrid_solve(g.handle, mg, bi, 8, SIG, 8, xs, prec=tm.TMND_S16, n_guess=0, guess=1, mg_tol=3e-7)
+    assert all(0 < r < 1e-3 for r in info["guess_res"][8:]), info
+    assert info["mg_iters"][8] > 0, info
     act = oracle.action(dims, KAPPA, MU, EPS)
     for i, k in ((11, 0), (9, 5), (3, 7), (0, 2)):
         x = g.unpack(xs[i], 8)[k].cpu().numpy()
