@@ -332,7 +332,9 @@ def workload_name(form, F, nrhs):
     return f"{F['lattice']} ND twisted-mass doublet, {desc}, {shifts}, {nrhs} RHS, rho 1e-10"
 
 
-def _timed(step, steps, flush, stream):
+def _timed(step, steps, flush, stream, nvtx=None):
+    """CUDA-event time of `steps` calls of step (L2 flushed before each); each call inside an
+    NVTX range named `nvtx` if given (profilers can select the timed steps by it)."""
     import torch
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -340,7 +342,11 @@ def _timed(step, steps, flush, stream):
     e0.record(stream)
     for _ in range(steps):
         flush.fill_(1.0)
+        if nvtx:
+            torch.cuda.nvtx.range_push(nvtx)
         out.append(step())
+        if nvtx:
+            torch.cuda.nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1), out
@@ -434,7 +440,7 @@ def run_form(args):
         step()
     if ws > 1:
         dist.barrier()
-    ms, infos = _timed(step, args.steps, flush, stream)
+    ms, infos = _timed(step, args.steps, flush, stream, nvtx="timed_step")
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
