@@ -382,6 +382,17 @@ def run_form(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     extra = {}
     mg = net = None
+    if args.form != "fp64":
+        # launch shapes of the 16-bit stencil for every batch size a solve may launch (1..16
+        # right-hand sides), tuned here so that no timed step pays for it
+        t0 = time.perf_counter()
+        per = {}
+        for R in range(1, tm.TMND_MAX_BATCH + 1):
+            sh, tms = tm.tmnd_autotune(g.handle, R, stream)
+            per[R] = {"shape": sh, "ms": [round(float(v), 4) for v in tms]}
+        extra["autotune"] = {"shapes": [tm.tmnd_s16_shape_info(i) for i in range(tm.S16_SHAPES)],
+                             "shape_fields": ["threads per block", "blocks per SM", "next-direction prefetch"],
+                             "per_nrhs": per, "s": time.perf_counter() - t0}
     if args.form == "hybrid":
         t0 = time.perf_counter()
         tv = torch.randn(MG_NV * 2 * 12 * g.vh, dtype=torch.complex64, device="cuda")

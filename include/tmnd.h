@@ -75,8 +75,11 @@ typedef enum {
     TMND_OP_MHAT_DAG = 1,  /* out = Mhat^+ in                          */
     TMND_OP_QHAT2 = 2,     /* out = (Mhat^+ Mhat + sigma) in           (Eq. "shifted_linear") */
     TMND_OP_QHAT = 3,      /* out = (gamma_5 (x) tau_1) Mhat in         (Eq. "g5tau1-hermiticity") */
-    TMND_OP_S16 = 16       /* flag OR-ed into the op: apply the sloppy operator (FP32 arithmetic,
+    TMND_OP_S16 = 16,      /* flag OR-ed into the op: apply the sloppy operator (FP32 arithmetic,
                               16-bit links and intermediates) to TMND_S16 spinors */
+    TMND_OP_F32 = 32       /* flag OR-ed into the op (TMND_OP_MHAT, _MHAT_DAG, _QHAT2): the FP32
+                              operator (FP32 arithmetic, FP32 links and intermediates, relative
+                              error ~1e-7) on TMND_F32 spinors */
 } tmnd_op;
 
 typedef struct {
@@ -130,7 +133,9 @@ tmnd_status tmnd_spinor_unpack(const tmnd_gauge *g, void *dev_canonical, const v
  * spinors and the operator is the sloppy one (FP32 arithmetic on 16-bit links,
  * intermediates rounded to 16 bits per site); then 1 <= nrhs <= 16 and every
  * stencil launch covers all nrhs right-hand sides (the links are read once per
- * launch and shared through the cache).  `out` and `in` must not overlap.  Uses
+ * launch and shared through the cache).  With TMND_OP_F32 in `op`, in and out
+ * are TMND_F32 spinors and the operator is the FP32 one (one right-hand side
+ * per launch sequence).  `out` and `in` must not overlap.  Uses
  * the handle's workspace (one even-site and one odd-site spinor per right-hand
  * side for TMND_OP_S16, one of each otherwise), growing it on first use.
  * (Sec. 2 even-odd Schur complement; Eq. "g5tau1-hermiticity".) */
@@ -172,6 +177,25 @@ tmnd_status tm_nd_apply(tmnd_gauge *g, void *out, const void *in, int op, double
 tmnd_status tm_nd_apply_noalloc(const tmnd_gauge *g, void *out, const void *in, int op, double sigma,
                                 int nrhs, void *stream);
 
+/* Launch-shape autotuner of the sloppy (16-bit) stencil.  Its kernels are compiled in
+ * TMND_S16_SHAPES launch shapes (threads per block x resident blocks per SM the register
+ * budget is cut for x next-direction prefetch; tmnd_s16_shape_info).  For each lattice
+ * and number of right-hand sides per launch (1..16) the library times every shape once on
+ * the current device -- one 16-bit Qhat^2 + sigma sequence of 4 launches on scratch data,
+ * CUDA events, best of 3 after a warm-up -- and keeps the fastest for the rest of the
+ * process.  This happens on the first 16-bit tm_nd_apply or sloppy solve of that pair
+ * (skipped while the stream is being captured: the default shape 0 is used then), or here,
+ * ahead of time.  Synchronous; allocates its scratch for the call.
+ *   shape_out : receives the chosen shape (may be NULL)
+ *   ms_out    : TMND_S16_SHAPES doubles, each shape's time in ms (may be NULL) */
+#define TMND_S16_SHAPES 4
+tmnd_status tmnd_autotune(tmnd_gauge *g, int nrhs, int *shape_out, double *ms_out, void *stream);
+/* Use shape `shape` for every later 16-bit stencil launch of this process (-1: back to the
+ * tuned choice).  For tests and measurements; results do not depend on the shape. */
+tmnd_status tmnd_s16_force_shape(int shape);
+/* Threads per block, resident blocks per SM, prefetch flag (0/1) of a shape (NULL outputs skipped). */
+tmnd_status tmnd_s16_shape_info(int shape, int *threads, int *blocks_per_sm, int *prefetch);
+
 #define TMND_MAX_SHIFTS 32
 
 typedef struct {
@@ -187,10 +211,15 @@ typedef struct {
                               TMND_S16: mixed precision.  A sloppy multi-shift CG (FP32
                               arithmetic, 16-bit stencil vectors and links, FP32 residual,
                               FP64 dot-product accumulation) down to rho_inner, then FP64
-                              defect correction per shift: FP64 true residual, sloppy CG on
-                              the defect to rho_inner, FP64 update, until every required
-                              shift's FP64 true residual is <= rho. */
-    double rho_inner;      /* TMND_S16: relative tolerance of each sloppy solve (0 = 1e-5) */
+                              defect correction per (RHS, shift) pair: FP64 true residual d;
+                              an inner refinement in FP32 (batched sloppy CGs on the 16-bit
+                              operator, each reducing its residual by the factor still needed
+                              but at most max(rho_inner, 1e-4), each followed by the residual
+                              of the accumulated correction with the FP32 operator, up to 4);
+                              FP64 update; repeated until every required shift's FP64 true
+                              residual is <= rho (one round is the rule). */
+    double rho_inner;      /* TMND_S16: relative tolerance of the first sloppy multi-shift solve
+                              (0 = 1e-5) */
     double *ab_hist;       /* optional host array: receives (alpha_k, beta_k), k = 1.., of the base
                               recursion of the first RHS (the Lanczos coefficients), zero-padded */
     int ab_hist_len;       /* length of ab_hist in doubles (2 per iteration) */
@@ -214,6 +243,8 @@ typedef struct {
     int refine_iters;                      /* TMND_S16: sloppy CG iterations of the corrections (sum) */
     int fp64_applies;                      /* FP64 applications of Qhat^2 + sigma (certification and
                                               defect correction, summed over RHS) */
+    int f32_applies;                       /* TMND_S16: FP32 applications of Qhat^2 + sigma (the inner
+                                              residuals of the defect correction) */
 } tmnd_solve_info;
 
 /* Multi-mass-shift CG (Sec. 1 "standard" solver; Sec. 4.2.2) for
@@ -389,6 +420,7 @@ typedef struct {
     double lebesgue[TMND_MAX_SHIFTS];      /* guess = 1: gamma of those nodes at the shift */
     long long launches;                    /* kernels launched by the multi-shift part and the defect
                                               corrections (the multigrid's own launches not counted) */
+    int f32_applies;                       /* FP32 applications of Qhat^2 + sigma (inner residuals) */
 } tmnd_hybrid_info;
 
 /* Hybrid solve of (Qhat^2 + sigma_i) x_i = b (Sec. 4.3): multi-shift CG for

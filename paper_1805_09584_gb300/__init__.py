@@ -22,6 +22,7 @@ MAX_SHIFTS = 32
 TMND_F64, TMND_F32, TMND_S16 = 0, 1, 2
 OP_MHAT, OP_MHAT_DAG, OP_QHAT2, OP_QHAT = 0, 1, 2, 3
 OP_S16 = 16  # flag: sloppy operator on TMND_S16 spinors
+OP_F32 = 32  # flag: FP32 operator on TMND_F32 spinors
 
 STATUS = {0: "TMND_OK", 1: "TMND_ERR_ARG", 2: "TMND_ERR_CUDA", 3: "TMND_ERR_OOM", 4: "TMND_ERR_NOCONV",
           5: "TMND_ERR_NAN", 6: "TMND_ERR_TIMEOUT", 7: "TMND_ERR_NOTSU3"}
@@ -36,7 +37,10 @@ EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd
            "tmnd_mlp_destroy", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad", "tmnd_mlp_train_step", "tmnd_mlp_predict",
            "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_zolotarev", "tmnd_rational_apply",
            "tmnd_hybrid_cost", "tmnd_fit_cg_time", "tmnd_fit_mg_time", "tmnd_lincomb_c", "tmnd_site_norm_range",
-           "tmnd_lagrange_weights", "tmnd_lagrange_degree", "tmnd_guess_quadratic_form", "tmnd_mg_status")
+           "tmnd_lagrange_weights", "tmnd_lagrange_degree", "tmnd_guess_quadratic_form", "tmnd_mg_status",
+           "tmnd_autotune", "tmnd_s16_force_shape", "tmnd_s16_shape_info")
+S16_SHAPES = 4
+TMND_MAX_BATCH = 16
 NOALLOC_MAX_VH = 32768
 
 
@@ -69,7 +73,7 @@ class HybridInfo(ctypes.Structure):
                 ("fp64_applies", ctypes.c_int), ("refine_iters", ctypes.c_int),
                 ("shift_ms", ctypes.c_double * MAX_SHIFTS), ("mms_ms", ctypes.c_double),
                 ("lag_nodes", ctypes.c_int * MAX_SHIFTS), ("lebesgue", ctypes.c_double * MAX_SHIFTS),
-                ("launches", ctypes.c_longlong)]
+                ("launches", ctypes.c_longlong), ("f32_applies", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
@@ -83,7 +87,8 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("conv_iter", ctypes.c_int * MAX_SHIFTS),
                 ("true_res", ctypes.c_double * MAX_SHIFTS), ("zeta", ctypes.c_double * MAX_SHIFTS),
                 ("hop_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("launches", ctypes.c_longlong),
-                ("refine_rounds", ctypes.c_int), ("refine_iters", ctypes.c_int), ("fp64_applies", ctypes.c_int)]
+                ("refine_rounds", ctypes.c_int), ("refine_iters", ctypes.c_int), ("fp64_applies", ctypes.c_int),
+                ("f32_applies", ctypes.c_int)]
 
 
 _lib = None
@@ -156,6 +161,9 @@ def lib() -> ctypes.CDLL:
         L.tmnd_rational_apply.argtypes = [vp, vp, i, i, d, d, ctypes.POINTER(SolveParams), vp, pd,
                                           ctypes.POINTER(SolveInfo), vp]
         L.tmnd_lagrange_weights.argtypes = [pd, i, d, pd, pd]
+        L.tmnd_autotune.argtypes = [vp, i, ctypes.POINTER(i), pd, vp]
+        L.tmnd_s16_force_shape.argtypes = [i]
+        L.tmnd_s16_shape_info.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
         L.tmnd_lagrange_degree.argtypes = [pd, i, d, d, ctypes.POINTER(i), pd]
         L.tmnd_guess_quadratic_form.argtypes = [pd, pd, i, d, d, pd]
         for name in ("tmnd_mlp_create", "tmnd_mlp_params", "tmnd_mlp_fit_inputs", "tmnd_mlp_loss_grad",
@@ -163,7 +171,7 @@ def lib() -> ctypes.CDLL:
                      "tmnd_fit_cg_time", "tmnd_fit_mg_time",
                      "tmnd_mlp_predict", "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_lincomb_c",
                      "tmnd_site_norm_range", "tmnd_lagrange_weights", "tmnd_lagrange_degree",
-                     "tmnd_guess_quadratic_form"):
+                     "tmnd_guess_quadratic_form", "tmnd_autotune", "tmnd_s16_force_shape", "tmnd_s16_shape_info"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
                      "tmnd_mg_status",
@@ -270,7 +278,7 @@ def mms_cg_solve(h, b, nrhs: int, sigma, x, rho: float = 1e-10, maxiter: int = 1
            "true_res": list(info.true_res[:ns]), "zeta": list(info.zeta[:ns]),
            "hop_ms": info.hop_ms, "update_ms": info.update_ms, "launches": info.launches,
            "refine_rounds": info.refine_rounds, "refine_iters": info.refine_iters,
-           "fp64_applies": info.fp64_applies}
+           "fp64_applies": info.fp64_applies, "f32_applies": info.f32_applies}
     _check(st)
     return out
 
@@ -362,13 +370,32 @@ def tmnd_hybrid_solve(h, mg, b, nrhs: int, sigma, n_mms: int, x, rho: float = 1e
            "fp64_applies": info.fp64_applies, "refine_iters": info.refine_iters,
            "shift_ms": list(info.shift_ms[:ns]), "mms_ms": info.mms_ms,
            "lag_nodes": list(info.lag_nodes[:ns]), "lebesgue": list(info.lebesgue[:ns]),
-           "launches": info.launches}
+           "launches": info.launches, "f32_applies": info.f32_applies}
     _check(st)
     return out
 
 
 def _pd(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def tmnd_autotune(h, nrhs: int, stream=None):
+    """(chosen shape, per-shape ms) of the 16-bit stencil for this lattice and nrhs per launch."""
+    sh = ctypes.c_int()
+    ms = np.zeros(S16_SHAPES)
+    _check(lib().tmnd_autotune(h, int(nrhs), ctypes.byref(sh), _pd(ms), _stream(stream)))
+    return sh.value, ms
+
+
+def tmnd_s16_force_shape(shape: int) -> None:
+    _check(lib().tmnd_s16_force_shape(int(shape)))
+
+
+def tmnd_s16_shape_info(shape: int):
+    """(threads per block, resident blocks per SM, prefetch) of a compiled launch shape."""
+    t, b, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().tmnd_s16_shape_info(int(shape), ctypes.byref(t), ctypes.byref(b), ctypes.byref(p)))
+    return t.value, b.value, bool(p.value)
 
 
 def tmnd_lagrange_weights(nodes, target: float):

@@ -25,8 +25,8 @@
 namespace {
 
 // (B_mu v) for the lower two spins, v[2][3]
-template <int MU>
-__device__ __forceinline__ double2 Bmul(const double2 v[2][3], int s, int c) {
+template <int MU, typename C>
+__device__ __forceinline__ C Bmul(const C v[2][3], int s, int c) {
     if (MU == 0) return cneg(v[s][c]);
     if (MU == 1) return cmulmi(v[1 - s][c]);                 // -i sigma_1
     if (MU == 2) return s == 0 ? cneg(v[1][c]) : v[0][c];    // -i sigma_2 = [[0,-1],[1,0]]
@@ -34,8 +34,8 @@ __device__ __forceinline__ double2 Bmul(const double2 v[2][3], int s, int c) {
 }
 
 // (B_mu^+ v)
-template <int MU>
-__device__ __forceinline__ double2 Bdag(const double2 v[2][3], int s, int c) {
+template <int MU, typename C>
+__device__ __forceinline__ C Bdag(const C v[2][3], int s, int c) {
     if (MU == 0) return cneg(v[s][c]);
     if (MU == 1) return cmuli(v[1 - s][c]);                  // i sigma_1
     if (MU == 2) return s == 0 ? v[1][c] : cneg(v[0][c]);    // i sigma_2 = [[0,1],[-1,0]]
@@ -45,11 +45,10 @@ __device__ __forceinline__ double2 Bdag(const double2 v[2][3], int s, int c) {
 // Accumulate the hop from neighbour hn in direction MU, DIR (+1 forward
 // with U_mu(x), -1 backward with U_mu(x-mu)^+) into acc[flavour][spin][colour].
 // G5IN: the input field is gamma_5 psi (lower spins negated).
-template <int MU, int DIR, bool G5IN, bool FIRST = false>
-__device__ __forceinline__ void hop_dir(const double2 *__restrict__ in, int Vh, int hn,
-                                        const double2 *__restrict__ U, int hl,
-                                        unsigned long long smask, double2 acc[2][4][3]) {
-    double2 u[3][3];
+template <typename C, int MU, int DIR, bool G5IN, bool FIRST = false>
+__device__ __forceinline__ void hop_dir(const C *__restrict__ in, int Vh, int hn, const C *__restrict__ U, int hl,
+                                        unsigned long long smask, C acc[2][4][3]) {
+    C u[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -58,7 +57,7 @@ __device__ __forceinline__ void hop_dir(const double2 *__restrict__ in, int Vh, 
     constexpr bool plus = (DIR < 0) != G5IN;
 #pragma unroll
     for (int f = 0; f < 2; f++) {
-        double2 up[2][3], lo[2][3];
+        C up[2][3], lo[2][3];
 #pragma unroll
         for (int s = 0; s < 2; s++)
 #pragma unroll
@@ -66,25 +65,25 @@ __device__ __forceinline__ void hop_dir(const double2 *__restrict__ in, int Vh, 
                 up[s][c] = __ldg(&in[(f * 12 + s * 3 + c) * Vh + hn]);
                 lo[s][c] = __ldg(&in[(f * 12 + (s + 2) * 3 + c) * Vh + hn]);
             }
-        double2 chi[2][3];
+        C chi[2][3];
 #pragma unroll
         for (int s = 0; s < 2; s++)
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                double2 b = Bmul<MU>(lo, s, c);
+                C b = Bmul<MU>(lo, s, c);
                 chi[s][c] = cflip(plus ? cadd(up[s][c], b) : csub(up[s][c], b), smask);
             }
-        double2 v[2][3];
+        C v[2][3];
 #pragma unroll
         for (int s = 0; s < 2; s++)
 #pragma unroll
             for (int i = 0; i < 3; i++) {
                 if (DIR > 0) {
-                    double2 t = cmul(u[i][0], chi[s][0]);
+                    C t = cmul(u[i][0], chi[s][0]);
                     t = cfma(u[i][1], chi[s][1], t);
                     v[s][i] = cfma(u[i][2], chi[s][2], t);
                 } else {
-                    double2 t = cmul_conj(u[0][i], chi[s][0]);
+                    C t = cmul_conj(u[0][i], chi[s][0]);
                     t = cfma_conj(u[1][i], chi[s][1], t);
                     v[s][i] = cfma_conj(u[2][i], chi[s][2], t);
                 }
@@ -93,7 +92,7 @@ __device__ __forceinline__ void hop_dir(const double2 *__restrict__ in, int Vh, 
         for (int s = 0; s < 2; s++)
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                double2 b = Bdag<MU>(v, s, c);
+                C b = Bdag<MU>(v, s, c);
                 if (FIRST) {  // the first direction initialises the accumulator
                     acc[f][s][c] = v[s][c];
                     acc[f][s + 2][c] = (DIR > 0) ? cneg(b) : b;
@@ -106,9 +105,9 @@ __device__ __forceinline__ void hop_dir(const double2 *__restrict__ in, int Vh, 
 }
 
 // H applied at output site of parity P, half-index h; in = field on parity 1-P.
-template <int P, bool G5IN>
-__device__ __forceinline__ void hop_all(const Geom &g, const double2 *__restrict__ links,
-                                        const double2 *__restrict__ in, int h, double2 acc[2][4][3]) {
+template <typename C, int P, bool G5IN>
+__device__ __forceinline__ void hop_all(const Geom &g, const C *__restrict__ links, const C *__restrict__ in, int h,
+                                        C acc[2][4][3]) {
     const int Vh = g.Vh;
     int zh = h % g.Zh;
     int r = h / g.Zh;
@@ -117,8 +116,8 @@ __device__ __forceinline__ void hop_all(const Geom &g, const double2 *__restrict
     int x = r % g.X;
     int t = r / g.X;
     int z = 2 * zh + ((P + t + x + y) & 1);
-    const double2 *Lp = links + (size_t)P * 4 * 9 * Vh;         // links based at parity P sites
-    const double2 *Lq = links + (size_t)(1 - P) * 4 * 9 * Vh;   // links based at parity 1-P sites
+    const C *Lp = links + (size_t)P * 4 * 9 * Vh;         // links based at parity P sites
+    const C *Lq = links + (size_t)(1 - P) * 4 * 9 * Vh;   // links based at parity 1-P sites
     const unsigned long long NEG = 0x8000000000000000ull;
     auto idx = [&](int tt, int xx, int yy, int zz) { return ((tt * g.X + xx) * g.Y + yy) * g.Zh + (zz >> 1); };
 
@@ -129,53 +128,54 @@ __device__ __forceinline__ void hop_all(const Geom &g, const double2 *__restrict
         unsigned long long mf = (g.apbc && t + 1 == g.T) ? NEG : 0ull;
         unsigned long long mb = (g.apbc && t == 0) ? NEG : 0ull;
         int hf = idx(tf, x, y, z), hb = idx(tb, x, y, z);
-        hop_dir<0, +1, G5IN, true>(in, Vh, hf, Lp + 0 * 9 * (size_t)Vh, h, mf, acc);
-        hop_dir<0, -1, G5IN>(in, Vh, hb, Lq + 0 * 9 * (size_t)Vh, hb, mb, acc);
+        hop_dir<C, 0, +1, G5IN, true>(in, Vh, hf, Lp + 0 * 9 * (size_t)Vh, h, mf, acc);
+        hop_dir<C, 0, -1, G5IN>(in, Vh, hb, Lq + 0 * 9 * (size_t)Vh, hb, mb, acc);
     }
     {
         int xf = (x + 1 == g.X) ? 0 : x + 1;
         int xb = (x == 0) ? g.X - 1 : x - 1;
         int hf = idx(t, xf, y, z), hb = idx(t, xb, y, z);
-        hop_dir<1, +1, G5IN>(in, Vh, hf, Lp + 1 * 9 * (size_t)Vh, h, 0ull, acc);
-        hop_dir<1, -1, G5IN>(in, Vh, hb, Lq + 1 * 9 * (size_t)Vh, hb, 0ull, acc);
+        hop_dir<C, 1, +1, G5IN>(in, Vh, hf, Lp + 1 * 9 * (size_t)Vh, h, 0ull, acc);
+        hop_dir<C, 1, -1, G5IN>(in, Vh, hb, Lq + 1 * 9 * (size_t)Vh, hb, 0ull, acc);
     }
     {
         int yf = (y + 1 == g.Y) ? 0 : y + 1;
         int yb = (y == 0) ? g.Y - 1 : y - 1;
         int hf = idx(t, x, yf, z), hb = idx(t, x, yb, z);
-        hop_dir<2, +1, G5IN>(in, Vh, hf, Lp + 2 * 9 * (size_t)Vh, h, 0ull, acc);
-        hop_dir<2, -1, G5IN>(in, Vh, hb, Lq + 2 * 9 * (size_t)Vh, hb, 0ull, acc);
+        hop_dir<C, 2, +1, G5IN>(in, Vh, hf, Lp + 2 * 9 * (size_t)Vh, h, 0ull, acc);
+        hop_dir<C, 2, -1, G5IN>(in, Vh, hb, Lq + 2 * 9 * (size_t)Vh, hb, 0ull, acc);
     }
     {
         int zf = (z + 1 == g.Z) ? 0 : z + 1;
         int zb = (z == 0) ? g.Z - 1 : z - 1;
         int hf = idx(t, x, y, zf), hb = idx(t, x, y, zb);
-        hop_dir<3, +1, G5IN>(in, Vh, hf, Lp + 3 * 9 * (size_t)Vh, h, 0ull, acc);
-        hop_dir<3, -1, G5IN>(in, Vh, hb, Lq + 3 * 9 * (size_t)Vh, hb, 0ull, acc);
+        hop_dir<C, 3, +1, G5IN>(in, Vh, hf, Lp + 3 * 9 * (size_t)Vh, h, 0ull, acc);
+        hop_dir<C, 3, -1, G5IN>(in, Vh, hb, Lq + 3 * 9 * (size_t)Vh, hb, 0ull, acc);
     }
 }
 
 // even sites: t_e = kappa^2 A^-1 H psi  (DAG: kappa^2 A(-mu)^-1 H gamma_5 psi)
-template <bool DAG>
-__global__ void __launch_bounds__(HOP_THREADS) k_hop_even(Geom g, SiteTerm st, const double2 *__restrict__ links,
-                                                         const double2 *__restrict__ psi, double2 *__restrict__ out,
+template <typename C, bool DAG>
+__global__ void __launch_bounds__(HOP_THREADS) k_hop_even(Geom g, SiteTerm st, const C *__restrict__ links,
+                                                         const C *__restrict__ psi, C *__restrict__ out,
                                                          const int *__restrict__ done, int chunk) {
+    using R = decltype(C::x);
     if (done && *done) return;
     const int h_end = min(g.Vh, (blockIdx.x + 1) * chunk);
     for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) {
-    double2 acc[2][4][3];
-    hop_all<0, DAG>(g, links, psi, h, acc);
-    const double a = st.kappa2 * st.inv_det;
-    const double e = a * st.kpp;
+    C acc[2][4][3];
+    hop_all<C, 0, DAG>(g, links, psi, h, acc);
+    const R a = (R)(st.kappa2 * st.inv_det);
+    const R e = (R)(st.kappa2 * st.inv_det * st.kpp);
     const int Vh = g.Vh;
 #pragma unroll
     for (int s = 0; s < 4; s++) {
         // A^-1 = [[1 - i kp g, kpp],[kpp, 1 + i kp g]] / det, g = gamma_5 eigenvalue
-        const double b = a * (DAG ? -st.kp : st.kp) * (s < 2 ? 1.0 : -1.0);
+        const R b = a * (R)(DAG ? -st.kp : st.kp) * (s < 2 ? (R)1 : (R)-1);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            double2 p0 = acc[0][s][c], p1 = acc[1][s][c];
-            double2 o0, o1;
+            C p0 = acc[0][s][c], p1 = acc[1][s][c];
+            C o0, o1;
             o0.x = fma(a, p0.x, fma(b, p0.y, e * p1.x));
             o0.y = fma(a, p0.y, fma(-b, p0.x, e * p1.y));
             o1.x = fma(a, p1.x, fma(-b, p1.y, e * p0.x));
@@ -188,10 +188,11 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop_even(Geom g, SiteTerm st, c
 }
 
 // odd sites: y = A psi - H t  (DAG: A(-mu) psi - gamma_5 H t), then the epilogue.
-template <bool DAG, int EPI>
-__global__ void __launch_bounds__(HOP_THREADS) k_hop_odd(Geom g, SiteTerm st, const double2 *__restrict__ links,
-                                                        const double2 *__restrict__ psi, const double2 *__restrict__ te,
-                                                        double2 *__restrict__ out, HopEpiArgs ea, int chunk) {
+template <typename C, bool DAG, int EPI>
+__global__ void __launch_bounds__(HOP_THREADS) k_hop_odd(Geom g, SiteTerm st, const C *__restrict__ links,
+                                                        const C *__restrict__ psi, const C *__restrict__ te,
+                                                        C *__restrict__ out, HopEpiT<C> ea, int chunk) {
+    using R = decltype(C::x);
     __shared__ double red[40];
     if (ea.done && *ea.done) return;
     const int Vh = g.Vh;
@@ -205,49 +206,58 @@ __global__ void __launch_bounds__(HOP_THREADS) k_hop_odd(Geom g, SiteTerm st, co
     double n1 = 0.0, n2 = 0.0;
     const int h_end = min(Vh, (int)(blockIdx.x + 1) * chunk);
     for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) {
-        double2 acc[2][4][3];
-        hop_all<1, false>(g, links, te, h, acc);
-        const double kp = DAG ? -st.kp : st.kp;
+        C acc[2][4][3];
+        hop_all<C, 1, false>(g, links, te, h, acc);
+        const R kp = (R)(DAG ? -st.kp : st.kp);
+        const R kpp = (R)st.kpp;
+        const R al = (R)alpha, sg = (R)ea.sigma;
 #pragma unroll
         for (int s = 0; s < 4; s++) {
-            const double b = kp * (s < 2 ? 1.0 : -1.0);
+            const R b = kp * (s < 2 ? (R)1 : (R)-1);
             // DAG: gamma_5 on the hop term flips the sign of the lower spins
             const bool hopneg = DAG && s >= 2;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                double2 p0 = __ldg(&psi[(0 * 12 + s * 3 + c) * Vh + h]);
-                double2 p1 = __ldg(&psi[(1 * 12 + s * 3 + c) * Vh + h]);
-                double2 h0 = acc[0][s][c], h1 = acc[1][s][c];
+                C p0 = __ldg(&psi[(0 * 12 + s * 3 + c) * Vh + h]);
+                C p1 = __ldg(&psi[(1 * 12 + s * 3 + c) * Vh + h]);
+                C h0 = acc[0][s][c], h1 = acc[1][s][c];
                 if (hopneg) { h0 = cneg(h0); h1 = cneg(h1); }
                 // A = [[1 + i kp g, -kpp],[-kpp, 1 - i kp g]]
-                double2 y0, y1;
-                y0.x = fma(-b, p0.y, fma(-st.kpp, p1.x, p0.x - h0.x));
-                y0.y = fma(b, p0.x, fma(-st.kpp, p1.y, p0.y - h0.y));
-                y1.x = fma(b, p1.y, fma(-st.kpp, p0.x, p1.x - h1.x));
-                y1.y = fma(-b, p1.x, fma(-st.kpp, p0.y, p1.y - h1.y));
+                C y0, y1;
+                y0.x = fma(-b, p0.y, fma(-kpp, p1.x, p0.x - h0.x));
+                y0.y = fma(b, p0.x, fma(-kpp, p1.y, p0.y - h0.y));
+                y1.x = fma(b, p1.y, fma(-kpp, p0.x, p1.x - h1.x));
+                y1.y = fma(-b, p1.x, fma(-kpp, p0.y, p1.y - h1.y));
                 const int i0 = (0 * 12 + s * 3 + c) * Vh + h, i1 = (1 * 12 + s * 3 + c) * Vh + h;
                 if (EPI == EPI_STORE || EPI == EPI_STORE_NORMS) {
                     out[i0] = y0;
                     out[i1] = y1;
                     if (EPI == EPI_STORE_NORMS) {
-                        n1 = fma(y0.x, y0.x, fma(y0.y, y0.y, fma(y1.x, y1.x, fma(y1.y, y1.y, n1))));
-                        n2 = fma(p0.x, p0.x, fma(p0.y, p0.y, fma(p1.x, p1.x, fma(p1.y, p1.y, n2))));
+                        n1 = fma((double)y0.x, (double)y0.x, fma((double)y0.y, (double)y0.y,
+                                 fma((double)y1.x, (double)y1.x, fma((double)y1.y, (double)y1.y, n1))));
+                        n2 = fma((double)p0.x, (double)p0.x, fma((double)p0.y, (double)p0.y,
+                                 fma((double)p1.x, (double)p1.x, fma((double)p1.y, (double)p1.y, n2))));
                     }
                 } else if (EPI == EPI_SHIFT) {
-                    double2 a0 = __ldg(&ea.aux[i0]), a1 = __ldg(&ea.aux[i1]);
-                    out[i0] = make_double2(fma(ea.sigma, a0.x, y0.x), fma(ea.sigma, a0.y, y0.y));
-                    out[i1] = make_double2(fma(ea.sigma, a1.x, y1.x), fma(ea.sigma, a1.y, y1.y));
+                    C a0 = __ldg(&ea.aux[i0]), a1 = __ldg(&ea.aux[i1]);
+                    C o0, o1;
+                    o0.x = fma(sg, a0.x, y0.x); o0.y = fma(sg, a0.y, y0.y);
+                    o1.x = fma(sg, a1.x, y1.x); o1.y = fma(sg, a1.y, y1.y);
+                    out[i0] = o0;
+                    out[i1] = o1;
                 } else {  // EPI_MMS_R
-                    double2 a0 = __ldg(&ea.aux[i0]), a1 = __ldg(&ea.aux[i1]);
-                    double2 w0 = make_double2(fma(ea.sigma, a0.x, y0.x), fma(ea.sigma, a0.y, y0.y));
-                    double2 w1 = make_double2(fma(ea.sigma, a1.x, y1.x), fma(ea.sigma, a1.y, y1.y));
-                    const double2 *rin = ea.r_in ? ea.r_in : ea.r;
-                    double2 r0 = rin[i0], r1 = rin[i1];
-                    r0.x = fma(-alpha, w0.x, r0.x); r0.y = fma(-alpha, w0.y, r0.y);
-                    r1.x = fma(-alpha, w1.x, r1.x); r1.y = fma(-alpha, w1.y, r1.y);
+                    C a0 = __ldg(&ea.aux[i0]), a1 = __ldg(&ea.aux[i1]);
+                    C w0, w1;
+                    w0.x = fma(sg, a0.x, y0.x); w0.y = fma(sg, a0.y, y0.y);
+                    w1.x = fma(sg, a1.x, y1.x); w1.y = fma(sg, a1.y, y1.y);
+                    const C *rin = ea.r_in ? ea.r_in : ea.r;
+                    C r0 = rin[i0], r1 = rin[i1];
+                    r0.x = fma(-al, w0.x, r0.x); r0.y = fma(-al, w0.y, r0.y);
+                    r1.x = fma(-al, w1.x, r1.x); r1.y = fma(-al, w1.y, r1.y);
                     ea.r[i0] = r0;
                     ea.r[i1] = r1;
-                    n1 = fma(r0.x, r0.x, fma(r0.y, r0.y, fma(r1.x, r1.x, fma(r1.y, r1.y, n1))));
+                    n1 = fma((double)r0.x, (double)r0.x, fma((double)r0.y, (double)r0.y,
+                             fma((double)r1.x, (double)r1.x, fma((double)r1.y, (double)r1.y, n1))));
                 }
             }
         }
@@ -279,8 +289,8 @@ int hop_blocks(const Geom &g) {
     if (!cached[dev]) {
         int sms = 0, per_sm = 0, per_sm2 = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hop_odd<true, EPI_MMS_R>, HOP_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_hop_even<true>, HOP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hop_odd<double2, true, EPI_MMS_R>, HOP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_hop_even<double2, true>, HOP_THREADS, 0);
         per_sm = per_sm < per_sm2 ? per_sm : per_sm2;
         if (sms <= 0) sms = 152;
         if (per_sm <= 0) per_sm = 1;
@@ -300,9 +310,9 @@ void launch_hop_even_f64(const Geom &g, const SiteTerm &st, const double2 *links
     dim3 grid(hop_blocks(g)), block(HOP_THREADS);
     const int chunk = hop_chunk(g);
     if (dag)
-        k_hop_even<true><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, done, chunk);
+        k_hop_even<double2, true><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, done, chunk);
     else
-        k_hop_even<false><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, done, chunk);
+        k_hop_even<double2, false><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, done, chunk);
 }
 
 void launch_hop_odd_f64(const Geom &g, const SiteTerm &st, const double2 *links, const double2 *psi_o,
@@ -310,7 +320,7 @@ void launch_hop_odd_f64(const Geom &g, const SiteTerm &st, const double2 *links,
                         cudaStream_t s) {
     dim3 grid(hop_blocks(g)), block(HOP_THREADS);
     const int chunk = hop_chunk(g);
-#define TMND_ODD(D, E) k_hop_odd<D, E><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, y_o, ea, chunk)
+#define TMND_ODD(D, E) k_hop_odd<double2, D, E><<<grid, block, 0, s>>>(g, st, links, psi_o, t_e, y_o, ea, chunk)
     if (!dag) {
         switch (epi) {
             case EPI_STORE: TMND_ODD(false, EPI_STORE); break;
@@ -327,4 +337,57 @@ void launch_hop_odd_f64(const Geom &g, const SiteTerm &st, const double2 *links,
         }
     }
 #undef TMND_ODD
+}
+
+// ------------------------------------------------------------- FP32 instantiation
+// The same stencil on FP32 planes with 18-real FP32 links: HBM-bound (4416 bytes per odd
+// site per Qhat^2), accurate to ~1e-7; the inner residuals of the defect correction.
+int hop_blocks_f32(const Geom &g) {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int sms = 0, per_sm = 0, per_sm2 = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hop_odd<float2, true, EPI_MMS_R>, HOP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_hop_even<float2, true>, HOP_THREADS, 0);
+        per_sm = per_sm < per_sm2 ? per_sm : per_sm2;
+        if (sms <= 0) sms = 152;
+        if (per_sm <= 0) per_sm = 1;
+        cached[dev] = sms * per_sm;
+    }
+    int want = (g.Vh + HOP_THREADS - 1) / HOP_THREADS;
+    return want < cached[dev] ? want : cached[dev];
+}
+
+void launch_hop_even_f32(const Geom &g, const SiteTerm &st, const float2 *links, const float2 *psi_o, float2 *t_e,
+                         bool dag, const int *done, cudaStream_t s) {
+    const int nb = hop_blocks_f32(g), chunk = (g.Vh + nb - 1) / nb;
+    if (dag)
+        k_hop_even<float2, true><<<nb, HOP_THREADS, 0, s>>>(g, st, links, psi_o, t_e, done, chunk);
+    else
+        k_hop_even<float2, false><<<nb, HOP_THREADS, 0, s>>>(g, st, links, psi_o, t_e, done, chunk);
+}
+
+void launch_hop_odd_f32(const Geom &g, const SiteTerm &st, const float2 *links, const float2 *psi_o,
+                        const float2 *t_e, float2 *y_o, bool dag, HopEpi epi, const HopEpiArgsF &ea, cudaStream_t s) {
+    const int nb = hop_blocks_f32(g), chunk = (g.Vh + nb - 1) / nb;
+#define TMND_ODD32(D, E) k_hop_odd<float2, D, E><<<nb, HOP_THREADS, 0, s>>>(g, st, links, psi_o, t_e, y_o, ea, chunk)
+    if (!dag) {
+        switch (epi) {
+            case EPI_STORE: TMND_ODD32(false, EPI_STORE); break;
+            case EPI_STORE_NORMS: TMND_ODD32(false, EPI_STORE_NORMS); break;
+            case EPI_SHIFT: TMND_ODD32(false, EPI_SHIFT); break;
+            case EPI_MMS_R: TMND_ODD32(false, EPI_MMS_R); break;
+        }
+    } else {
+        switch (epi) {
+            case EPI_STORE: TMND_ODD32(true, EPI_STORE); break;
+            case EPI_STORE_NORMS: TMND_ODD32(true, EPI_STORE_NORMS); break;
+            case EPI_SHIFT: TMND_ODD32(true, EPI_SHIFT); break;
+            case EPI_MMS_R: TMND_ODD32(true, EPI_MMS_R); break;
+        }
+    }
+#undef TMND_ODD32
 }

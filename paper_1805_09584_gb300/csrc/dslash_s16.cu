@@ -20,14 +20,20 @@
 //   * PF: the words of the next direction are loaded before the current one is
 //     processed (more memory requests in flight per warp).
 //   * Links are read once per launch, so their loads bypass L1.
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "s16_hop.cuh"
 
 namespace {
 
-constexpr int S16_THREADS = 128;
-// resident blocks per SM the register budget is cut for (168 registers; 4 blocks
-// at 128 registers spill and ran slower)
-constexpr int S16_MINB = 3;
+// Launch shapes the kernels are compiled in: threads per block, resident blocks per
+// SM the register budget is cut for, next-direction prefetch.  The autotuner below
+// times each on the GPU per (lattice, right-hand sides per launch) and keeps the
+// fastest; shape 0 is the default (168 registers, 12 warps per SM; 4 blocks of 128
+// at 128 registers spill and ran slower).
+#define TMND_S16_SHAPE_LIST(X) X(0, 128, 3, true) X(1, 128, 3, false) X(2, 64, 6, true) X(3, 256, 1, true)
 
 __device__ __forceinline__ int2 ld_link(const int2 *p) {
     int2 r;
@@ -109,10 +115,10 @@ __device__ __forceinline__ void hop_all(const Geom &g, const int2 *__restrict__ 
     hop_seq<P, 0, G5IN, PF>(links, q, nrm, g.Vh, n, r0, acc);
 }
 
-template <bool DAG, bool PF>
-__global__ void __launch_bounds__(S16_THREADS, S16_MINB) k_hop_even_s16(Geom g, SiteTermF st, const int2 *__restrict__ links,
-                                                             S16In in, S16Out out, const int *__restrict__ done,
-                                                             int chunk, S16Batch bt) {
+template <bool DAG, bool PF, int NT, int MB>
+__global__ void __launch_bounds__(NT, MB) k_hop_even_s16(Geom g, SiteTermF st, const int2 *__restrict__ links,
+                                                         S16In in, S16Out out, const int *__restrict__ done,
+                                                         int chunk, S16Batch bt) {
     if (done && *done) return;
     const int h_end = min(g.Vh, (int)(blockIdx.x + 1) * chunk);
     for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) {
@@ -131,10 +137,10 @@ __global__ void __launch_bounds__(S16_THREADS, S16_MINB) k_hop_even_s16(Geom g, 
 
 // Per-right-hand-side block partials: each thread keeps its running sums in its own
 // slots of dynamic shared memory, part[(q * nrhs + k) * blockDim + tid], q = 0, 1.
-template <bool DAG, int EPI, bool PF>
-__global__ void __launch_bounds__(S16_THREADS, S16_MINB) k_hop_odd_s16(Geom g, SiteTermF st, const int2 *__restrict__ links,
-                                                            S16In psi_all, S16In te_all, S16Out out_all, S16EpiArgs ea,
-                                                            int chunk, S16Batch bt) {
+template <bool DAG, int EPI, bool PF, int NT, int MB>
+__global__ void __launch_bounds__(NT, MB) k_hop_odd_s16(Geom g, SiteTermF st, const int2 *__restrict__ links,
+                                                        S16In psi_all, S16In te_all, S16Out out_all, S16EpiArgs ea,
+                                                        int chunk, S16Batch bt) {
     __shared__ double red[40];
     __shared__ float alpha_s[TMND_MAX_BATCH];
     extern __shared__ double part[];
@@ -194,48 +200,141 @@ __global__ void __launch_bounds__(S16_THREADS, S16_MINB) k_hop_odd_s16(Geom g, S
     }
 }
 
-constexpr bool PFD = true;  // prefetch the next direction (0.106 vs 0.113 ms for Mhat at 24^3x48)
+struct ShapeDesc {
+    int threads, minb, pf;
+};
+constexpr ShapeDesc kShapes[] = {
+#define TMND_S16_DESC(I, T, B, P) {T, B, P},
+    TMND_S16_SHAPE_LIST(TMND_S16_DESC)
+#undef TMND_S16_DESC
+};
+constexpr int NSHAPES = sizeof(kShapes) / sizeof(kShapes[0]);
+static_assert(NSHAPES == TMND_S16_SHAPES, "shape count of include/tmnd.h");
 
-int s16_blocks_cached[64] = {0};
+// resident blocks per SM of each shape, per device (the smaller of the even and odd kernels')
+int g_per_sm[64][NSHAPES] = {};
 
-}  // namespace
+template <bool DAG, int EPI, bool PF, int NT, int MB>
+void odd_smem_attr() {
+    static bool done = false;  // dynamic shared memory above 48 KB needs an opt-in (256 threads, 16 RHS)
+    if (!done) {
+        cudaFuncSetAttribute(k_hop_odd_s16<DAG, EPI, PF, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * 2 * TMND_MAX_BATCH * NT));
+        done = true;
+    }
+}
 
-// blocks of the stencil launches: one per resident slot (3 per SM at 168 registers), at most one site per thread
-int hop_blocks_s16(const Geom &g) {
+template <bool PF, int NT, int MB>
+int per_sm_of(int dev) {
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_hop_odd_s16<true, EPI_MMS_R, PF, NT, MB>, NT,
+                                                  sizeof(double) * 2 * NT);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hop_even_s16<true, PF, NT, MB>, NT, 0);
+    a = a < b ? a : b;
+    (void)dev;
+    return a > 0 ? a : 1;
+}
+
+int per_sm(int shape) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    if (!s16_blocks_cached[dev]) {
-        int sms = 0, a = 0, b = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_hop_odd_s16<true, EPI_MMS_R, PFD>, S16_THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hop_even_s16<true, PFD>, S16_THREADS, 0);
-        a = a < b ? a : b;
-        if (sms <= 0) sms = 152;
-        if (a <= 0) a = 1;
-        s16_blocks_cached[dev] = sms * a;
+    if (!g_per_sm[dev][shape]) {
+        switch (shape) {
+#define TMND_S16_OCC(I, T, B, P) \
+    case I: g_per_sm[dev][I] = per_sm_of<P, T, B>(dev); break;
+            TMND_S16_SHAPE_LIST(TMND_S16_OCC)
+#undef TMND_S16_OCC
+        }
     }
-    int want = (g.Vh + S16_THREADS - 1) / S16_THREADS;
-    return want < s16_blocks_cached[dev] ? want : s16_blocks_cached[dev];
+    return g_per_sm[dev][shape];
+}
+
+int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = sms > 0 ? sms : 152;
+    }
+    return cached[dev];
+}
+
+// ---------------------------------------------------------------- autotuner state
+// (device, T, X, Y, Z, right-hand sides per launch) -> chosen shape
+std::mutex g_tune_mutex;
+std::map<std::array<int, 6>, int> g_tuned;
+std::map<std::array<int, 6>, std::array<float, NSHAPES>> g_tune_ms;
+int g_forced = -1;
+
+std::array<int, 6> tune_key(const Geom &g, int nrhs) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return {dev, g.T, g.X, g.Y, g.Z, nrhs};
+}
+
+}  // namespace
+
+// blocks of a stencil launch in this shape: one per resident slot on every SM (persistent
+// grid), at most one site per thread
+int hop_blocks_s16(const Geom &g, int shape) {
+    if (shape < 0 || shape >= NSHAPES) shape = 0;
+    const int nt = kShapes[shape].threads;
+    const int cap = sm_count() * per_sm(shape);
+    const int want = (g.Vh + nt - 1) / nt;
+    return want < cap ? want : cap;
+}
+
+int hop_blocks_s16_max(const Geom &g) {
+    int m = 0;
+    for (int s = 0; s < NSHAPES; s++) {
+        const int b = hop_blocks_s16(g, s);
+        m = b > m ? b : m;
+    }
+    return m;
+}
+
+// the shape for this lattice and number of right-hand sides: forced, else tuned, else 0
+int s16_shape(const Geom &g, int nrhs) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    if (g_forced >= 0) return g_forced;
+    auto it = g_tuned.find(tune_key(g, nrhs));
+    return it == g_tuned.end() ? 0 : it->second;
 }
 
 void launch_hop_even_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In in, S16Out out, bool dag,
                          const int *done, cudaStream_t s, const S16Batch &bt) {
-    const int nb = hop_blocks_s16(g);
+    const int shape = bt.shape >= 0 ? bt.shape : s16_shape(g, bt.nrhs);
+    const int nb = hop_blocks_s16(g, shape);
     const int chunk = (g.Vh + nb - 1) / nb;
-    if (dag)
-        k_hop_even_s16<true, PFD><<<nb, S16_THREADS, 0, s>>>(g, st, links, in, out, done, chunk, bt);
-    else
-        k_hop_even_s16<false, PFD><<<nb, S16_THREADS, 0, s>>>(g, st, links, in, out, done, chunk, bt);
+    switch (shape) {
+#define TMND_S16_EVEN(I, T, B, P)                                                                              \
+    case I:                                                                                                    \
+        if (dag)                                                                                               \
+            k_hop_even_s16<true, P, T, B><<<nb, T, 0, s>>>(g, st, links, in, out, done, chunk, bt);            \
+        else                                                                                                   \
+            k_hop_even_s16<false, P, T, B><<<nb, T, 0, s>>>(g, st, links, in, out, done, chunk, bt);           \
+        break;
+        TMND_S16_SHAPE_LIST(TMND_S16_EVEN)
+#undef TMND_S16_EVEN
+        default: break;
+    }
 }
 
-void launch_hop_odd_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In psi, S16In te, S16Out out,
-                        bool dag, HopEpi epi, const S16EpiArgs &ea, cudaStream_t s, const S16Batch &bt) {
-    const int nb = hop_blocks_s16(g);
+namespace {
+template <bool PF, int NT, int MB>
+void launch_odd_shape(const Geom &g, const SiteTermF &st, const int2 *links, S16In psi, S16In te, S16Out out,
+                      bool dag, HopEpi epi, const S16EpiArgs &ea, cudaStream_t s, const S16Batch &bt, int nb) {
     const int chunk = (g.Vh + nb - 1) / nb;
-    const size_t smem = sizeof(double) * 2 * bt.nrhs * S16_THREADS;
-#define TMND_ODD16(D, E) \
-    k_hop_odd_s16<D, E, PFD><<<nb, S16_THREADS, smem, s>>>(g, st, links, psi, te, out, ea, chunk, bt)
+    const size_t smem = sizeof(double) * 2 * bt.nrhs * NT;
+#define TMND_ODD16(D, E)                                                                              \
+    do {                                                                                              \
+        odd_smem_attr<D, E, PF, NT, MB>();                                                            \
+        k_hop_odd_s16<D, E, PF, NT, MB><<<nb, NT, smem, s>>>(g, st, links, psi, te, out, ea, chunk, bt); \
+    } while (0)
     if (!dag) {
         switch (epi) {
             case EPI_STORE: TMND_ODD16(false, EPI_STORE); break;
@@ -252,4 +351,131 @@ void launch_hop_odd_s16(const Geom &g, const SiteTermF &st, const int2 *links, S
         }
     }
 #undef TMND_ODD16
+}
+}  // namespace
+
+void launch_hop_odd_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In psi, S16In te, S16Out out,
+                        bool dag, HopEpi epi, const S16EpiArgs &ea, cudaStream_t s, const S16Batch &bt) {
+    const int shape = bt.shape >= 0 ? bt.shape : s16_shape(g, bt.nrhs);
+    const int nb = hop_blocks_s16(g, shape);
+    switch (shape) {
+#define TMND_S16_ODD(I, T, B, P) \
+    case I: launch_odd_shape<P, T, B>(g, st, links, psi, te, out, dag, epi, ea, s, bt, nb); break;
+        TMND_S16_SHAPE_LIST(TMND_S16_ODD)
+#undef TMND_S16_ODD
+        default: break;
+    }
+}
+
+// Autotuner: time one 16-bit Qhat^2 + sigma sequence (the 4 launches a solver iteration
+// makes, with the odd kernels' norm partials) of nrhs right-hand sides in every shape on
+// scratch data, CUDA events, best of 3 after one warm-up; keep the fastest shape for this
+// (device, lattice, nrhs).  Skipped (shape 0 stays) while the stream is being captured.
+tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out, float *ms_out) {
+    TMND_ARG_CHECK(nrhs >= 1 && nrhs <= TMND_MAX_BATCH, "tmnd_autotune: nrhs = %d not in [1, %d]", nrhs,
+                   TMND_MAX_BATCH);
+    const auto key = tune_key(g->geom, nrhs);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            if (shape_out) *shape_out = it->second;
+            if (ms_out) {
+                const auto &t = g_tune_ms[key];
+                for (int i = 0; i < NSHAPES; i++) ms_out[i] = t[i];
+            }
+            return TMND_OK;
+        }
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        if (shape_out) *shape_out = 0;
+        return TMND_OK;
+    }
+    const int Vh = g->geom.Vh;
+    const size_t sb = spinor_bytes_prec(Vh, TMND_S16);
+    const size_t part_b = sizeof(double) * 2 * (size_t)nrhs * hop_blocks_s16_max(g->geom);
+    char *buf = nullptr;
+    TMND_CUDA_TRY(cudaMalloc(&buf, 3 * (size_t)nrhs * sb + part_b + 256));
+    // biased 16-bit words of 0x4000 and unit scales: finite, data-independent timing
+    cudaMemsetAsync(buf, 0x40, 3 * (size_t)nrhs * sb, s);
+    const S16In in = s16_in(buf, Vh);
+    const S16Out te = s16_out(buf + (size_t)nrhs * sb, Vh), y = s16_out(buf + 2 * (size_t)nrhs * sb, Vh);
+    const S16In tei{te.q, te.nrm}, yi{y.q, y.nrm};
+    double *part = (double *)(buf + 3 * (size_t)nrhs * sb);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::array<float, NSHAPES> best;
+    int choice = 0;
+    cudaError_t err = cudaSuccess;
+    for (int sh = 0; sh < NSHAPES && err == cudaSuccess; sh++) {
+        S16Batch bt;
+        bt.nrhs = nrhs;
+        bt.stride = sb;
+        bt.shape = sh;
+        S16EpiArgs e1a = {};
+        e1a.part_out = part;
+        S16EpiArgs e2a = {};
+        e2a.sigma = 0.01;
+        e2a.aux = in;
+        best[sh] = 1e30f;
+        for (int rep = 0; rep < 4 && err == cudaSuccess; rep++) {
+            cudaEventRecord(e0, s);
+            launch_hop_even_s16(g->geom, g->stf, g->links_s16, in, te, false, nullptr, s, bt);
+            launch_hop_odd_s16(g->geom, g->stf, g->links_s16, in, tei, y, false, EPI_STORE_NORMS, e1a, s, bt);
+            launch_hop_even_s16(g->geom, g->stf, g->links_s16, yi, te, true, nullptr, s, bt);
+            launch_hop_odd_s16(g->geom, g->stf, g->links_s16, yi, tei, te, true, EPI_SHIFT, e2a, s, bt);
+            cudaEventRecord(e1, s);
+            err = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best[sh]) best[sh] = ms;
+        }
+        if (best[sh] < best[choice]) choice = sh;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (err != cudaSuccess) {
+        tmnd_set_error("tmnd_autotune: %s", cudaGetErrorString(err));
+        return TMND_ERR_CUDA;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tuned[key] = choice;
+        g_tune_ms[key] = best;
+    }
+    if (shape_out) *shape_out = choice;
+    if (ms_out)
+        for (int i = 0; i < NSHAPES; i++) ms_out[i] = best[i];
+    return TMND_OK;
+}
+
+extern "C" tmnd_status tmnd_autotune(tmnd_gauge *g, int nrhs, int *shape_out, double *ms_out, void *stream) {
+    TMND_ARG_CHECK(g, "tmnd_autotune: NULL handle");
+    cudaGetLastError();
+    float ms[NSHAPES];
+    int sh = 0;
+    const tmnd_status st = s16_autotune(g, nrhs, (cudaStream_t)stream, &sh, ms);
+    if (st != TMND_OK) return st;
+    if (shape_out) *shape_out = sh;
+    if (ms_out)
+        for (int i = 0; i < NSHAPES; i++) ms_out[i] = ms[i];
+    return TMND_OK;
+}
+
+extern "C" tmnd_status tmnd_s16_force_shape(int shape) {
+    TMND_ARG_CHECK(shape >= -1 && shape < NSHAPES, "tmnd_s16_force_shape: shape %d not in [-1, %d)", shape, NSHAPES);
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    g_forced = shape;
+    return TMND_OK;
+}
+
+extern "C" tmnd_status tmnd_s16_shape_info(int shape, int *threads, int *blocks_per_sm, int *prefetch) {
+    TMND_ARG_CHECK(shape >= 0 && shape < NSHAPES, "tmnd_s16_shape_info: shape %d not in [0, %d)", shape, NSHAPES);
+    if (threads) *threads = kShapes[shape].threads;
+    if (blocks_per_sm) *blocks_per_sm = kShapes[shape].minb;
+    if (prefetch) *prefetch = kShapes[shape].pf;
+    return TMND_OK;
 }

@@ -82,6 +82,12 @@ static bool su3_ok(const std::complex<double> *u) {
     return err < 1e-10 && std::abs(det - 1.0) < 1e-10;
 }
 
+// packed FP64 links -> the same layout in FP32 (the FP32 operator)
+__global__ void k_links_to_f32(long n, const double2 *__restrict__ in, float2 *__restrict__ out) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
 extern "C" tmnd_status tmnd_gauge_create(const double *host_links, const tmnd_action *act, int prec,
                                          tmnd_gauge **out) {
     TMND_ARG_CHECK(out != nullptr, "tmnd_gauge_create: out is NULL");
@@ -131,12 +137,14 @@ extern "C" tmnd_status tmnd_gauge_create(const double *host_links, const tmnd_ac
     double2 *canon = nullptr;
     cudaError_t e = cudaMalloc(&g->links, nb);
     if (e == cudaSuccess) e = cudaMalloc(&g->links_s16, sizeof(int2) * 3 * 4 * (size_t)V);
+    if (e == cudaSuccess) e = cudaMalloc(&g->links_f32, sizeof(float2) * 4 * V * 9);
     if (e == cudaSuccess) e = cudaMalloc(&canon, nb);
     if (e == cudaSuccess) e = cudaMemcpy(canon, host_links, nb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         long n = 4 * V * 9;
         k_pack_links<<<(unsigned)((n + 255) / 256), 256>>>(g->geom, canon, g->links);
         launch_pack_links_s16(g->geom, canon, g->links_s16, 0);
+        k_links_to_f32<<<(unsigned)((n + 255) / 256), 256>>>(n, g->links, g->links_f32);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -145,6 +153,7 @@ extern "C" tmnd_status tmnd_gauge_create(const double *host_links, const tmnd_ac
         tmnd_set_error("tmnd_gauge_create: %s", cudaGetErrorString(e));
         if (g->links) cudaFree(g->links);
         if (g->links_s16) cudaFree(g->links_s16);
+        if (g->links_f32) cudaFree(g->links_f32);
         delete g;
         return e == cudaErrorMemoryAllocation ? TMND_ERR_OOM : TMND_ERR_CUDA;
     }
@@ -157,6 +166,7 @@ extern "C" void tmnd_gauge_destroy(tmnd_gauge *g) {
     cudaDeviceSynchronize();
     if (g->links) cudaFree(g->links);
     if (g->links_s16) cudaFree(g->links_s16);
+    if (g->links_f32) cudaFree(g->links_f32);
     if (g->work) cudaFree(g->work);
     if (g->partials) cudaFree(g->partials);
     delete g;
@@ -251,7 +261,9 @@ static tmnd_status apply_s16(tmnd_gauge *g, void *out, const void *in, int op, d
                              cudaStream_t s) {
     const int Vh = g->geom.Vh;
     const size_t sb = spinor_bytes_prec(Vh, TMND_S16);
-    tmnd_status st = tmnd_ensure_workspace(g, 2 * (size_t)nrhs * sb);
+    tmnd_status st = s16_autotune(g, nrhs, s, nullptr, nullptr);  // first use of (lattice, nrhs)
+    if (st != TMND_OK) return st;
+    st = tmnd_ensure_workspace(g, 2 * (size_t)nrhs * sb);
     if (st != TMND_OK) return st;
     S16Out te = s16_out(g->work, Vh);
     S16Out yo = s16_out((char *)g->work + (size_t)nrhs * sb, Vh);
@@ -289,9 +301,57 @@ static tmnd_status apply_s16(tmnd_gauge *g, void *out, const void *in, int op, d
     return TMND_OK;
 }
 
+// FP32 operator on TMND_F32 spinors (24 complex64 planes per right-hand side), one
+// right-hand side per launch sequence.
+tmnd_status apply_f32(tmnd_gauge *g, float2 *out, const float2 *in, int op, double sigma, int nrhs, float2 *te,
+                      float2 *yo, cudaStream_t s) {
+    const size_t n = (size_t)NCOMP * g->geom.Vh;
+    HopEpiArgsF ea = {};
+    for (int k = 0; k < nrhs; k++) {
+        const float2 *ik = in + k * n;
+        float2 *ok = out + k * n;
+        switch (op) {
+            case TMND_OP_MHAT:
+            case TMND_OP_MHAT_DAG: {
+                const bool dag = op == TMND_OP_MHAT_DAG;
+                launch_hop_even_f32(g->geom, g->st, g->links_f32, ik, te, dag, nullptr, s);
+                launch_hop_odd_f32(g->geom, g->st, g->links_f32, ik, te, ok, dag, EPI_STORE, ea, s);
+                break;
+            }
+            case TMND_OP_QHAT2: {
+                launch_hop_even_f32(g->geom, g->st, g->links_f32, ik, te, false, nullptr, s);
+                launch_hop_odd_f32(g->geom, g->st, g->links_f32, ik, te, yo, false, EPI_STORE, ea, s);
+                HopEpiArgsF e2 = {};
+                e2.sigma = sigma;
+                e2.aux = ik;
+                launch_hop_even_f32(g->geom, g->st, g->links_f32, yo, te, true, nullptr, s);
+                launch_hop_odd_f32(g->geom, g->st, g->links_f32, yo, te, ok, true, EPI_SHIFT, e2, s);
+                break;
+            }
+            default:
+                tmnd_set_error("tm_nd_apply: op %d not available for TMND_F32 spinors", op);
+                return TMND_ERR_ARG;
+        }
+    }
+    TMND_CUDA_TRY(cudaGetLastError());
+    return TMND_OK;
+}
+
 extern "C" tmnd_status tm_nd_apply(tmnd_gauge *g, void *out, const void *in, int op, double sigma, int nrhs,
                                    void *stream) {
     TMND_ARG_CHECK(g && out && in, "tm_nd_apply: NULL argument");
+    if (op & TMND_OP_F32) {
+        TMND_ARG_CHECK(!(op & TMND_OP_S16), "tm_nd_apply: TMND_OP_F32 and TMND_OP_S16 both set");
+        TMND_ARG_CHECK(nrhs >= 1 && out != in && ((uintptr_t)out & 15) == 0 && ((uintptr_t)in & 15) == 0 &&
+                           isfinite(sigma),
+                       "tm_nd_apply: bad arguments (FP32 spinors)");
+        cudaGetLastError();
+        const size_t s32 = spinor_bytes_prec(g->geom.Vh, TMND_F32);
+        tmnd_status st = tmnd_ensure_workspace(g, 2 * s32);
+        if (st != TMND_OK) return st;
+        return apply_f32(g, (float2 *)out, (const float2 *)in, op & ~TMND_OP_F32, sigma, nrhs, (float2 *)g->work,
+                         (float2 *)((char *)g->work + s32), (cudaStream_t)stream);
+    }
     if (op & TMND_OP_S16) {
         TMND_ARG_CHECK(nrhs >= 1 && nrhs <= TMND_MAX_BATCH && out != in && ((uintptr_t)out & 15) == 0 &&
                            ((uintptr_t)in & 15) == 0 && isfinite(sigma),

@@ -18,9 +18,6 @@ size_t tmnd_mg_nblock_nv(const tmnd_mg *mg, int *nv);
 
 namespace {
 
-__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
-    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
-}
 
 // Full-lattice doublet operator, output parity P, FP32 (links rounded from FP64):
 // y = (1 + i kp g5 t3 - kpp t1 [+ i s g5 t1 on odd sites]) x_P - kappa H x_{1-P}

@@ -877,7 +877,12 @@ static tmnd_status mms_sloppy(tmnd_gauge *g, const MixedWork &m, const double *s
     const int Vh = g->geom.Vh;
     const long n = 24L * Vh;
     const int R = m.nrhs;
-    const int nb_hop = hop_blocks_s16(g->geom);
+    // launch shape of the stencil for R right-hand sides per launch (tuned on first use, before
+    // any graph capture); every launch of the solve uses it, so the partial counts agree
+    tmnd_status ts = s16_autotune(g, R, s, nullptr, nullptr);
+    if (ts != TMND_OK) return ts;
+    const int shape = s16_shape(g->geom, R);
+    const int nb_hop = hop_blocks_s16(g->geom, shape);
     const int nb_str = stream_blocks(n);
     const int nb_site = site_blocks(Vh);
     double *part_norm = (double *)g->partials;                 // [R][2][nb_hop]
@@ -915,6 +920,7 @@ static tmnd_status mms_sloppy(tmnd_gauge *g, const MixedWork &m, const double *s
     bt.stride = v.sb;
     bt.rdone = &st->done;
     bt.rdone_stride = (int)(st_stride / sizeof(int));
+    bt.shape = shape;
 
     k_init_s<<<dim3(nb_site, R), 128, 0, s>>>(Vh, v, part_str);
     k_init_state_b<<<R, 256, 0, s>>>(st, st_stride, part_str, nb_site, c, bc);
@@ -970,7 +976,7 @@ static tmnd_status mms_sloppy(tmnd_gauge *g, const MixedWork &m, const double *s
 // partial-buffer bytes the sloppy solve of nrhs right-hand sides needs
 static size_t sloppy_partial_bytes(const Geom &geom, int nrhs) {
     const long n = 24L * geom.Vh;
-    const int nb_hop = hop_blocks_s16(geom);
+    const int nb_hop = hop_blocks_s16_max(geom);
     const int nb_str = stream_blocks(n), nb_site = site_blocks(geom.Vh);
     const size_t st_stride = (sizeof(MMSState) + 255) & ~(size_t)255;
     const size_t cf_stride = (sizeof(MMSCoef) + 255) & ~(size_t)255;
@@ -1003,7 +1009,7 @@ static tmnd_status fp64_defect(tmnd_gauge *g, const MixedWork &m, const double2 
 }
 
 struct RefineStats {
-    int fp64 = 0, rounds = 0, iters = 0;
+    int fp64 = 0, rounds = 0, iters = 0, f32 = 0;
     long long launches = 0;
     double hop_ms = 0, upd_ms = 0;
 };
@@ -1023,6 +1029,131 @@ struct DCItem {
     double *res0 = nullptr;  // optional: the relative residual of the first round (before any correction)
 };
 
+// Inner iterative refinement of one chunk of pairs, in FP32 (between two FP64 defects):
+// the defect d (FP32 copy) is solved by batched sloppy CGs on the 16-bit operator, each
+// reducing the current inner residual by the factor the pair still needs (at least
+// `floor`); after each, the correction accumulated so far is checked with the FP32
+// operator, r = d - (Qhat^2 + sigma) e (accurate to ~1e-7 of |d|, where the 16-bit
+// operator's own ~4e-5 would stall), and r is the next right-hand side.  A pair stops
+// once |r| <= target; the others go on, at most `max_inner` sloppy solves.
+tmnd_status apply_f32(tmnd_gauge *g, float2 *out, const float2 *in, int op, double sigma, int nrhs, float2 *te,
+                      float2 *yo, cudaStream_t s);
+
+// r = d - y (FP32) and block partials |r|^2 (FP64)
+__global__ void k_resid32(long n, const float2 *__restrict__ d, const float2 *__restrict__ y, float2 *__restrict__ r,
+                          double *__restrict__ part) {
+    __shared__ double red[40];
+    double acc = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float2 u = d[i], v = y[i];
+        const float2 w = make_float2(u.x - v.x, u.y - v.y);
+        r[i] = w;
+        acc = fma((double)w.x, (double)w.x, fma((double)w.y, (double)w.y, acc));
+    }
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// e += c (FP32)
+__global__ void k_add32(long n, const float2 *__restrict__ c, float2 *__restrict__ e) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float2 u = c[i];
+        float2 v = e[i];
+        v.x += u.x;
+        v.y += u.y;
+        e[i] = v;
+    }
+}
+
+// FP32 vectors of the inner refinement after the sloppy workspace: d and e per slot, two temporaries
+struct InnerVecs {
+    float2 *d0, *e0, *te, *yo;
+    long n;
+    float2 *d(int c) const { return d0 + (size_t)c * n; }
+    float2 *e(int c) const { return e0 + (size_t)c * n; }
+};
+static size_t dc_work_bytes(int Vh, int R) {
+    return mixed_work_bytes(Vh, 1, R) + (2 * (size_t)R + 2) * spinor_bytes_prec(Vh, TMND_F32);
+}
+static InnerVecs inner_vecs(void *base, int Vh, int R) {
+    const size_t s32 = spinor_bytes_prec(Vh, TMND_F32);
+    char *w = (char *)base + mixed_work_bytes(Vh, 1, R);
+    InnerVecs v;
+    v.n = 24L * Vh;
+    v.d0 = (float2 *)w;
+    v.e0 = (float2 *)(w + (size_t)R * s32);
+    v.te = (float2 *)(w + 2 * (size_t)R * s32);
+    v.yo = (float2 *)(w + (2 * (size_t)R + 1) * s32);
+    return v;
+}
+
+static tmnd_status inner_refine(tmnd_gauge *g, const MixedWork &mc, const InnerVecs &iv, const double *sig,
+                                const double *target, const double *dnorm, int R, double floor, int max_inner,
+                                int maxiter, int check_every, int profile, cudaStream_t s, RefineStats &rs) {
+    const int Vh = g->geom.Vh;
+    const long n = 24L * Vh;
+    const int nb = stream_blocks(n);
+    double *part = (double *)g->partials;
+    std::vector<double> rn(dnorm, dnorm + R), tl(R);
+    std::vector<int> active(R, 1);
+    std::vector<double> hpart(nb);
+    for (int c = 0; c < R; c++) {
+        TMND_CUDA_TRY(cudaMemcpyAsync(iv.d(c), mc.b32(c), sizeof(float2) * n, cudaMemcpyDeviceToDevice, s));
+        TMND_CUDA_TRY(cudaMemsetAsync(iv.e(c), 0, sizeof(float2) * n, s));
+    }
+    for (int j = 0; j < max_inner; j++) {
+        int nact = 0;
+        for (int c = 0; c < R; c++) {
+            if (!active[c]) {  // a zero right-hand side is done at once
+                TMND_CUDA_TRY(cudaMemsetAsync(mc.b32(c), 0, sizeof(float2) * n, s));
+                tl[c] = 0.5;
+                continue;
+            }
+            nact++;
+            const double need = target[c] / rn[c];
+            tl[c] = need > floor ? need : floor;
+        }
+        if (nact == 0) break;
+        std::vector<MMSState> hv;
+        LoopOut lc;
+        tmnd_status st = mms_sloppy(g, mc, sig, 1, 1, floor, maxiter, check_every, profile, s, hv, lc, nullptr, 0,
+                                    sig, tl.data());
+        if (st != TMND_OK) return st;
+        int maxit = 0;
+        for (const MMSState &h : hv) {
+            rs.iters += h.iter;
+            maxit = h.iter > maxit ? h.iter : maxit;
+        }
+        for (int k = 0; k < maxit && k < (int)lc.hop_t.size(); k++) {
+            rs.hop_ms += lc.hop_t[k];
+            rs.upd_ms += lc.upd_t[k];
+        }
+        rs.launches += 3 + lc.nlaunch * ((long long)check_every * 7 + check_every / WIN);
+        // accumulate, then the FP32 residual of the accumulated correction as the next right-hand side
+        for (int c = 0; c < R; c++) {
+            if (!active[c]) continue;
+            k_add32<<<nb, UPD_THREADS, 0, s>>>(n, mc.x32(c, 0), iv.e(c));
+            st = apply_f32(g, iv.yo + 0, iv.e(c), TMND_OP_QHAT2, sig[c], 1, iv.te, mc.x32(c, 0), s);
+            if (st != TMND_OK) return st;
+            // apply_f32 left (Qhat^2 + sigma) e in iv.yo (its odd temporary is the slot's x32, free now)
+            k_resid32<<<nb, UPD_THREADS, 0, s>>>(n, iv.d(c), iv.yo, mc.b32(c), part);
+            TMND_CUDA_TRY(cudaMemcpyAsync(hpart.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+            TMND_CUDA_TRY(cudaStreamSynchronize(s));
+            double acc = 0;
+            for (int q = 0; q < nb; q++) acc += hpart[q];
+            rn[c] = sqrt(acc);
+            rs.f32 += 1;
+            rs.launches += 5;
+            if (!isfinite(rn[c])) {
+                tmnd_set_error("solve: NaN/Inf in an FP32 inner residual (shift %g)", sig[c]);
+                return TMND_ERR_NAN;
+            }
+            if (rn[c] <= target[c]) active[c] = 0;
+        }
+    }
+    return TMND_OK;
+}
+
 static tmnd_status defect_correct(tmnd_gauge *g, void *base, std::vector<DCItem> todo, double rho,
                                   double rho_inner, int maxiter, int check_every, int profile, cudaStream_t s,
                                   RefineStats &rs, int max_batch) {
@@ -1032,14 +1163,16 @@ static tmnd_status defect_correct(tmnd_gauge *g, void *base, std::vector<DCItem>
     tmnd_status st;
     if (max_batch < 1) max_batch = 1;
     if (max_batch > TMND_MAX_BATCH) max_batch = TMND_MAX_BATCH;
+    const double floor = rho_inner > 1e-4 ? rho_inner : 1e-4;  // a sloppy correction gains at most ~1/(4e-5)
     for (int round = 0; !todo.empty(); round++) {
         std::vector<DCItem> next;
         size_t q = 0;
         while (q < todo.size()) {
             // defects of up to max_batch pending pairs, each converted into its sloppy slot
             const MixedWork mw = mixed_work(base, Vh, 1, max_batch);
+            const InnerVecs iv = inner_vecs(base, Vh, max_batch);
             std::vector<DCItem> chunk;
-            std::vector<double> sg, tl;
+            std::vector<double> sg, target, dn;
             for (; q < todo.size() && (int)chunk.size() < max_batch; q++) {
                 DCItem &it = todo[q];
                 double rr = 0;
@@ -1061,31 +1194,19 @@ static tmnd_status defect_correct(tmnd_gauge *g, void *base, std::vector<DCItem>
                 }
                 st = convert_spinor(Vh, mw.b32((int)chunk.size()), TMND_F32, mw.r64, TMND_F64, 1, s);
                 if (st != TMND_OK) return st;
-                const double need = 0.3 * rho / *it.res;
                 sg.push_back(it.sigma);
-                tl.push_back(need > rho_inner ? need : rho_inner);
+                target.push_back(0.3 * rho * sqrt(it.bb));  // |d - (Qhat^2 + sigma) e| for |b - ... x'| <= rho |b|
+                dn.push_back(sqrt(rr));
                 chunk.push_back(it);
             }
             if (chunk.empty()) continue;
             MixedWork mc = mw;  // the slots the defects were converted into
             mc.nrhs = (int)chunk.size();
-            std::vector<MMSState> hv;
-            LoopOut lc;
-            st = mms_sloppy(g, mc, sg.data(), 1, 1, rho_inner, maxiter, check_every, profile, s, hv, lc, nullptr, 0,
-                            sg.data(), tl.data());
+            st = inner_refine(g, mc, iv, sg.data(), target.data(), dn.data(), mc.nrhs, floor, 4, maxiter, check_every,
+                              profile, s, rs);
             if (st != TMND_OK) return st;
-            int maxit = 0;
-            for (const MMSState &h : hv) {
-                rs.iters += h.iter;
-                maxit = h.iter > maxit ? h.iter : maxit;
-            }
-            for (int k = 0; k < maxit && k < (int)lc.hop_t.size(); k++) {
-                rs.hop_ms += lc.hop_t[k];
-                rs.upd_ms += lc.upd_t[k];
-            }
-            rs.launches += 3 + lc.nlaunch * ((long long)check_every * 7 + check_every / WIN);
             for (size_t c = 0; c < chunk.size(); c++) {
-                k_add_f32_to_f64<<<stream_blocks(n), UPD_THREADS, 0, s>>>(n, mc.x32((int)c, 0), chunk[c].x);
+                k_add_f32_to_f64<<<stream_blocks(n), UPD_THREADS, 0, s>>>(n, iv.e((int)c), chunk[c].x);
                 next.push_back(chunk[c]);
             }
             TMND_CUDA_TRY(cudaGetLastError());
@@ -1105,7 +1226,7 @@ static int refine_batch(int R, int nsolve) {
 // workspace of the mixed solve of R right-hand sides: the batched multi-shift vectors, then
 // (same memory) the single-shift vectors of one batch of defect-correction pairs
 static size_t mixed_total_bytes(int Vh, int nshift, int nsolve, int R) {
-    const size_t a = mixed_work_bytes(Vh, nshift, R), b = mixed_work_bytes(Vh, 1, refine_batch(R, nsolve));
+    const size_t a = mixed_work_bytes(Vh, nshift, R), b = dc_work_bytes(Vh, refine_batch(R, nsolve));
     return a > b ? a : b;
 }
 
@@ -1193,6 +1314,7 @@ static tmnd_status mixed_batch(tmnd_gauge *g, const double2 *b, double2 *const *
                 if (k0 + k == 0 || res[k][i] > info->true_res[i]) info->true_res[i] = res[k][i];
     if (info) {
         info->fp64_applies += fp64;
+        info->f32_applies += rs.f32;
         info->refine_iters += riters;
         if (rounds > info->refine_rounds) info->refine_rounds = rounds;
         info->launches += launches;
@@ -1238,7 +1360,8 @@ extern "C" tmnd_status mms_cg_solve(tmnd_gauge *g, const void *b, int nrhs, cons
         g, mixed ? mixed_total_bytes(g->geom.Vh, nshift, nsolve, R) : (WIN + 3 + (size_t)nshift) * sp);
     if (st != TMND_OK) return st;
     const long n = (long)(sp / sizeof(double2));
-    const int nbh = hop_blocks(g->geom) > hop_blocks_s16(g->geom) ? hop_blocks(g->geom) : hop_blocks_s16(g->geom);
+    const int nbh = hop_blocks(g->geom) > hop_blocks_s16_max(g->geom) ? hop_blocks(g->geom)
+                                                                       : hop_blocks_s16_max(g->geom);
     const int nbs = stream_blocks(n) > site_blocks(g->geom.Vh) ? stream_blocks(n) : site_blocks(g->geom.Vh);
     size_t pbytes = sizeof(double) * (3 * (size_t)nbh + nbs) + 256 + 2 * 4096 + sizeof(MMSState) + sizeof(MMSCoef);
     if (mixed) {
@@ -1355,6 +1478,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
         hinfo->launches = si.launches;
         hinfo->mms_iters = si.iters;
         hinfo->fp64_applies = si.fp64_applies;
+        hinfo->f32_applies = si.f32_applies;
         hinfo->refine_iters = si.refine_iters;
         for (int i = 0; i < n_mms; i++) hinfo->true_res[i] = si.true_res[i];
     }
@@ -1396,7 +1520,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
     // case-C multigrid solve, then one batched FP64 defect correction of all its (RHS, shift) pairs
     const double rho_inner = hp->rho_inner > 0 ? hp->rho_inner : 1e-5;
     const int dc_batch = nrhs < TMND_MAX_BATCH ? nrhs : TMND_MAX_BATCH;
-    st = tmnd_ensure_workspace(g, mixed_work_bytes(Vh, 1, dc_batch));
+    st = tmnd_ensure_workspace(g, dc_work_bytes(Vh, dc_batch));
     if (st != TMND_OK) return st;
     const long nfull = 2 * n;  // full-lattice FP32 doublet (complex numbers)
     const size_t f32b = sizeof(float2) * nfull;
@@ -1534,6 +1658,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
             hinfo->shift_ms[i] =
                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_shift).count();
             hinfo->fp64_applies += rs.fp64;
+            hinfo->f32_applies += rs.f32;
             hinfo->refine_iters += rs.iters;
             hinfo->launches += rs.launches;
             for (int k = 0; k < nrhs; k++)

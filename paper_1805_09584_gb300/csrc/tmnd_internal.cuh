@@ -59,6 +59,7 @@ struct tmnd_gauge {
     Geom geom;
     SiteTerm st;
     double2 *links;        // [2 parity][4 mu][9][Vh] complex, U_mu(x) stored at the parity/half-index of x
+    float2 *links_f32;     // the same in FP32 (the FP32 operator)
     int2 *links_s16;       // [2 parity][4 mu][3][Vh]: rows 0, 1 as int16 pairs (scale 32767)
     SiteTermF stf;         // FP32 copy of st for the sloppy kernels
     void *work;            // grow-only workspace
@@ -105,6 +106,29 @@ __device__ __forceinline__ double2 cflip(double2 a, unsigned long long mask) {
     return make_double2(dflip(a.x, mask), dflip(a.y, mask));
 }
 
+// The same complex helpers in FP32 (the FP32 instantiation of the FP64 stencil).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(-a.y, a.x); }
+__device__ __forceinline__ float2 cmulmi(float2 a) { return make_float2(a.y, -a.x); }
+__device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cfma_conj(float2 a, float2 b, float2 acc) {
+    return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 cflip(float2 a, unsigned long long mask) {
+    const int m = mask ? (int)0x80000000 : 0;
+    return make_float2(__int_as_float(__float_as_int(a.x) ^ m), __int_as_float(__float_as_int(a.y) ^ m));
+}
+
 // Block-wide sum of one double (blockDim.x a multiple of 32, <= 1024); result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double *smem /* >= 32 */) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -145,17 +169,20 @@ enum HopEpi {
 
 constexpr int HOP_THREADS = 128;
 
-struct HopEpiArgs {
+template <typename C2>
+struct HopEpiT {
     double sigma;
-    const double2 *aux;     // EPI_SHIFT / EPI_MMS_R: the vector multiplied by sigma
-    double2 *r;             // EPI_MMS_R: updated residual (written)
-    const double2 *r_in;    // EPI_MMS_R: residual before the update (NULL: update r in place)
+    const C2 *aux;          // EPI_SHIFT / EPI_MMS_R: the vector multiplied by sigma
+    C2 *r;                  // EPI_MMS_R: updated residual (written)
+    const C2 *r_in;         // EPI_MMS_R: residual before the update (NULL: update r in place)
     double *part_out;       // partial sums written per block (EPI_STORE_NORMS: 2 per block; EPI_MMS_R: 1)
     const double *part_in;  // EPI_MMS_R: partials of |y|^2, |p|^2 from the previous kernel
     int npart_in;           // number of blocks that wrote part_in
     const double *rr;       // EPI_MMS_R: (r,r) before the update (device scalar)
     const int *done;        // if non-null and *done != 0 the kernel returns immediately
 };
+using HopEpiArgs = HopEpiT<double2>;
+using HopEpiArgsF = HopEpiT<float2>;
 
 // even-site kernel: t_e = kappa^2 A^-1 H_eo psi_o   (dag: kappa^2 A(-mu)^-1 H_eo gamma_5 psi_o)
 void launch_hop_even_f64(const Geom &g, const SiteTerm &st, const double2 *links, const double2 *psi_o,
@@ -166,6 +193,13 @@ void launch_hop_odd_f64(const Geom &g, const SiteTerm &st, const double2 *links,
                         cudaStream_t s);
 // Number of blocks (= reduction partials) of every hop launch for this geometry.
 int hop_blocks(const Geom &g);
+// The same stencil in FP32 on FP32 planes with 18-real FP32 links (the FP32 operator:
+// accurate to ~1e-7, used for inner residuals of the defect correction)
+void launch_hop_even_f32(const Geom &g, const SiteTerm &st, const float2 *links, const float2 *psi_o, float2 *t_e,
+                         bool dag, const int *done, cudaStream_t s);
+void launch_hop_odd_f32(const Geom &g, const SiteTerm &st, const float2 *links, const float2 *psi_o,
+                        const float2 *t_e, float2 *y_o, bool dag, HopEpi epi, const HopEpiArgsF &ea, cudaStream_t s);
+int hop_blocks_f32(const Geom &g);
 
 // ------------------------------------------------- sloppy (16-bit) path
 
@@ -226,9 +260,14 @@ struct S16Batch {
     size_t stride = 0;
     const int *rdone = nullptr;
     int rdone_stride = 0;
+    int shape = -1;  // compiled launch shape (dslash_s16.cu); -1: the autotuner's choice for (lattice, nrhs)
 };
 
-int hop_blocks_s16(const Geom &g);
+// launch shapes of the 16-bit stencil and their autotuner (dslash_s16.cu)
+int hop_blocks_s16(const Geom &g, int shape);
+int hop_blocks_s16_max(const Geom &g);
+int s16_shape(const Geom &g, int nrhs);
+tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out, float *ms_out);
 void launch_hop_even_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In in, S16Out out, bool dag,
                          const int *done, cudaStream_t s, const S16Batch &bt = S16Batch());
 void launch_hop_odd_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In psi, S16In te, S16Out out,

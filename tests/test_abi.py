@@ -73,3 +73,18 @@ def test_oracle_and_library_share_no_code():
                 if f.endswith((".cu", ".cuh", ".c", ".h")):
                     txt = open(os.path.join(dp, f)).read()
                     assert "tmnd_oracle" not in txt or path.endswith("oracle")
+
+
+def test_s16_shape_table_host(tm):
+    """The compiled launch shapes of the 16-bit stencil (host queries, no GPU needed)."""
+    seen = set()
+    for sh in range(tm.S16_SHAPES):
+        t, b, pf = tm.tmnd_s16_shape_info(sh)
+        assert t % 32 == 0 and 1 <= b <= 8 and t * b <= 1024
+        seen.add((t, b, pf))
+    assert len(seen) == tm.S16_SHAPES
+    with pytest.raises(tm.TmndError):
+        tm.tmnd_s16_shape_info(tm.S16_SHAPES)
+    with pytest.raises(tm.TmndError):
+        tm.tmnd_s16_force_shape(tm.S16_SHAPES)
+    tm.tmnd_s16_force_shape(-1)

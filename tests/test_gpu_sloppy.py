@@ -64,3 +64,25 @@ def test_s16_apply_matches_oracle(dims, op, tol):
     got = g.unpack(g.convert(out, tm.TMND_S16, tm.TMND_F64))[0].cpu().numpy()
     assert rel_err(got, ref) <= tol
     g.close()
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 6, 8)])
+def test_f32_operator_matches_oracle(dims):
+    """The FP32 operator (TMND_OP_F32: the FP64 stencil instantiated in FP32 with FP32 links,
+    used for the inner residuals of the defect correction) against the oracle: FP32 rounding
+    of inputs, links and ~100 summed products per component gives a norm-wise relative error
+    of a few 1e-7; bound 2e-6 for Mhat, Mhat^+ and Qhat^2 + sigma, two right-hand sides."""
+    tm, U, g = _gauge(dims, seed=7)
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    b = synth.gaussian_rhs(dims, 31, nrhs=2)
+    bi = g.pack(torch.from_numpy(b).cuda(), nrhs=2)
+    f = g.convert(bi, tm.TMND_F64, tm.TMND_F32, nrhs=2)
+    for op, ref_fn in ((tm.OP_MHAT, lambda v: oracle.schur(act, U, v)),
+                       (tm.OP_MHAT_DAG, lambda v: oracle.schur(act, U, v, dagger=True)),
+                       (tm.OP_QHAT2, lambda v: oracle.qhat2(act, U, v, 0.021))):
+        o = g.spinor(2, prec=tm.TMND_F32)
+        tm.tm_nd_apply(g.handle, o, f, op | tm.OP_F32, 0.021, nrhs=2)
+        got = g.unpack(g.convert(o, tm.TMND_F32, tm.TMND_F64, nrhs=2), nrhs=2).cpu().numpy()
+        for k in range(2):
+            assert rel_err(got[k], ref_fn(b[k])) < 2e-6, (op, k)
+    g.close()
