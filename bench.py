@@ -39,6 +39,7 @@ Each form's line also times the plain FP64 multi-shift CG on its workload
 16^3x32 field against a known solution, rho = 1e-2 .. 1e-10.
 --study learned runs config 5: train on solves of 20 fields, evaluate on 5 unseen
 fields (CG iterations for the 4 smallest shifts from zero, Lagrange and learned guesses).
+--study mg compares the case-C multigrid's smoothers and setups at small shifts (24^3x48).
 --study hybrid measures the hybrid cost model of Sec. 4.3 on GB300 (24^3x48):
 per-shift CG and MG times, their fits, the model's optimal n and the measured
 hybrid time for every n, without and with Lagrange guesses.
@@ -772,6 +773,67 @@ def run_study_learned(args):
 
 
 
+def run_study_mg(args):
+    """Case-C multigrid at small shifts (Sec. 3: DD-alphaAMG smooths with SAP and builds its
+    prolongator adaptively), 24^3x48, 4^4 aggregates, 24 test vectors per chirality: for
+    s^2 = sigma in (0.07, 7.8e-3, 2.8e-4, 1e-5) the outer iterations and the time to reach
+    1e-4 from a zero start (at most 100 outer iterations, GCR(24), 2 smoothing steps) of
+    D_ND + i s gamma_5 tau_1 Pi_odd on a Gaussian full-lattice right-hand side, for minimal-
+    residual smoothing (test vectors relaxed by 4 MR steps), SAP smoothing with the same
+    vectors, and SAP after one round of adaptive setup; next to the mixed CG on the same shift."""
+    import torch
+
+    import paper_1805_09584_gb300 as tm
+    import synth
+    from paper_1805_09584_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    dims = (48, 24, 24, 24)
+    g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
+    nv, blk = 24, (4, 4, 4, 4)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    tv = torch.randn(nv * 2 * 12 * g.vh, dtype=torch.complex64, device="cuda", generator=gen)
+    tm.tmnd_mg_smooth_vectors(g.handle, tv, nv, 4)
+    t0 = time.perf_counter()
+    mg_mr = tm.tmnd_mg_create(g.handle, blk, nv, tv)
+    mg_sap = tm.tmnd_mg_create(g.handle, blk, nv, tv, smoother=1)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mg_boot = tm.tmnd_mg_bootstrap(mg_sap, tv, 3, blk, nv, smoother=1)
+    torch.cuda.synchronize()
+    t_boot = time.perf_counter() - t0
+    rhs = torch.randn(2 * 24 * g.vh, dtype=torch.complex64, device="cuda", generator=gen)
+    b_odd = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, 2003)).cuda())
+    rows = []
+    for sigma in (0.07, 7.8e-3, 2.8e-4, 1e-5):
+        s = float(sigma) ** 0.5
+        row = {"sigma": sigma}
+        for name, mg in (("mr", mg_mr), ("sap", mg_sap), ("sap_bootstrap", mg_boot)):
+            x = torch.zeros_like(rhs)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            info = tm.tmnd_mg_solve(mg, x, rhs, s, tol=1e-4, maxiter=100, restart=24, nu=2)
+            torch.cuda.synchronize()
+            row[name] = {"iters": info["iters"], "res": info["res"], "s": time.perf_counter() - t}
+        xs = [g.spinor()]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        inf = tm.mms_cg_solve(g.handle, b_odd, 1, [sigma], xs, rho=1e-10, prec=tm.TMND_S16)
+        torch.cuda.synchronize()
+        row["mixed_cg_1e-10"] = {"iters": inf["iters"] + inf["refine_iters"], "s": time.perf_counter() - t}
+        rows.append(row)
+    for mg in (mg_boot, mg_sap, mg_mr):
+        tm.tmnd_mg_destroy(mg)
+    g.close()
+    return {"study": "case-C multigrid at small shifts (SAP, adaptive setup)", "lattice": "24^3x48",
+            "aggregates": "4^4", "test_vectors": nv, "setup_s": t_setup, "bootstrap_s": t_boot,
+            "solve": "GCR(24), 2 pre/post smoothing steps, tol 1e-4, at most 100 outer iterations, zero start, "
+                     "Gaussian full-lattice right-hand side",
+            "rows": rows}
+
+
 def run_study_errors(args):
     """App. A (error and residual of equivalent solutions) on the 16^3x32 field: a known
     Gaussian x, b = (Qhat^2 + mu^2) x, methods A (direct), B (two consecutive single
@@ -944,10 +1006,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="hybrid", choices=list(FORMS))
     ap.add_argument("--kernel", default=None, choices=["fp64", "s16", "coarse"])
-    ap.add_argument("--study", default=None, choices=["hybrid", "learned", "errors"])
+    ap.add_argument("--study", default=None, choices=["hybrid", "learned", "errors", "mg"])
     args = ap.parse_args()
     if args.study:
-        fn = {"hybrid": run_study, "learned": run_study_learned, "errors": run_study_errors}[args.study]
+        fn = {"hybrid": run_study, "learned": run_study_learned, "errors": run_study_errors,
+              "mg": run_study_mg}[args.study]
         print(json.dumps(fn(args)))
         return
     if args.kernel:

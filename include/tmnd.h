@@ -320,6 +320,14 @@ typedef struct {
                                   make their MMA warps wait on a barrier that nothing completes, so
                                   that the wait runs out after wait_limit_s and the error path
                                   (drain of copies and MMAs in flight, flag, clean exit) runs */
+    int smoother;              /* 0: minimal-residual steps on the whole lattice; 1: SAP (Schwarz
+                                  alternating procedure, the DD-alphaAMG smoother of Sec. 3) on the
+                                  aggregation blocks (at most 256 sites each): per sweep and per
+                                  colour of a red/black block colouring, the residual on the whole
+                                  lattice, then sap_mr minimal-residual steps on every block of that
+                                  colour with the block-local operator (hops leaving the block
+                                  dropped), solved independently in parallel */
+    int sap_mr;                /* SAP: minimal-residual steps per block solve (0 = 4) */
 } tmnd_mg_params;
 
 /* Build the hierarchy from `nvec` caller-provided test vectors (device, FP32
@@ -354,6 +362,16 @@ tmnd_status tmnd_mg_prolong(const tmnd_mg *mg, void *out_fine, const void *in_c,
 tmnd_status mg_coarse_apply(const tmnd_mg *mg, void *out_c, const void *in_c, int nrhs, double odd_shift_s,
                             void *stream);
 
+/* Adaptive (bootstrap) setup (Sec. 3: the multigrid's own solves improve the test vectors
+ * it is built from).  Every one of the nvec test vectors v (device, single-flavour fine MG
+ * vectors as for tmnd_mg_create, updated in place) is replaced by the flavour-0 part of
+ * w ~ D_ND^-1 (v, 0) from `iters` outer iterations of mg's two-level method (s = 0; MR/SAP
+ * smoothing as configured, 2 steps), normalised; then a new hierarchy is built from the
+ * improved vectors with parameters p and returned in *out (the caller destroys both
+ * handles).  Call again on the result for more rounds.  Synchronous. */
+tmnd_status tmnd_mg_bootstrap(tmnd_mg *mg, const tmnd_mg_params *p, void *test_vectors, int iters, tmnd_mg **out,
+                              void *stream);
+
 /* Waits for the device, then reports whether a tensor-core coarse apply on this handle gave
  * up a bounded wait since the last check: TMND_ERR_TIMEOUT (and the flag is cleared), else
  * TMND_OK.  The handle stays usable either way.  Synchronous. */
@@ -369,8 +387,8 @@ tmnd_status tmnd_dnd_full_apply(tmnd_gauge *g, void *out, const void *in, double
 /* Solve D' x = b (fine doublet MG vectors, FP32; x holds the initial guess and
  * receives the solution) by flexible GCR(restart) preconditioned with one
  * two-level V-cycle per iteration (Sec. 3, Eq. "error_propagation"): `nu`
- * minimal-residual pre- and post-smoothing steps and a coarse GCR on
- * mg_coarse_apply.  Stops at |b - D'x| <= tol |b| or after maxiter outer
+ * pre- and post-smoothing steps (minimal residual on the whole lattice, or SAP sweeps,
+ * per the handle's smoother) and a coarse GCR on mg_coarse_apply.  Stops at |b - D'x| <= tol |b| or after maxiter outer
  * iterations; iters / res (relative residual, FP32 operator) may be NULL.
  * Synchronous; allocates its scratch for the call. */
 tmnd_status tmnd_mg_solve(tmnd_mg *mg, void *x, const void *b, double s, double tol, int maxiter, int restart,

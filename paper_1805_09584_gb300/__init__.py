@@ -38,7 +38,7 @@ EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd
            "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_zolotarev", "tmnd_rational_apply",
            "tmnd_hybrid_cost", "tmnd_fit_cg_time", "tmnd_fit_mg_time", "tmnd_lincomb_c", "tmnd_site_norm_range",
            "tmnd_lagrange_weights", "tmnd_lagrange_degree", "tmnd_guess_quadratic_form", "tmnd_mg_status",
-           "tmnd_autotune", "tmnd_s16_force_shape", "tmnd_s16_shape_info")
+           "tmnd_autotune", "tmnd_s16_force_shape", "tmnd_s16_shape_info", "tmnd_mg_bootstrap")
 S16_SHAPES = 4
 TMND_MAX_BATCH = 16
 NOALLOC_MAX_VH = 32768
@@ -57,7 +57,8 @@ class Action(ctypes.Structure):
 
 class MGParams(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int * 4), ("nvec", ctypes.c_int), ("coarse_mu_factor", ctypes.c_double),
-                ("coarse_simt", ctypes.c_int), ("wait_limit_s", ctypes.c_double), ("stall_test", ctypes.c_int)]
+                ("coarse_simt", ctypes.c_int), ("wait_limit_s", ctypes.c_double), ("stall_test", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("sap_mr", ctypes.c_int)]
 
 
 class HybridParams(ctypes.Structure):
@@ -132,6 +133,7 @@ def lib() -> ctypes.CDLL:
         L.mg_coarse_apply.argtypes = [vp, vp, vp, i, d, vp]
         L.tmnd_mg_export.argtypes = [vp, vp, vp, vp]
         L.tmnd_mg_status.argtypes = [vp]
+        L.tmnd_mg_bootstrap.argtypes = [vp, ctypes.POINTER(MGParams), vp, i, ctypes.POINTER(vp), vp]
         L.tmnd_dnd_full_apply.argtypes = [vp, vp, vp, d, vp]
         L.tmnd_mg_solve.argtypes = [vp, vp, vp, d, d, i, i, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]
         L.tmnd_mg_smooth_vectors.argtypes = [vp, vp, i, i, vp]
@@ -174,7 +176,7 @@ def lib() -> ctypes.CDLL:
                      "tmnd_guess_quadratic_form", "tmnd_autotune", "tmnd_s16_force_shape", "tmnd_s16_shape_info"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
-                     "tmnd_mg_status",
+                     "tmnd_mg_status", "tmnd_mg_bootstrap",
                      "tmnd_dnd_full_apply", "tmnd_mg_solve", "tmnd_mg_smooth_vectors", "tmnd_hybrid_solve"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_gauge_create", "tmnd_spinor_pack", "tmnd_spinor_unpack", "tm_nd_apply",
@@ -293,13 +295,35 @@ def lagrange_guess(h, nodes, xs, target: float, out, nrhs: int = 1, stream=None)
     return leb.value
 
 
-def tmnd_mg_create(h, block, nvec: int, test_vectors, coarse_mu_factor: float = 1.0, coarse_simt: bool = False,
-                   wait_limit_s: float = 0.0, stall_test: int = 0):
+def mg_params(block, nvec: int, coarse_mu_factor: float = 1.0, coarse_simt: bool = False, wait_limit_s: float = 0.0,
+              stall_test: int = 0, smoother: int = 0, sap_mr: int = 0) -> MGParams:
     p = MGParams()
     for k in range(4):
         p.block[k] = int(block[k])
     p.nvec, p.coarse_mu_factor, p.coarse_simt = int(nvec), float(coarse_mu_factor), int(bool(coarse_simt))
     p.wait_limit_s, p.stall_test = float(wait_limit_s), int(stall_test)
+    p.smoother, p.sap_mr = int(smoother), int(sap_mr)
+    return p
+
+
+def tmnd_mg_bootstrap(mg, test_vectors, iters: int, block, nvec: int, stream=None, **kw):
+    """A new hierarchy from the test vectors improved by `iters` outer iterations of mg's
+    two-level method (the vectors are updated in place); the caller destroys both handles."""
+    p = mg_params(block, nvec, **kw)
+    out = ctypes.c_void_p()
+    _check(lib().tmnd_mg_bootstrap(mg, ctypes.byref(p), _ptr(test_vectors), int(iters), ctypes.byref(out),
+                                   _stream(stream)))
+    return out
+
+
+def tmnd_mg_create(h, block, nvec: int, test_vectors, coarse_mu_factor: float = 1.0, coarse_simt: bool = False,
+                   wait_limit_s: float = 0.0, stall_test: int = 0, smoother: int = 0, sap_mr: int = 0):
+    p = MGParams()
+    for k in range(4):
+        p.block[k] = int(block[k])
+    p.nvec, p.coarse_mu_factor, p.coarse_simt = int(nvec), float(coarse_mu_factor), int(bool(coarse_simt))
+    p.wait_limit_s, p.stall_test = float(wait_limit_s), int(stall_test)
+    p.smoother, p.sap_mr = int(smoother), int(sap_mr)
     out = ctypes.c_void_p()
     _check(lib().tmnd_mg_create(h, ctypes.byref(p), _ptr(test_vectors), ctypes.byref(out)))
     return out

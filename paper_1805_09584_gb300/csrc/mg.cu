@@ -36,6 +36,8 @@ struct tmnd_mg {
     int tc;             // coarse apply on the tensor cores where the shape allows
     int *tc_err;        // device flag: a tensor-core kernel gave up waiting
     uint64_t wait_ns;   // limit of the tensor-core kernel's bounded waits
+    int smoother;       // 0: minimal residual on the whole lattice, 1: SAP on the aggregation blocks
+    int sap_mr;         // SAP: minimal-residual steps per block solve
     mutable int stall_next;  // test hook: tensor-core launches still to run with the stall barrier
     void *Dt, *Gt;      // D_W,c and G_odd again, in the tensor-core operand-tile layout
     void *Bt;           // B operand tiles of one application (up to 16 right-hand sides)
@@ -385,6 +387,9 @@ extern "C" tmnd_status tmnd_mg_create(tmnd_gauge *g, const tmnd_mg_params *p, co
     TMND_ARG_CHECK(p->nvec >= 1 && p->nvec <= MG_MAXV, "tmnd_mg_create: nvec = %d not in [1, %d]", p->nvec, MG_MAXV);
     TMND_ARG_CHECK(p->wait_limit_s >= 0 && p->wait_limit_s <= 60 && p->stall_test >= 0,
                    "tmnd_mg_create: wait_limit_s = %g not in [0, 60] or stall_test < 0", p->wait_limit_s);
+    TMND_ARG_CHECK(p->smoother == 0 || (p->smoother == 1 && p->block[0] * p->block[1] * p->block[2] * p->block[3] <= 256),
+                   "tmnd_mg_create: smoother %d (SAP needs blocks of at most 256 sites)", p->smoother);
+    TMND_ARG_CHECK(p->sap_mr >= 0 && p->sap_mr <= 64, "tmnd_mg_create: sap_mr = %d", p->sap_mr);
     for (int i = 0; i < 4; i++)
         TMND_ARG_CHECK(p->block[i] >= 1 && g->act.dims[i] % p->block[i] == 0,
                        "tmnd_mg_create: block[%d] = %d does not divide dims[%d] = %d", i, p->block[i], i,
@@ -404,6 +409,8 @@ extern "C" tmnd_status tmnd_mg_create(tmnd_gauge *g, const tmnd_mg_params *p, co
     mg->tc = p->coarse_simt ? 0 : 1;
     mg->wait_ns = p->wait_limit_s > 0 ? (uint64_t)(p->wait_limit_s * 1e9) : 2000000000ull;
     mg->stall_next = p->stall_test;
+    mg->smoother = p->smoother;
+    mg->sap_mr = p->sap_mr > 0 ? p->sap_mr : 4;
     const double d = p->coarse_mu_factor > 0 ? p->coarse_mu_factor : 1.0;
     mg->mu_c = 2 * g->act.kappa * g->act.mu_bar * d;
     mg->eps_c = 2 * g->act.kappa * g->act.eps_bar;
@@ -607,6 +614,11 @@ size_t tmnd_mg_nblock_nv(const tmnd_mg *mg, int *nv) {
     return (size_t)mg->nblock;
 }
 tmnd_gauge *tmnd_mg_gauge(const tmnd_mg *mg) { return mg->g; }
+void tmnd_mg_smoother(const tmnd_mg *mg, int *kind, int *mr, int bd[4]) {
+    *kind = mg->smoother;
+    *mr = mg->sap_mr;
+    for (int i = 0; i < 4; i++) bd[i] = mg->bd[i];
+}
 extern "C" tmnd_status tmnd_mg_coarse_apply_internal(const tmnd_mg *mg, float2 *out, const float2 *in, double s,
                                                      cudaStream_t st) {
     return mg_coarse_apply(mg, out, in, 1, s, st);

@@ -15,6 +15,9 @@
 
 struct tmnd_mg;  // defined in mg.cu
 size_t tmnd_mg_nblock_nv(const tmnd_mg *mg, int *nv);
+void tmnd_mg_smoother(const tmnd_mg *mg, int *kind, int *mr, int bd[4]);
+tmnd_status launch_sap_color(const tmnd_gauge *g, const int bd[4], int color, double s_odd, const float2 *r,
+                             float2 *x, int mr_iters, cudaStream_t s);
 
 namespace {
 
@@ -221,6 +224,7 @@ struct MGSolver {
     long n;      // fine complex numbers (2 parities x 24 x Vh)
     long nc;     // coarse complex numbers
     int nu_pre, nu_post, coarse_iters;
+    int smoother, sap_mr, bd[4];
     double coarse_tol;
     // fine scratch
     float2 *r1, *t1, *t2, *sm_r, *sm_x;
@@ -231,9 +235,23 @@ struct MGSolver {
         k_dnd_full<<<nblk(n / 24), 256, 0, st>>>(g->geom, g->act.kappa, (float)g->st.kp, (float)g->st.kpp, (float)s,
                                                 g->links, in, out, 2);
     }
-    // MR smoothing on D' x = r, x from 0, nu steps
+    // smoothing of D' x = r from x = 0: nu SAP sweeps (each: per colour the residual of the
+    // whole lattice, then block-local MR on the blocks of that colour), or nu MR steps
     void smooth(const float2 *r, float2 *x, int nu) {
         blas.zero(n, x);
+        if (smoother == 1) {
+            for (int k = 0; k < nu; k++)
+                for (int color = 0; color < 2; color++) {
+                    const float2 *res = r;
+                    if (k > 0 || color > 0) {
+                        apply(x, sm_r);
+                        k_rsub<<<nblk(n), 256, 0, st>>>(n, r, sm_r);  // sm_r = r - D' x
+                        res = sm_r;
+                    }
+                    launch_sap_color(g, bd, color, s, res, x, sap_mr, st);
+                }
+            return;
+        }
         blas.copy(n, r, sm_r);
         for (int k = 0; k < nu; k++) {
             apply(sm_r, t1);
@@ -304,6 +322,7 @@ tmnd_status mg_gcr_solve(tmnd_mg *mg, float2 *x, const float2 *b, double s, doub
     S.nc = (long)nblock * 2 * 2 * nv;
     S.nu_pre = nu;
     S.nu_post = nu;
+    tmnd_mg_smoother(mg, &S.smoother, &S.sap_mr, S.bd);
     S.coarse_iters = 64;
     S.coarse_tol = 0.05;
     const int mr = restart > 16 ? 16 : restart;
@@ -369,6 +388,8 @@ size_t mg_gcr_scratch_bytes(tmnd_mg *mg, int restart) {
 }
 
 tmnd_status tmnd_mg_tc_status(const tmnd_mg *mg);
+extern "C" tmnd_status tmnd_mg_create(tmnd_gauge *g, const tmnd_mg_params *p, const void *test_vectors,
+                                      tmnd_mg **out);
 
 extern "C" tmnd_status tmnd_mg_solve(tmnd_mg *mg, void *x, const void *b, double s, double tol, int maxiter,
                                      int restart, int nu, int *iters, double *res, void *stream) {
@@ -436,4 +457,59 @@ extern "C" tmnd_status tmnd_mg_smooth_vectors(tmnd_gauge *g, void *vecs, int nve
         return TMND_ERR_CUDA;
     }
     return TMND_OK;
+}
+
+// Adaptive (bootstrap) setup: each test vector v is replaced by the flavour-0 part of
+// w ~ D_ND^-1 (v, 0) from `iters` outer iterations of the current two-level method, then
+// normalised, and a new hierarchy is built from the improved vectors.
+extern "C" tmnd_status tmnd_mg_bootstrap(tmnd_mg *mg, const tmnd_mg_params *p, void *test_vectors, int iters,
+                                         tmnd_mg **out, void *stream) {
+    TMND_ARG_CHECK(mg && p && test_vectors && out, "tmnd_mg_bootstrap: NULL argument");
+    TMND_ARG_CHECK(iters >= 1 && iters <= 1000, "tmnd_mg_bootstrap: iters = %d", iters);
+    *out = nullptr;
+    cudaGetLastError();
+    cudaStream_t st = (cudaStream_t)stream;
+    tmnd_gauge *g = tmnd_mg_gauge(mg);
+    int nv = 0;
+    tmnd_mg_nblock_nv(mg, &nv);
+    const long vh = g->geom.Vh, n1 = 2L * 12 * vh, n2 = 2L * 24 * vh;
+    const int restart = 16;
+    const size_t sb = mg_gcr_scratch_bytes(mg, restart);
+    char *buf = nullptr;
+    TMND_CUDA_TRY(cudaMalloc(&buf, sb + 2 * sizeof(float2) * n2 + sizeof(double) * 2 * 1024));
+    float2 *rhs = (float2 *)(buf + sb), *x = rhs + n2;
+    Blas blas;
+    blas.s = st;
+    blas.part = (double *)(x + n2);
+    blas.nb_max = 1024;
+    blas.h.resize(2048);
+    tmnd_status res = TMND_OK;
+    for (int v = 0; v < nv && res == TMND_OK; v++) {
+        float2 *tv = (float2 *)test_vectors + (size_t)v * n1;
+        // (v, 0) in the doublet layout [parity][flavour][12][V/2]
+        cudaMemsetAsync(rhs, 0, sizeof(float2) * n2, st);
+        for (int par = 0; par < 2; par++)
+            cudaMemcpyAsync(rhs + (size_t)par * 24 * vh, tv + (size_t)par * 12 * vh, sizeof(float2) * 12 * vh,
+                            cudaMemcpyDeviceToDevice, st);
+        cudaMemsetAsync(x, 0, sizeof(float2) * n2, st);
+        int it = 0;
+        double rr = 0;
+        res = mg_gcr_solve(mg, x, rhs, 0.0, 1e-12, iters, restart, 2, st, &it, &rr, buf);
+        if (res != TMND_OK) break;
+        for (int par = 0; par < 2; par++)
+            cudaMemcpyAsync(tv + (size_t)par * 12 * vh, x + (size_t)par * 24 * vh, sizeof(float2) * 12 * vh,
+                            cudaMemcpyDeviceToDevice, st);
+        const double nn = blas.norm2(n1, tv);
+        if (nn > 0 && isfinite(nn)) blas.scale(n1, 1.0 / sqrt(nn), tv, tv);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (res != TMND_OK) return res;
+    if (e != cudaSuccess) {
+        tmnd_set_error("tmnd_mg_bootstrap: %s", cudaGetErrorString(e));
+        return TMND_ERR_CUDA;
+    }
+    const tmnd_status tc = tmnd_mg_tc_status(mg);
+    if (tc != TMND_OK) return tc;
+    return tmnd_mg_create(g, p, test_vectors, out);
 }

@@ -18,8 +18,9 @@ from test_gpu_mg import from_mg_layout, to_mg_layout
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("s", [0.05, -0.05])
-def test_mg_solve_case_c(s):
+@pytest.mark.parametrize("s,smoother", [(0.05, 0), (-0.05, 0), (0.05, 1), (-0.05, 1)])
+def test_mg_solve_case_c(s, smoother):
+    """smoother 0: minimal residual on the whole lattice; 1: SAP on the 2^4 aggregation blocks."""
     tm = require_gpu()
     dims, bdims, nv = (8, 4, 4, 4), (2, 2, 2, 2), 6
     V = int(np.prod(dims))
@@ -30,7 +31,7 @@ def test_mg_solve_case_c(s):
     tv = rng.standard_normal((nv, V, 12)) + 1j * rng.standard_normal((nv, V, 12))
     tvd = torch.from_numpy(to_mg_layout(dims, tv.astype(np.complex64), 12)).cuda().contiguous()
     tm.tmnd_mg_smooth_vectors(g.handle, tvd, nv, 6)
-    mg = tm.tmnd_mg_create(g.handle, bdims, nv, tvd)
+    mg = tm.tmnd_mg_create(g.handle, bdims, nv, tvd, smoother=smoother)
     b = synth.gaussian_rhs(dims, 5)[0]                      # odd-site doublet [V/2, 2, 4, 3]
     g5t1 = (b[:, ::-1] * np.array([1, 1, -1, -1])[None, None, :, None])
     rhs = np.zeros((V, 2, 4, 3), np.complex128)
@@ -69,4 +70,39 @@ def test_full_operator_matches_oracle():
         got = from_mg_layout(dims, out.cpu().numpy().reshape(2, 24, V // 2), 24)
         ref = oracle.dnd_odd_shift(act, U, v.reshape(V, 2, 4, 3), s).reshape(V, 24)
         assert np.max(np.abs(got - ref)) < 2e-6 * np.abs(ref).max()
+    g.close()
+
+
+def test_bootstrap_setup_then_case_c_certified():
+    """Adaptive setup (tmnd_mg_bootstrap: test vectors improved by the two-level method itself,
+    SAP smoothing), then a case-C solve with the new hierarchy, certified by the oracle as above."""
+    tm = require_gpu()
+    dims, bdims, nv, s = (8, 4, 4, 4), (2, 2, 2, 2), 6, 0.05
+    V = int(np.prod(dims))
+    U = synth.random_su3_field(dims, 0.5, 31)
+    g = tm.Gauge(U, dims, KAPPA, MU, EPS)
+    act = oracle.action(dims, KAPPA, MU, EPS)
+    rng = np.random.default_rng(1)
+    tv = rng.standard_normal((nv, V, 12)) + 1j * rng.standard_normal((nv, V, 12))
+    tvd = torch.from_numpy(to_mg_layout(dims, tv.astype(np.complex64), 12)).cuda().contiguous()
+    tm.tmnd_mg_smooth_vectors(g.handle, tvd, nv, 6)
+    mg0 = tm.tmnd_mg_create(g.handle, bdims, nv, tvd, smoother=1)
+    mg1 = tm.tmnd_mg_bootstrap(mg0, tvd, 3, bdims, nv, smoother=1)
+    assert torch.isfinite(torch.view_as_real(tvd)).all()
+    b = synth.gaussian_rhs(dims, 5)[0]
+    g5t1 = (b[:, ::-1] * np.array([1, 1, -1, -1])[None, None, :, None])
+    rhs = np.zeros((V, 2, 4, 3), np.complex128)
+    rhs[synth.odd_sites(dims)] = g5t1
+    rd = torch.from_numpy(to_mg_layout(dims, rhs.reshape(V, 24).astype(np.complex64), 24)).cuda().contiguous()
+    its = []
+    for mg in (mg0, mg1):
+        x = torch.zeros_like(rd)
+        info = tm.tmnd_mg_solve(mg, x, rd, s, tol=1e-4, maxiter=300, restart=8, nu=2)
+        xs = from_mg_layout(dims, x.cpu().numpy().reshape(2, 24, V // 2), 24).reshape(V, 2, 4, 3)
+        r = rhs - oracle.dnd_odd_shift(act, U, xs, s)
+        assert np.linalg.norm(r) / np.linalg.norm(rhs) < 2e-4, info
+        its.append(info["iters"])
+    assert its[1] <= its[0] + 5, its
+    tm.tmnd_mg_destroy(mg1)
+    tm.tmnd_mg_destroy(mg0)
     g.close()
