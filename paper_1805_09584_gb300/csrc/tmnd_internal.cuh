@@ -260,7 +260,8 @@ struct S16Batch {
     size_t stride = 0;
     const int *rdone = nullptr;
     int rdone_stride = 0;
-    int shape = -1;  // compiled launch shape (dslash_s16.cu); -1: the autotuner's choice for (lattice, nrhs)
+    int shape = -1;  // launch variant (dslash_s16.cu); -1: the autotuner's choice for (lattice, nrhs)
+    int rhs_outer = 0;  // set by the launchers from the variant: loop over right-hand sides outside the sites
 };
 
 // launch shapes of the 16-bit stencil and their autotuner (dslash_s16.cu)

@@ -79,9 +79,9 @@ def test_s16_shape_table_host(tm):
     """The compiled launch shapes of the 16-bit stencil (host queries, no GPU needed)."""
     seen = set()
     for sh in range(tm.S16_SHAPES):
-        t, b, pf = tm.tmnd_s16_shape_info(sh)
+        t, b, pf, ro = tm.tmnd_s16_shape_info(sh)
         assert t % 32 == 0 and 1 <= b <= 8 and t * b <= 1024
-        seen.add((t, b, pf))
+        seen.add((t, b, pf, ro))
     assert len(seen) == tm.S16_SHAPES
     with pytest.raises(tm.TmndError):
         tm.tmnd_s16_shape_info(tm.S16_SHAPES)

@@ -45,15 +45,16 @@ def test_noalloc_matches_tm_nd_apply(dims):
 def test_noalloc_allocates_nothing():
     """The defining property: a handle that has never run tm_nd_apply (so its workspace
     was never grown) applies the operator through tm_nd_apply_noalloc without any change
-    in the device's free memory.  A warm-up call on another handle first loads the library's
-    module (which places the fixed array) and looks up the array's address."""
+    in the device's free memory.  Warm-up calls on another handle first load the library's
+    kernels (module loading places the fixed array) and look up the array's address."""
     tm = require_gpu()
     dims = (8, 8, 8, 8)
     U = synth.random_su3_field(dims, 0.5, 4243)
     warm = tm.Gauge(U, dims, KAPPA, MU, EPS)
     b = warm.pack(torch.from_numpy(synth.gaussian_rhs(dims, 18)).cuda())
     o = warm.spinor()
-    tm.tm_nd_apply_noalloc(warm.handle, o, b, tm.OP_QHAT2, 0.02)
+    for op in (tm.OP_MHAT, tm.OP_MHAT_DAG, tm.OP_QHAT2, tm.OP_QHAT):  # every kernel loaded once
+        tm.tm_nd_apply_noalloc(warm.handle, o, b, op, 0.02)
     fresh = tm.Gauge(U, dims, KAPPA, MU, EPS)
     out = fresh.spinor()
     torch.cuda.synchronize()
