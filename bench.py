@@ -475,8 +475,9 @@ def run_form(args):
                                     "fp64_applies": infos[-1]["fp64_applies"]}
     # solver statistics of the last timed step
     last = infos[-1]
-    stats = {k: last[k] for k in ("iters", "mms_iters", "refine_iters", "fp64_applies", "refine_rounds", "mg_iters",
-                                  "guess_res", "lag_nodes") if k in last}
+    stats = {k: last[k] for k in ("iters", "mms_iters", "refine_iters", "fp64_applies", "f32_applies",
+                                  "refine_rounds", "mg_iters", "guess_res", "lag_nodes", "phase_ms", "mms_ms",
+                                  "shift_ms") if k in last}
     # e2e: host buffers in and out through the public API: the canonical right-hand sides
     # from pinned host memory, packed, solved, and every shift's solutions unpacked and read
     # back into pinned host memory (one buffer, reused shift by shift)

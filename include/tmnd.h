@@ -248,6 +248,10 @@ typedef struct {
                                               defect correction, summed over RHS) */
     int f32_applies;                       /* TMND_S16: FP32 applications of Qhat^2 + sigma (the inner
                                               residuals of the defect correction) */
+    double mms_ms;                         /* TMND_S16: wall time of the sloppy multi-shift solves */
+    double fp64_ms;                        /* TMND_S16: wall time of the FP64 defects (true residuals) */
+    double refine_ms;                      /* TMND_S16: wall time of the rest of the defect correction
+                                              (sloppy corrections, FP32 residuals, FP64 updates) */
 } tmnd_solve_info;
 
 /* Multi-mass-shift CG (Sec. 1 "standard" solver; Sec. 4.2.2) for
@@ -415,7 +419,9 @@ typedef struct {
                               over the solutions of the 8 shifts just above (n_mms >= 8; the
                               network's features use the first RHS's base-recursion history) */
     double mg_tol;         /* relative tolerance of each case-C MG solve (0 = 1e-4; the solve is
-                              FP32, the FP64 defect correction finishes the shift) */
+                              FP32, the FP64 defect correction finishes the shift).  A shift whose
+                              guess (RHS 0) already has an FP64 relative residual <= mg_tol skips
+                              the multigrid for all its RHS */
     int mg_maxiter, mg_restart, mg_nu;   /* 0 = 100, 24, 4 (GCR(8) stagnates on the indefinite
                                             full-lattice operator at small shifts) */
     const struct tmnd_mlp *net;          /* guess = 2: a trained network (see tmnd_mlp_*), else NULL */

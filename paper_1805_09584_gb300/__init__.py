@@ -89,7 +89,8 @@ class SolveInfo(ctypes.Structure):
                 ("true_res", ctypes.c_double * MAX_SHIFTS), ("zeta", ctypes.c_double * MAX_SHIFTS),
                 ("hop_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("launches", ctypes.c_longlong),
                 ("refine_rounds", ctypes.c_int), ("refine_iters", ctypes.c_int), ("fp64_applies", ctypes.c_int),
-                ("f32_applies", ctypes.c_int)]
+                ("f32_applies", ctypes.c_int), ("mms_ms", ctypes.c_double), ("fp64_ms", ctypes.c_double),
+                ("refine_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -281,7 +282,8 @@ def mms_cg_solve(h, b, nrhs: int, sigma, x, rho: float = 1e-10, maxiter: int = 1
            "true_res": list(info.true_res[:ns]), "zeta": list(info.zeta[:ns]),
            "hop_ms": info.hop_ms, "update_ms": info.update_ms, "launches": info.launches,
            "refine_rounds": info.refine_rounds, "refine_iters": info.refine_iters,
-           "fp64_applies": info.fp64_applies, "f32_applies": info.f32_applies}
+           "fp64_applies": info.fp64_applies, "f32_applies": info.f32_applies,
+           "phase_ms": {"multi_shift": info.mms_ms, "fp64_defects": info.fp64_ms, "refinement": info.refine_ms}}
     _check(st)
     return out
 

@@ -1012,7 +1012,13 @@ struct RefineStats {
     int fp64 = 0, rounds = 0, iters = 0, f32 = 0;
     long long launches = 0;
     double hop_ms = 0, upd_ms = 0;
+    double fp64_ms = 0;  // wall time of the FP64 defects (each ends with a host read)
 };
+
+// wall-clock milliseconds since t0
+static double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
 
 // FP64 defect correction (Sec. 3.1 stopping rule on the true residual) of a set of
 // (right-hand side, shift) pairs: per round, each pending pair's defect
@@ -1176,8 +1182,11 @@ static tmnd_status defect_correct(tmnd_gauge *g, void *base, std::vector<DCItem>
             for (; q < todo.size() && (int)chunk.size() < max_batch; q++) {
                 DCItem &it = todo[q];
                 double rr = 0;
+                TMND_CUDA_TRY(cudaStreamSynchronize(s));
+                const auto t_f = std::chrono::steady_clock::now();
                 st = fp64_defect(g, mw, it.b, it.x, it.sigma, s, &rr);
                 if (st != TMND_OK) return st;
+                rs.fp64_ms += ms_since(t_f);  // fp64_defect ends with a host read of its partials
                 rs.fp64++;
                 rs.launches += 5;
                 *it.res = sqrt(rr / it.bb);
@@ -1257,6 +1266,8 @@ static tmnd_status mixed_batch(tmnd_gauge *g, const double2 *b, double2 *const *
     // 1. batched sloppy multi-shift CG (a zero right-hand side is done at once)
     std::vector<MMSState> hs;
     LoopOut lo;
+    TMND_CUDA_TRY(cudaStreamSynchronize(s));
+    const auto t_mms = std::chrono::steady_clock::now();
     st = mms_sloppy(g, m, sigma, nshift, nsolve, rho_inner, maxiter, check_every, profile, s, hs, lo,
                     k0 == 0 ? hist : nullptr, hist_cap);
     if (st != TMND_OK) return st;
@@ -1297,7 +1308,9 @@ static tmnd_status mixed_batch(tmnd_gauge *g, const double2 *b, double2 *const *
             items.push_back(DCItem{b + (size_t)rhs * n, xk[i], sigma[i], bb[k], &res[k][i]});
     }
     // 2. FP64 defect correction of every (RHS, shift) pair that must converge, batched
+    const double mms_ms = ms_since(t_mms);  // the multi-shift solve ends with host reads of its state
     RefineStats rs;
+    const auto t_dc = std::chrono::steady_clock::now();
     st = defect_correct(g, g->work, items, rho, rho_inner, maxiter, check_every, profile, s, rs,
                         refine_batch(R, nsolve));
     if (st != TMND_OK && st != TMND_ERR_NOCONV) return st;
@@ -1313,6 +1326,10 @@ static tmnd_status mixed_batch(tmnd_gauge *g, const double2 *b, double2 *const *
             for (int i = 0; i < nshift; i++)
                 if (k0 + k == 0 || res[k][i] > info->true_res[i]) info->true_res[i] = res[k][i];
     if (info) {
+        cudaStreamSynchronize(s);
+        info->mms_ms += mms_ms;
+        info->fp64_ms += rs.fp64_ms;
+        info->refine_ms += ms_since(t_dc) - rs.fp64_ms;
         info->fp64_applies += fp64;
         info->f32_applies += rs.f32;
         info->refine_iters += riters;
@@ -1565,6 +1582,8 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
     for (int i = n_mms; i < nshift && res_status == TMND_OK; i++) {
         const auto t_shift = std::chrono::steady_clock::now();
         const double sq = sqrt(sigma[i]);
+        const double mg_tol = hp->mg_tol > 0 ? hp->mg_tol : 1e-4;
+        bool mg_shift = mg != nullptr;
         std::vector<double> res(nrhs, 0.0), res0(nrhs, 0.0);
         std::vector<DCItem> items;
         for (int k = 0; k < nrhs && res_status == TMND_OK; k++) {
@@ -1606,16 +1625,21 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
                 }
             }
             int mg_it = 0;
-            if (mg) {
-                if (k == 0) {  // the guess's FP64 residual (RHS 0), before the multigrid
-                    double rr0 = 0;
-                    st = fp64_defect(g, m, bk, xk[i], sigma[i], s, &rr0);
-                    if (st != TMND_OK) { res_status = st; break; }
-                    if (hinfo) {
-                        hinfo->guess_res[i] = bbk[0] > 0 ? sqrt(rr0 / bbk[0]) : 0.0;
-                        hinfo->fp64_applies += 1;
-                    }
+            if (mg && k == 0) {  // the guess's FP64 residual (RHS 0), before the multigrid
+                double rr0 = 0;
+                st = fp64_defect(g, m, bk, xk[i], sigma[i], s, &rr0);
+                if (st != TMND_OK) { res_status = st; break; }
+                const double gr = bbk[k] > 0 ? sqrt(rr0 / bbk[k]) : 0.0;
+                // the multigrid solves a case-C system to mg_tol of |b|; a guess already below that
+                // (on RHS 0, taken for every RHS of the shift) leaves it nothing to do: the case-C
+                // set-up is skipped and the defect correction starts from the guess
+                mg_shift = gr > mg_tol;
+                if (hinfo) {
+                    hinfo->guess_res[i] = gr;
+                    hinfo->fp64_applies += 1;
                 }
+            }
+            if (mg && mg_shift) {
                 // case-C right-hand side (0, gamma_5 tau_1 b) in FP32 full layout (parity 0 even, 1 odd)
                 k_g5tau1<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Vh, bk, gb);
                 cudaMemsetAsync(rhs, 0, sizeof(float2) * n, s);
@@ -1634,8 +1658,7 @@ extern "C" tmnd_status tmnd_hybrid_solve(tmnd_gauge *g, tmnd_mg *mg, const void 
                     k_to_f32_scaled<<<nbs, 256, 0, s>>>(n, 1.0, gb, y + n);
                     int it = 0;
                     double rres = 0;
-                    const double tol = hp->mg_tol > 0 ? hp->mg_tol : 1e-4;
-                    st = mg_gcr_solve(mg, y, rhs, sgn * sq, tol, hp->mg_maxiter > 0 ? hp->mg_maxiter : 100,
+                    st = mg_gcr_solve(mg, y, rhs, sgn * sq, mg_tol, hp->mg_maxiter > 0 ? hp->mg_maxiter : 100,
                                       hp->mg_restart > 0 ? hp->mg_restart : 24, hp->mg_nu > 0 ? hp->mg_nu : 4, s, &it,
                                       &rres, gcr);
                     if (st != TMND_OK) { res_status = st; break; }
