@@ -49,6 +49,7 @@ between applications) and prints its achieved rate against the roofline:
   fp64    FP64 Qhat^2 + sigma (4 stencil launches), 16^3x32
   s16     16-bit Qhat^2 + sigma (4 stencil launches), 24^3x48 (1 and 8 RHS per launch)
           and 32^3x64 (1 and 8 RHS)
+  f32     FP32-operator Qhat^2 + sigma (4 launches), 24^3x48 and 32^3x64
   coarse  coarse doublet operator, tensor cores and CUDA cores, 24^3x48 with 4^4
           aggregates and 24 vectors per chirality, 1 and 8 RHS
 
@@ -98,6 +99,9 @@ FP64_TRAFFIC_VH = 65536
 # 2 odd launches and the sigma term's 100; with R right-hand sides per launch the links
 # (4 x 192) are read once: R (2 (200 + 300) + 100) + 4 x 192 bytes per odd site
 S16_SPINOR_BYTES_PER_SITE = 2 * (200 + 300) + 100
+# FP32 operator (FP32 planes, 18-real FP32 links), per odd site per Qhat^2 + sigma: even launch
+# 192 + 8 x 72 + 192, odd launch + psi 192, the sigma term's 192
+F32_Q2_BYTES_PER_SITE = 2 * ((192 + 576 + 192) + (192 + 192 + 576 + 192)) + 192
 S16_LINK_BYTES_PER_SITE = 4 * 192
 # DRAM bytes (read + write) of one 16-bit Qhat^2 + sigma, one ncu capture of its 4 launches:
 # {(lattice V/2, RHS per launch): bytes}
@@ -200,7 +204,7 @@ def count_kernels(fn, prefix=("k_",)):
             torch.cuda.synchronize()
         n, names = 0, {}
         for ev in prof.events():
-            nm = ev.name or ""
+            nm = (ev.name or "").replace("(anonymous namespace)::", "")
             dev = str(getattr(ev, "device_type", ""))
             base = nm.split("(")[0].split("<")[0].split(" ")[-1]
             if "CUDA" in dev and any(base.startswith(p) for p in prefix):
@@ -608,6 +612,22 @@ def run_kernel(args):
         tf = 4 * HOP_FLOP_PER_SITE * g.vh / (ms / 1e3) / 1e12
         out.update(lattice="16^3x32", ms_qhat2=ms, tflops=tf, fp64_peak_tflops=FP64_PEAK_TFLOPS,
                    frac=tf / FP64_PEAK_TFLOPS, gbs=4 * HOP_BYTES_PER_SITE * g.vh / (ms / 1e3) / 1e9)
+    elif args.kernel == "f32":
+        for dims, name in (((48, 24, 24, 24), "24^3x48"), ((64, 32, 32, 32), "32^3x64")):
+            g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
+            b = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, 2003)).cuda())
+            q = g.convert(b, tm.TMND_F64, tm.TMND_F32)
+            o = g.spinor(prec=tm.TMND_F32)
+            del b
+            ms = timed(lambda: tm.tm_nd_apply(g.handle, o, q, tm.OP_QHAT2 | tm.OP_F32, 0.01, stream=stream))
+            byts = g.vh * F32_Q2_BYTES_PER_SITE
+            out[f"{name}"] = {"ms_qhat2": ms, "gbs": byts / (ms / 1e3) / 1e9,
+                              "frac_hbm": byts / (ms / 1e3) / 1e9 / peak_hbm,
+                              "tflops": 4 * HOP_FLOP_PER_SITE * g.vh / (ms / 1e3) / 1e12}
+            del q, o
+            g.close()
+        out.update(hbm_peak_gbs=peak_hbm, bytes_per_site=F32_Q2_BYTES_PER_SITE)
+        return out
     elif args.kernel == "s16":
         for dims, name, rs in (((48, 24, 24, 24), "24^3x48", (1, 8)), ((64, 32, 32, 32), "32^3x64", (1, 8))):
             g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
@@ -1013,7 +1033,7 @@ def main():
     ap.add_argument("--impl", default="tmnd", choices=["tmnd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="hybrid", choices=list(FORMS))
-    ap.add_argument("--kernel", default=None, choices=["fp64", "s16", "coarse"])
+    ap.add_argument("--kernel", default=None, choices=["fp64", "s16", "f32", "coarse"])
     ap.add_argument("--study", default=None, choices=["hybrid", "learned", "errors", "mg"])
     args = ap.parse_args()
     if args.study:
