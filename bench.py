@@ -397,7 +397,8 @@ def run_form(args):
             per[R] = {"shape": sh, "ms": [round(float(v), 4) for v in tms]}
         extra["autotune"] = {"shapes": [tm.tmnd_s16_shape_info(i) for i in range(tm.S16_SHAPES)],
                              "shape_fields": ["threads per block", "blocks per SM", "next-direction prefetch",
-                                              "right-hand sides outside the sites"],
+                                              "loop order (0 chunk, sites outside; 1 chunk, RHS outside; "
+                                              "2 grid stride, sites outside)"],
                              "per_nrhs": per, "s": time.perf_counter() - t0}
     if args.form == "hybrid":
         t0 = time.perf_counter()

@@ -27,10 +27,12 @@ constexpr ShapeDesc kShapes[] = {
 #undef TMND_S16_DESC
 };
 constexpr int NCOMPILED = sizeof(kShapes) / sizeof(kShapes[0]);
-// a launch variant = compiled shape (v % NCOMPILED) x loop order over right-hand sides
-// (v / NCOMPILED: 0 = all right-hand sides of a site in turn, 1 = one right-hand side
-// over the whole chunk after another)
-constexpr int NSHAPES = 2 * NCOMPILED;
+// a launch variant = compiled shape (v % NCOMPILED) x loop order (v / NCOMPILED): 0 = every
+// block walks its own chunk of sites, all right-hand sides of a site in turn; 1 = the same
+// chunk once per right-hand side; 2 = all blocks sweep the lattice together (grid stride),
+// all right-hand sides of a site in turn
+constexpr int NORDERS = 3;
+constexpr int NSHAPES = NORDERS * NCOMPILED;
 static_assert(NSHAPES == TMND_S16_SHAPES, "variant count of include/tmnd.h");
 
 // resident blocks per SM of each shape, per device (the smaller of the even and odd kernels')
@@ -111,7 +113,7 @@ void launch_hop_even_s16(const Geom &g, const SiteTermF &st, const int2 *links, 
                          const int *done, cudaStream_t s, const S16Batch &bt_in) {
     const int shape = bt_in.shape >= 0 ? bt_in.shape : s16_shape(g, bt_in.nrhs);
     S16Batch bt = bt_in;
-    bt.rhs_outer = shape >= NCOMPILED;
+    bt.order = shape / NCOMPILED;
     const int nb = hop_blocks_s16(g, shape);
     switch (shape % NCOMPILED) {
 #define TMND_S16_EVEN(I, T, B, P) \
@@ -127,7 +129,7 @@ void launch_hop_odd_s16(const Geom &g, const SiteTermF &st, const int2 *links, S
                         bool dag, HopEpi epi, const S16EpiArgs &ea, cudaStream_t s, const S16Batch &bt_in) {
     const int shape = bt_in.shape >= 0 ? bt_in.shape : s16_shape(g, bt_in.nrhs);
     S16Batch bt = bt_in;
-    bt.rhs_outer = shape >= NCOMPILED;
+    bt.order = shape / NCOMPILED;
     const int nb = hop_blocks_s16(g, shape);
     switch (shape % NCOMPILED) {
 #define TMND_S16_ODD(I, T, B, P) \
@@ -181,7 +183,7 @@ tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out
     int choice = 0;
     cudaError_t err = cudaSuccess;
     for (int sh = 0; sh < NSHAPES && err == cudaSuccess; sh++) {
-        if (nrhs == 1 && sh >= NCOMPILED) {  // one right-hand side: both loop orders are the same launch
+        if (nrhs == 1 && sh / NCOMPILED == 1) {  // one right-hand side: orders 0 and 1 are the same launch
             best[sh] = best[sh - NCOMPILED];
             continue;
         }
@@ -248,12 +250,12 @@ extern "C" tmnd_status tmnd_s16_force_shape(int shape) {
 }
 
 extern "C" tmnd_status tmnd_s16_shape_info(int shape, int *threads, int *blocks_per_sm, int *prefetch,
-                                           int *rhs_outer) {
+                                           int *order) {
     TMND_ARG_CHECK(shape >= 0 && shape < NSHAPES, "tmnd_s16_shape_info: shape %d not in [0, %d)", shape, NSHAPES);
     const ShapeDesc &d = kShapes[shape % NCOMPILED];
     if (threads) *threads = d.threads;
     if (blocks_per_sm) *blocks_per_sm = d.minb;
     if (prefetch) *prefetch = d.pf;
-    if (rhs_outer) *rhs_outer = shape >= NCOMPILED;
+    if (order) *order = shape / NCOMPILED;
     return TMND_OK;
 }

@@ -133,7 +133,14 @@ __global__ void __launch_bounds__(NT, MB) k_hop_even_s16(Geom g, SiteTermF st, c
         const S16Out ok = s16_at(out, k * bt.stride);
         store_site(ok.q, ok.nrm, g.Vh, h, o);
     };
-    if (bt.rhs_outer) {  // each right-hand side over the block's chunk, one after another
+    if (bt.order == 2) {  // grid-stride sweep: all blocks move through the lattice together, so
+                          // every right-hand side's neighbours stay in L2 while the band passes
+        for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x)
+            for (int k = 0; k < bt.nrhs; k++) {
+                if (bt.rdone && bt.rdone[k * bt.rdone_stride]) continue;
+                site(h, k);
+            }
+    } else if (bt.order == 1) {  // each right-hand side over the block's chunk, one after another
         for (int k = 0; k < bt.nrhs; k++) {
             if (bt.rdone && bt.rdone[k * bt.rdone_stride]) continue;
             for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) site(h, k);
@@ -199,7 +206,13 @@ __global__ void __launch_bounds__(NT, MB) k_hop_odd_s16(Geom g, SiteTermF st, co
             part[k * blockDim.x + threadIdx.x] += s1;
         }
     };
-    if (bt.rhs_outer) {
+    if (bt.order == 2) {
+        for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x)
+            for (int k = 0; k < bt.nrhs; k++) {
+                if (bt.rdone && bt.rdone[k * bt.rdone_stride]) continue;
+                site(h, k);
+            }
+    } else if (bt.order == 1) {
         for (int k = 0; k < bt.nrhs; k++) {
             if (bt.rdone && bt.rdone[k * bt.rdone_stride]) continue;
             for (int h = blockIdx.x * chunk + threadIdx.x; h < h_end; h += blockDim.x) site(h, k);
