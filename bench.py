@@ -478,13 +478,14 @@ def run_form(args):
                                      "fp64_applies": inf_l[-1]["fp64_applies"]}
         extra["learned_guesses"] = {"guess_res": infos[-1]["guess_res"][8:], "refine_iters": infos[-1]["refine_iters"],
                                     "fp64_applies": infos[-1]["fp64_applies"]}
-    if args.form == "batched":   # the same solve with one RHS per sloppy launch (batching's gain)
+    if args.form == "batched":   # the same solve one RHS at a time (batching's gain): the multi-shift
+        # solve of each RHS alone, its defect corrections batched over its own 12 shifts only
         def step_one():
             return tm.mms_cg_solve(g.handle, b_dev, nrhs, sig, xs, rho=RHO, prec=tm.TMND_S16, batch=1,
                                    stream=stream)
         step_one()
         ms_1, _ = _timed(step_one, 1, flush, stream)
-        extra["one_rhs_per_launch"] = {"value": len(sig) * nrhs / (ms_1 / 1e3), "ms_per_step": ms_1}
+        extra["one_rhs_at_a_time"] = {"value": len(sig) * nrhs / (ms_1 / 1e3), "ms_per_step": ms_1}
     # solver statistics of the last timed step
     last = infos[-1]
     stats = {k: last[k] for k in ("iters", "mms_iters", "refine_iters", "fp64_applies", "f32_applies",
