@@ -188,7 +188,8 @@ tmnd_status tm_nd_apply_noalloc(const tmnd_gauge *g, void *out, const void *in, 
  * CUDA events, best of 3 after a warm-up -- and keeps the fastest for the rest of the
  * process.  This happens on the first 16-bit tm_nd_apply or sloppy solve of that pair
  * (skipped while the stream is being captured: the default shape 0 is used then), or here,
- * ahead of time.  Synchronous; allocates its scratch for the call.
+ * ahead of time.  Synchronous; allocates its scratch for the call (if that allocation fails,
+ * the default variant 0 is kept for the pair and its times are reported as 0).
  *   shape_out : receives the chosen shape (may be NULL)
  *   ms_out    : TMND_S16_SHAPES doubles, each shape's time in ms (may be NULL) */
 #define TMND_S16_SHAPES 12

@@ -169,7 +169,17 @@ tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out
     const size_t sb = spinor_bytes_prec(Vh, TMND_S16);
     const size_t part_b = sizeof(double) * 2 * (size_t)nrhs * hop_blocks_s16_max(g->geom);
     char *buf = nullptr;
-    TMND_CUDA_TRY(cudaMalloc(&buf, 3 * (size_t)nrhs * sb + part_b + 256));
+    if (cudaMalloc(&buf, 3 * (size_t)nrhs * sb + part_b + 256) != cudaSuccess) {
+        // no room for the scratch: keep the default shape for this pair (tuning is an optimisation)
+        cudaGetLastError();
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tuned[key] = 0;
+        g_tune_ms[key].fill(0.0f);
+        if (shape_out) *shape_out = 0;
+        if (ms_out)
+            for (int i = 0; i < NSHAPES; i++) ms_out[i] = 0.0f;
+        return TMND_OK;
+    }
     // biased 16-bit words of 0x4000 and unit scales: finite, data-independent timing
     cudaMemsetAsync(buf, 0x40, 3 * (size_t)nrhs * sb, s);
     const S16In in = s16_in(buf, Vh);
