@@ -303,31 +303,47 @@ __device__ __forceinline__ void add_shift(const Site &aux, float sigma, f2 y[4][
     }
 }
 
-// w = y + sigma aux; r' = r - alpha w on the FP32 residual planes (component c of
-// site h at c * Vh + h); returns the site's |r'|^2
-template <class Site>
-__device__ __forceinline__ float mms_r_update(const Site &aux, float sigma, float alpha, const float2 *rin,
-                                              float2 *rout, int Vh, int h, const f2 y[4][3][2]) {
+// The odd site term fused with the multi-shift residual update, one 16-byte plane of the
+// site at a time (4 components, both flavours): p decoded from psi, y = A p - H t (odd_term's
+// arithmetic per component), w = y + sigma aux, r' = r - alpha w; returns the site's |r'|^2.
+// Plane by plane, so that p, y and w of the whole site are never live at once.
+template <bool DAG, class Site>
+__device__ __forceinline__ float odd_mms_r_fused(const SiteTermF &st, const f2 acc[4][3][2], const Site &psi,
+                                                 const Site &aux, float sigma, float alpha, const float2 *rin,
+                                                 float2 *rout, int Vh, int h) {
+    const float kp = DAG ? -st.kp : st.kp;
+    const f2 sc2 = dup(psi.s()), nb2 = dup(-S16_DEC_BIAS);
     const float sa = sigma * aux.s();
     float s1 = 0.0f;
 #pragma unroll
-    for (int f = 0; f < 2; f++)
+    for (int j = 0; j < 3; j++) {
+        const int4 p0 = psi.w(j), p1 = psi.w(3 + j), a0 = aux.w(j), a1 = aux.w(3 + j);
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            const int4 aw = aux.w(f * 3 + j);
+        for (int m = 0; m < 4; m++) {
+            const int kk = 4 * j + m, sp = kk / 3, c = kk % 3;
+            const int w0 = word(p0, m), w1 = word(p1, m);
+            const f2 pr = mul2(add2(make_float2(s16_flo(w0), s16_flo(w1)), nb2), sc2);
+            const f2 pi = mul2(add2(make_float2(s16_fhi(w0), s16_fhi(w1)), nb2), sc2);
+            const float b = kp * (sp < 2 ? 1.0f : -1.0f);
+            f2 hr = acc[sp][c][0], hi = acc[sp][c][1];
+            if (DAG && sp >= 2) { hr = mul2(hr, dup(-1.0f)); hi = mul2(hi, dup(-1.0f)); }
+            const f2 yr = make_float2(fmaf(-b, pi.x, fmaf(-st.kpp, pr.y, pr.x - hr.x)),
+                                      fmaf(b, pi.y, fmaf(-st.kpp, pr.x, pr.y - hr.y)));
+            const f2 yi = make_float2(fmaf(b, pr.x, fmaf(-st.kpp, pi.y, pi.x - hi.x)),
+                                      fmaf(-b, pr.y, fmaf(-st.kpp, pi.x, pi.y - hi.y)));
 #pragma unroll
-            for (int m = 0; m < 4; m++) {
-                const int kk = 4 * j + m, s = kk / 3, c = kk % 3;
+            for (int f = 0; f < 2; f++) {
                 const size_t i = (size_t)(f * 12 + kk) * Vh + h;
-                const float2 rv = rin[i];
-                const float yr = f ? y[s][c][0].y : y[s][c][0].x, yi = f ? y[s][c][1].y : y[s][c][1].x;
-                const float wx = fmaf(sa, s16_lo(word(aw, m)), yr);
-                const float wy = fmaf(sa, s16_hi(word(aw, m)), yi);
+                const float2 rv = __ldcs(rin + i);  // touched once per launch: evict first
+                const int aw = word(f ? a1 : a0, m);
+                const float wx = fmaf(sa, s16_lo(aw), f ? yr.y : yr.x);
+                const float wy = fmaf(sa, s16_hi(aw), f ? yi.y : yi.x);
                 const float2 rn = make_float2(fmaf(-alpha, wx, rv.x), fmaf(-alpha, wy, rv.y));
-                rout[i] = rn;
+                __stcs(rout + i, rn);
                 s1 = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, s1));
             }
         }
+    }
     return s1;
 }
 

@@ -183,6 +183,15 @@ __global__ void __launch_bounds__(NT, MB) k_hop_odd_s16(Geom g, SiteTermF st, co
         const S16Out out = s16_at(out_all, k * bt.stride);
         f2 acc[4][3][2];
         hop_all<1, false, PF>(g, links, te.q, te.nrm, h, acc);
+        if constexpr (EPI == EPI_MMS_R) {  // w = y + sigma aux; r' = r - alpha w (FP32 planes), plane by plane
+            const S16In aux = s16_at(ea.aux, k * bt.stride);
+            const float sg = (float)(ea.per_rhs_sigma ? ea.sigma_k[k] : ea.sigma);
+            const float s1 = odd_mms_r_fused<DAG>(st, acc, GSite{psi.q, psi.nrm, h}, GSite{aux.q, aux.nrm, h}, sg,
+                                                  alpha_s[k], ea.r_in + k * ea.r_stride, ea.r + k * ea.r_stride, Vh,
+                                                  h);
+            part[k * blockDim.x + threadIdx.x] += s1;
+            return;
+        }
         f2 p[4][3][2];
         load_site(GSite{psi.q, psi.nrm, h}, p);
         f2 y[4][3][2];
@@ -194,16 +203,10 @@ __global__ void __launch_bounds__(NT, MB) k_hop_odd_s16(Geom g, SiteTermF st, co
                 part[k * blockDim.x + threadIdx.x] += s1;
                 part[(bt.nrhs + k) * blockDim.x + threadIdx.x] += s2;
             }
-        } else if (EPI == EPI_SHIFT) {  // y + sigma aux
+        } else {  // EPI_SHIFT: y + sigma aux
             const S16In aux = s16_at(ea.aux, k * bt.stride);
             add_shift(GSite{aux.q, aux.nrm, h}, (float)ea.sigma, y);
             store_site(out.q, out.nrm, Vh, h, y);
-        } else {  // EPI_MMS_R: w = y + sigma aux; r' = r - alpha w (FP32 planes)
-            const S16In aux = s16_at(ea.aux, k * bt.stride);
-            const float sg = (float)(ea.per_rhs_sigma ? ea.sigma_k[k] : ea.sigma);
-            s1 = mms_r_update(GSite{aux.q, aux.nrm, h}, sg, alpha_s[k], ea.r_in + k * ea.r_stride,
-                              ea.r + k * ea.r_stride, Vh, h, y);
-            part[k * blockDim.x + threadIdx.x] += s1;
         }
     };
     if (bt.order == 2) {
