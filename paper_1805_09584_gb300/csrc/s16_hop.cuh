@@ -309,19 +309,35 @@ __device__ __forceinline__ void add_shift(const Site &aux, float sigma, f2 y[4][
 // Plane by plane, so that p, y and w of the whole site are never live at once.
 template <bool DAG, class Site>
 __device__ __forceinline__ float odd_mms_r_fused(const SiteTermF &st, const f2 acc[4][3][2], const Site &psi,
-                                                 const Site &aux, float sigma, float alpha, const float2 *rin,
-                                                 float2 *rout, int Vh, int h) {
+                                                 const Site &aux, float sigma, float alpha,
+                                                 const float2 *__restrict__ rin, float2 *__restrict__ rout, int Vh,
+                                                 int h) {
     const float kp = DAG ? -st.kp : st.kp;
     const f2 sc2 = dup(psi.s()), nb2 = dup(-S16_DEC_BIAS);
     const float sa = sigma * aux.s();
     float s1 = 0.0f;
+    // loads one plane ahead: plane j + 1's words and residuals are in flight while plane j is
+    // computed and stored (no round trip per component, at most two planes' loads live)
+    int4 pw[3][2], aw[3][2];
+    float2 rv[3][4][2];
+    auto load_plane = [&](int j) {
+        pw[j][0] = psi.w(j);
+        pw[j][1] = psi.w(3 + j);
+        aw[j][0] = aux.w(j);
+        aw[j][1] = aux.w(3 + j);
+#pragma unroll
+        for (int m = 0; m < 4; m++)
+#pragma unroll
+            for (int f = 0; f < 2; f++) rv[j][m][f] = __ldcs(rin + (size_t)(f * 12 + 4 * j + m) * Vh + h);
+    };
+    load_plane(0);
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-        const int4 p0 = psi.w(j), p1 = psi.w(3 + j), a0 = aux.w(j), a1 = aux.w(3 + j);
+        if (j + 1 < 3) load_plane(j + 1);
 #pragma unroll
         for (int m = 0; m < 4; m++) {
             const int kk = 4 * j + m, sp = kk / 3, c = kk % 3;
-            const int w0 = word(p0, m), w1 = word(p1, m);
+            const int w0 = word(pw[j][0], m), w1 = word(pw[j][1], m);
             const f2 pr = mul2(add2(make_float2(s16_flo(w0), s16_flo(w1)), nb2), sc2);
             const f2 pi = mul2(add2(make_float2(s16_fhi(w0), s16_fhi(w1)), nb2), sc2);
             const float b = kp * (sp < 2 ? 1.0f : -1.0f);
@@ -333,13 +349,12 @@ __device__ __forceinline__ float odd_mms_r_fused(const SiteTermF &st, const f2 a
                                       fmaf(-b, pr.y, fmaf(-st.kpp, pi.x, pi.y - hi.y)));
 #pragma unroll
             for (int f = 0; f < 2; f++) {
-                const size_t i = (size_t)(f * 12 + kk) * Vh + h;
-                const float2 rv = __ldcs(rin + i);  // touched once per launch: evict first
-                const int aw = word(f ? a1 : a0, m);
-                const float wx = fmaf(sa, s16_lo(aw), f ? yr.y : yr.x);
-                const float wy = fmaf(sa, s16_hi(aw), f ? yi.y : yi.x);
-                const float2 rn = make_float2(fmaf(-alpha, wx, rv.x), fmaf(-alpha, wy, rv.y));
-                __stcs(rout + i, rn);
+                const int a = word(aw[j][f], m);
+                const float wx = fmaf(sa, s16_lo(a), f ? yr.y : yr.x);
+                const float wy = fmaf(sa, s16_hi(a), f ? yi.y : yi.x);
+                const float2 rn =
+                    make_float2(fmaf(-alpha, wx, rv[j][m][f].x), fmaf(-alpha, wy, rv[j][m][f].y));
+                __stcs(rout + (size_t)(f * 12 + kk) * Vh + h, rn);  // touched once per launch: evict first
                 s1 = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, s1));
             }
         }
