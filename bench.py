@@ -105,8 +105,11 @@ F32_Q2_BYTES_PER_SITE = 2 * ((192 + 576 + 192) + (192 + 192 + 576 + 192)) + 192
 S16_LINK_BYTES_PER_SITE = 4 * 192
 # DRAM bytes (read + write) of one 16-bit Qhat^2 + sigma, one ncu capture of its 4 launches:
 # {(lattice V/2, RHS per launch): bytes}
+# (the 8-RHS entry: the grid-stride variant the autotuner keeps there, 64 threads x 6 blocks per SM)
 S16_Q2_TRAFFIC = {(331776, 1): (97.503232e6 + 3.967232e6) + (132.547840e6 + 8.404480e6)
-                  + (97.519360e6 + 3.632896e6) + (169.893632e6 + 15.372288e6)}
+                  + (97.519360e6 + 3.632896e6) + (169.893632e6 + 15.372288e6),
+                  (1048576, 8): (3218.8e6 + 820.7e6) + (4144.8e6 + 821.5e6)
+                  + (3223.5e6 + 816.4e6) + (4910.6e6 + 823.1e6)}
 
 
 def _dist():
@@ -398,7 +401,7 @@ def run_form(args):
         extra["autotune"] = {"shapes": [tm.tmnd_s16_shape_info(i) for i in range(tm.S16_SHAPES)],
                              "shape_fields": ["threads per block", "blocks per SM", "next-direction prefetch",
                                               "loop order (0 chunk, sites outside; 1 chunk, RHS outside; "
-                                              "2 grid stride, sites outside)"],
+                                              "2 grid stride, sites outside; 3 grid stride over (32-site group, RHS) per warp)"],
                              "per_nrhs": per, "s": time.perf_counter() - t0}
     if args.form == "hybrid":
         t0 = time.perf_counter()
@@ -638,6 +641,8 @@ def run_kernel(args):
         out.update(hbm_peak_gbs=peak_hbm, bytes_per_site=F32_Q2_BYTES_PER_SITE)
         return out
     elif args.kernel == "s16":
+        tm.tmnd_s16_force_shape(args.variant)  # -1: the autotuner's choice
+        out.update(forced_variant=args.variant if args.variant >= 0 else None)
         for dims, name, rs in (((48, 24, 24, 24), "24^3x48", (1, 8)), ((64, 32, 32, 32), "32^3x64", (1, 8))):
             g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
             for R in rs:
@@ -650,6 +655,8 @@ def run_kernel(args):
                 # links are read once per launch for all R right-hand sides
                 byts = g.vh * (R * (2 * (200 + 300) + 100) + 4 * 192)
                 sh, tms = tm.tmnd_autotune(g.handle, R, stream)
+                if args.variant >= 0:
+                    sh = args.variant
                 out[f"{name}_nrhs{R}"] = {"ms_qhat2": ms, "ms_per_rhs": ms / R, "gbs": byts / (ms / 1e3) / 1e9,
                                           "frac_hbm": byts / (ms / 1e3) / 1e9 / peak_hbm, "variant": sh,
                                           "variant_ms": [round(float(v), 4) for v in tms]}
@@ -1043,6 +1050,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="hybrid", choices=list(FORMS))
     ap.add_argument("--kernel", default=None, choices=["fp64", "s16", "f32", "coarse"])
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="--kernel s16: time this launch variant of the 16-bit stencil (tmnd_s16_force_shape) "
+                         "instead of the autotuner's choice")
     ap.add_argument("--study", default=None, choices=["hybrid", "learned", "errors", "mg"])
     args = ap.parse_args()
     if args.study:

@@ -179,10 +179,12 @@ tmnd_status tm_nd_apply_noalloc(const tmnd_gauge *g, void *out, const void *in, 
 
 /* Launch-shape autotuner of the sloppy (16-bit) stencil.  Its kernels run in
  * TMND_S16_SHAPES launch variants: 4 compiled shapes (threads per block x resident blocks
- * per SM the register budget is cut for x next-direction prefetch) x 3 loop orders (0: every
+ * per SM the register budget is cut for x next-direction prefetch) x 4 loop orders (0: every
  * block walks its own chunk of sites, all right-hand sides of a site in turn; 1: the chunk
  * once per right-hand side; 2: all blocks sweep the lattice together by grid stride, all
- * right-hand sides of a site in turn); tmnd_s16_shape_info.  For each lattice
+ * right-hand sides of a site in turn; 3: grid stride over (group of 32 sites, right-hand
+ * side) items, one per warp, a group's right-hand sides on consecutive warps);
+ * tmnd_s16_shape_info.  For each lattice
  * and number of right-hand sides per launch (1..16) the library times every shape once on
  * the current device -- one 16-bit Qhat^2 + sigma sequence of 4 launches on scratch data,
  * CUDA events, best of 3 after a warm-up -- and keeps the fastest for the rest of the
@@ -192,12 +194,12 @@ tmnd_status tm_nd_apply_noalloc(const tmnd_gauge *g, void *out, const void *in, 
  * the default variant 0 is kept for the pair and its times are reported as 0).
  *   shape_out : receives the chosen shape (may be NULL)
  *   ms_out    : TMND_S16_SHAPES doubles, each shape's time in ms (may be NULL) */
-#define TMND_S16_SHAPES 12
+#define TMND_S16_SHAPES 16
 tmnd_status tmnd_autotune(tmnd_gauge *g, int nrhs, int *shape_out, double *ms_out, void *stream);
 /* Use shape `shape` for every later 16-bit stencil launch of this process (-1: back to the
  * tuned choice).  For tests and measurements; results do not depend on the shape. */
 tmnd_status tmnd_s16_force_shape(int shape);
-/* Threads per block, resident blocks per SM, prefetch flag (0/1) and loop order (0, 1, 2 as
+/* Threads per block, resident blocks per SM, prefetch flag (0/1) and loop order (0..3 as
  * above) of a variant (NULL outputs skipped). */
 tmnd_status tmnd_s16_shape_info(int shape, int *threads, int *blocks_per_sm, int *prefetch, int *order);
 

@@ -39,7 +39,7 @@ EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd
            "tmnd_hybrid_cost", "tmnd_fit_cg_time", "tmnd_fit_mg_time", "tmnd_lincomb_c", "tmnd_site_norm_range",
            "tmnd_lagrange_weights", "tmnd_lagrange_degree", "tmnd_guess_quadratic_form", "tmnd_mg_status",
            "tmnd_autotune", "tmnd_s16_force_shape", "tmnd_s16_shape_info", "tmnd_mg_bootstrap")
-S16_SHAPES = 12
+S16_SHAPES = 16
 TMND_MAX_BATCH = 16
 NOALLOC_MAX_VH = 32768
 
@@ -419,7 +419,7 @@ def tmnd_s16_force_shape(shape: int) -> None:
 
 
 def tmnd_s16_shape_info(shape: int):
-    """(threads per block, resident blocks per SM, prefetch, loop order 0/1/2) of a launch variant."""
+    """(threads per block, resident blocks per SM, prefetch, loop order 0..3) of a launch variant."""
     t, b, p, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().tmnd_s16_shape_info(int(shape), ctypes.byref(t), ctypes.byref(b), ctypes.byref(p), ctypes.byref(o)))
     return t.value, b.value, bool(p.value), o.value

@@ -30,8 +30,9 @@ constexpr int NCOMPILED = sizeof(kShapes) / sizeof(kShapes[0]);
 // a launch variant = compiled shape (v % NCOMPILED) x loop order (v / NCOMPILED): 0 = every
 // block walks its own chunk of sites, all right-hand sides of a site in turn; 1 = the same
 // chunk once per right-hand side; 2 = all blocks sweep the lattice together (grid stride),
-// all right-hand sides of a site in turn
-constexpr int NORDERS = 3;
+// all right-hand sides of a site in turn; 3 = grid stride over (32-site group, right-hand
+// side) items, one per warp
+constexpr int NORDERS = 4;
 constexpr int NSHAPES = NORDERS * NCOMPILED;
 static_assert(NSHAPES == TMND_S16_SHAPES, "variant count of include/tmnd.h");
 
@@ -193,7 +194,8 @@ tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out
     int choice = 0;
     cudaError_t err = cudaSuccess;
     for (int sh = 0; sh < NSHAPES && err == cudaSuccess; sh++) {
-        if (nrhs == 1 && sh / NCOMPILED == 1) {  // one right-hand side: orders 0 and 1 are the same launch
+        if (nrhs == 1 && (sh / NCOMPILED == 1 || sh / NCOMPILED == 3)) {
+            // one right-hand side: orders 0 and 1 are the same launch, and so are orders 2 and 3
             best[sh] = best[sh - NCOMPILED];
             continue;
         }

@@ -118,6 +118,24 @@ __device__ __forceinline__ void hop_all(const Geom &g, const int2 *__restrict__ 
     hop_seq<P, 0, G5IN, PF>(links, q, nrm, g.Vh, n, r0, acc);
 }
 
+// Loop order 3: grid stride over (group of 32 consecutive sites, right-hand side) work items,
+// one per warp, the right-hand sides of a group on consecutive warps.  All warps move through
+// the lattice together as in order 2, but each carries one right-hand side, so the band of
+// sites in flight (and the neighbour words it keeps live in L2) is nrhs times narrower; the
+// warps of a group read the same links side by side.
+template <class F>
+__device__ __forceinline__ void grid_stride_rhs_warps(int Vh, const S16Batch &bt, F &&site) {
+    const int lane = threadIdx.x & 31;
+    const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+    const long items = (long)((Vh + 31) >> 5) * bt.nrhs;
+    for (long w = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < items; w += nwarps) {
+        const int k = (int)(w % bt.nrhs);
+        const int h = (int)(w / bt.nrhs) * 32 + lane;
+        if (h >= Vh || (bt.rdone && bt.rdone[k * bt.rdone_stride])) continue;
+        site(h, k);
+    }
+}
+
 template <bool DAG, bool PF, int NT, int MB>
 __global__ void __launch_bounds__(NT, MB) k_hop_even_s16(Geom g, SiteTermF st, const int2 *__restrict__ links,
                                                          S16In in, S16Out out, const int *__restrict__ done,
@@ -133,8 +151,10 @@ __global__ void __launch_bounds__(NT, MB) k_hop_even_s16(Geom g, SiteTermF st, c
         const S16Out ok = s16_at(out, k * bt.stride);
         store_site(ok.q, ok.nrm, g.Vh, h, o);
     };
-    if (bt.order == 2) {  // grid-stride sweep: all blocks move through the lattice together, so
-                          // every right-hand side's neighbours stay in L2 while the band passes
+    if (bt.order == 3) {
+        grid_stride_rhs_warps(g.Vh, bt, site);
+    } else if (bt.order == 2) {  // grid-stride sweep: all blocks move through the lattice together, so
+                                 // every right-hand side's neighbours stay in L2 while the band passes
         for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x)
             for (int k = 0; k < bt.nrhs; k++) {
                 if (bt.rdone && bt.rdone[k * bt.rdone_stride]) continue;
@@ -209,7 +229,9 @@ __global__ void __launch_bounds__(NT, MB) k_hop_odd_s16(Geom g, SiteTermF st, co
             store_site(out.q, out.nrm, Vh, h, y);
         }
     };
-    if (bt.order == 2) {
+    if (bt.order == 3) {
+        grid_stride_rhs_warps(Vh, bt, site);
+    } else if (bt.order == 2) {
         for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x)
             for (int k = 0; k < bt.nrhs; k++) {
                 if (bt.rdone && bt.rdone[k * bt.rdone_stride]) continue;

@@ -262,7 +262,8 @@ struct S16Batch {
     int rdone_stride = 0;
     int shape = -1;  // launch variant (dslash_s16.cu); -1: the autotuner's choice for (lattice, nrhs)
     int order = 0;   // set by the launchers from the variant: 0 sites of the block's chunk outside the
-                     // right-hand sides, 1 right-hand sides outside the chunk, 2 grid-stride sites outside
+                     // right-hand sides, 1 right-hand sides outside the chunk, 2 grid-stride sites outside,
+                     // 3 grid stride over (32-site group, right-hand side), one per warp
 };
 
 // launch shapes of the 16-bit stencil and their autotuner (dslash_s16.cu)

@@ -37,7 +37,7 @@ def test_shapes_agree_bitwise_and_tuner_picks_one(nrhs):
     g.close()
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3])
+@pytest.mark.parametrize("shape", [1, 2, 3, 12, 14])
 def test_mixed_solve_certified_under_each_shape(shape):
     tm = require_gpu()
     dims = (4, 4, 4, 4)
