@@ -168,6 +168,13 @@ class ClockSampler:
                                        "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        # nvidia-smi's start-up (NVML initialisation) stalls the GPU's work for a few hundred ms:
+        # wait for its first sample, so that the start-up overlaps neither warm-up nor timing
+        t0 = time.time()
+        while self.p is not None and self.p.poll() is None and time.time() - t0 < 10:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.05)
 
     def stop(self):
         if self.p is None:
@@ -207,7 +214,8 @@ def count_kernels(fn, prefix=("k_",)):
             torch.cuda.synchronize()
         n, names = 0, {}
         for ev in prof.events():
-            nm = (ev.name or "").replace("(anonymous namespace)::", "")
+            # CUPTI writes the anonymous namespace as "(anonymous namespace)::" or "<unnamed>::"
+            nm = (ev.name or "").replace("(anonymous namespace)::", "").replace("<unnamed>::", "")
             dev = str(getattr(ev, "device_type", ""))
             base = nm.split("(")[0].split("<")[0].split(" ")[-1]
             if "CUDA" in dev and any(base.startswith(p) for p in prefix):
@@ -340,24 +348,27 @@ def workload_name(form, F, nrhs):
     return f"{F['lattice']} ND twisted-mass doublet, {desc}, {shifts}, {nrhs} RHS, rho 1e-10"
 
 
-def _timed(step, steps, flush, stream, nvtx=None):
+def _timed(step, steps, flush, stream, nvtx=None, per_step=None):
     """CUDA-event time of `steps` calls of step (L2 flushed before each); each call inside an
-    NVTX range named `nvtx` if given (profilers can select the timed steps by it)."""
+    NVTX range named `nvtx` if given (profilers can select the timed steps by it).  With a
+    list `per_step`, it receives each step's own event time (ms, flush included)."""
     import torch
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     out = []
-    e0.record(stream)
-    for _ in range(steps):
+    ev[0].record(stream)
+    for i in range(steps):
         flush.fill_(1.0)
         if nvtx:
             torch.cuda.nvtx.range_push(nvtx)
         out.append(step())
         if nvtx:
             torch.cuda.nvtx.range_pop()
-    e1.record(stream)
+        ev[i + 1].record(stream)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1), out
+    if per_step is not None:
+        per_step.extend(ev[i].elapsed_time(ev[i + 1]) for i in range(steps))
+    return ev[0].elapsed_time(ev[steps]), out
 
 
 def run_form(args):
@@ -461,7 +472,8 @@ def run_form(args):
         step()
     if ws > 1:
         dist.barrier()
-    ms, infos = _timed(step, args.steps, flush, stream, nvtx="timed_step")
+    step_ms = []
+    ms, infos = _timed(step, args.steps, flush, stream, nvtx="timed_step", per_step=step_ms)
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -560,6 +572,7 @@ def run_form(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "flushed between steps (512 MB write); solve working set > L2"},
             "max_true_rel_residual": worst,
+            "step_ms": [round(v, 3) for v in step_ms],
             "e2e": {"value": whole_job_rate(e2e_steps * len(sig) * nrhs, ws, e2e_all), "unit": "solves/s",
                     "h2d_bytes_per_step": b_host.nbytes, "d2h_bytes_per_step": len(outs) * b_host.nbytes,
                     "steps": e2e_steps},
@@ -567,7 +580,7 @@ def run_form(args):
             "gpu_launches": launches_claim,
             "gpu_launches_note": ("kernels per step counted from torch.profiler's CUDA activity trace of one "
                                   "step, times the timed steps" if nk else "the library's own launch count"),
-            "kernels_per_step": knames, "clocks": clocks, **extra,
+            **({"kernels_per_step": knames} if knames else {}), "clocks": clocks, **extra,
         }
     if net is not None:
         tm.tmnd_mlp_destroy(net)
