@@ -338,9 +338,10 @@ def workload_name(form, F, nrhs):
         "mixed": "mixed-precision multi-shift CG (FP32 on 16-bit data + FP64 defect correction), RHS one at a time",
         "batched": "mixed-precision multi-shift CG with all RHS in every 16-bit stencil launch + batched FP64 "
                    "defect correction",
-        "hybrid": "hybrid solve: batched mixed multi-shift CG for the 8 largest shifts, Lagrange guesses and case-C "
-                  "two-level multigrid (4^4 aggregates, 24 vectors per chirality, tensor-core coarse operator) for "
-                  "the 4 smallest, batched FP64 defect correction",
+        "hybrid": "hybrid solve: batched mixed multi-shift CG for the 8 largest shifts, Lagrange guesses for the "
+                  "4 smallest, batched FP64 defect correction of every shift; case-C two-level multigrid (4^4 "
+                  "aggregates, 24 vectors per chirality, tensor-core coarse operator) set up and entered for a shift "
+                  "whose guess residual exceeds 1e-4 (none at this workload: mg_iters in the line)",
         "learned": "mixed multi-shift CG for the 8 largest shifts, learned guesses for the 4 smallest",
         "rational": "Zolotarev n = 10 rational approximation of (Qhat^2)^(-1/2) over a mixed multi-shift solve",
     }[form]
