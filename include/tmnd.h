@@ -230,9 +230,11 @@ typedef struct {
     double *ab_hist;       /* optional host array: receives (alpha_k, beta_k), k = 1.., of the base
                               recursion of the first RHS (the Lanczos coefficients), zero-padded */
     int ab_hist_len;       /* length of ab_hist in doubles (2 per iteration) */
-    int batch;             /* TMND_S16: right-hand sides the sloppy solver iterates together, every
-                              16-bit stencil launch covering all of them (0 = min(nrhs, 16);
-                              1 = one at a time); the FP64 defect correction stays per RHS */
+    int batch;             /* TMND_S16: right-hand sides the sloppy multi-shift solver iterates
+                              together, every 16-bit stencil launch covering all of them
+                              (0 = min(nrhs, 16); 1 = one at a time).  The FP64 defects are taken
+                              one (RHS, shift) pair at a time; the inner refinements of up to
+                              min(batch x nsolve, 16) pairs share each stencil launch. */
 } tmnd_solve_params;
 
 typedef struct {
