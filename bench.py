@@ -838,7 +838,11 @@ def run_study_mg(args):
     1e-4 from a zero start (at most 100 outer iterations, GCR(24), 2 smoothing steps) of
     D_ND + i s gamma_5 tau_1 Pi_odd on a Gaussian full-lattice right-hand side, for minimal-
     residual smoothing (test vectors relaxed by 4 MR steps), SAP smoothing with the same
-    vectors, and SAP after one round of adaptive setup; next to the mixed CG on the same shift."""
+    vectors, and SAP after one round of adaptive setup; next to the mixed CG on the same shift.
+    With --kappa k1 k2 ..., the same for each hopping parameter (harder spectra as kappa grows
+    toward its critical value), SAP after the adaptive setup only, with the extreme Ritz values
+    of Qhat^2 from the CG history."""
+    import numpy as np
     import torch
 
     import paper_1805_09584_gb300 as tm
@@ -848,48 +852,69 @@ def run_study_mg(args):
     _build.build()
     torch.cuda.set_device(0)
     dims = (48, 24, 24, 24)
-    g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, KAPPA, MU_BAR, EPS_BAR)
     nv, blk = 24, (4, 4, 4, 4)
-    gen = torch.Generator(device="cuda").manual_seed(7)
-    tv = torch.randn(nv * 2 * 12 * g.vh, dtype=torch.complex64, device="cuda", generator=gen)
-    tm.tmnd_mg_smooth_vectors(g.handle, tv, nv, 4)
-    t0 = time.perf_counter()
-    mg_mr = tm.tmnd_mg_create(g.handle, blk, nv, tv)
-    mg_sap = tm.tmnd_mg_create(g.handle, blk, nv, tv, smoother=1)
-    torch.cuda.synchronize()
-    t_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    mg_boot = tm.tmnd_mg_bootstrap(mg_sap, tv, 3, blk, nv, smoother=1)
-    torch.cuda.synchronize()
-    t_boot = time.perf_counter() - t0
-    rhs = torch.randn(2 * 24 * g.vh, dtype=torch.complex64, device="cuda", generator=gen)
-    b_odd = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, 2003)).cuda())
-    rows = []
-    for sigma in (0.07, 7.8e-3, 2.8e-4, 1e-5):
-        s = float(sigma) ** 0.5
-        row = {"sigma": sigma}
-        for name, mg in (("mr", mg_mr), ("sap", mg_sap), ("sap_bootstrap", mg_boot)):
-            x = torch.zeros_like(rhs)
+    kappas = args.kappa or [KAPPA]
+    out = {"study": "case-C multigrid at small shifts (SAP, adaptive setup)", "lattice": "24^3x48",
+           "aggregates": "4^4", "test_vectors": nv,
+           "solve": "GCR(24), 2 pre/post smoothing steps, tol 1e-4, at most 100 outer iterations, zero start, "
+                    "Gaussian full-lattice right-hand side", "per_kappa": []}
+    for kappa in kappas:
+        g = tm.Gauge(synth.random_su3_field(dims, ROUGHNESS, 1003), dims, kappa, MU_BAR, EPS_BAR)
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        tv = torch.randn(nv * 2 * 12 * g.vh, dtype=torch.complex64, device="cuda", generator=gen)
+        tm.tmnd_mg_smooth_vectors(g.handle, tv, nv, 4)
+        t0 = time.perf_counter()
+        mg_mr = tm.tmnd_mg_create(g.handle, blk, nv, tv) if not args.kappa else None
+        mg_sap = tm.tmnd_mg_create(g.handle, blk, nv, tv, smoother=1)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        mg_boot = tm.tmnd_mg_bootstrap(mg_sap, tv, 3, blk, nv, smoother=1)
+        torch.cuda.synchronize()
+        t_boot = time.perf_counter() - t0
+        del tv
+        rhs = torch.randn(2 * 24 * g.vh, dtype=torch.complex64, device="cuda", generator=gen)
+        b_odd = g.pack(torch.from_numpy(synth.gaussian_rhs(dims, 2003)).cuda())
+        variants = (("mr", mg_mr), ("sap", mg_sap), ("sap_bootstrap", mg_boot)) if not args.kappa else \
+            (("sap_bootstrap", mg_boot),)
+        rows = []
+        for sigma in (0.07, 7.8e-3, 2.8e-4, 1e-5):
+            s = float(sigma) ** 0.5
+            row = {"sigma": sigma}
+            for name, mg in variants:
+                x = torch.zeros_like(rhs)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                info = tm.tmnd_mg_solve(mg, x, rhs, s, tol=1e-4, maxiter=100, restart=24, nu=2)
+                torch.cuda.synchronize()
+                row[name] = {"iters": info["iters"], "res": info["res"], "s": time.perf_counter() - t}
+            xs = [g.spinor()]
             torch.cuda.synchronize()
             t = time.perf_counter()
-            info = tm.tmnd_mg_solve(mg, x, rhs, s, tol=1e-4, maxiter=100, restart=24, nu=2)
+            inf = tm.mms_cg_solve(g.handle, b_odd, 1, [sigma], xs, rho=1e-10, prec=tm.TMND_S16)
             torch.cuda.synchronize()
-            row[name] = {"iters": info["iters"], "res": info["res"], "s": time.perf_counter() - t}
-        xs = [g.spinor()]
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        inf = tm.mms_cg_solve(g.handle, b_odd, 1, [sigma], xs, rho=1e-10, prec=tm.TMND_S16)
-        torch.cuda.synchronize()
-        row["mixed_cg_1e-10"] = {"iters": inf["iters"] + inf["refine_iters"], "s": time.perf_counter() - t}
-        rows.append(row)
-    for mg in (mg_boot, mg_sap, mg_mr):
-        tm.tmnd_mg_destroy(mg)
-    g.close()
-    return {"study": "case-C multigrid at small shifts (SAP, adaptive setup)", "lattice": "24^3x48",
-            "aggregates": "4^4", "test_vectors": nv, "setup_s": t_setup, "bootstrap_s": t_boot,
-            "solve": "GCR(24), 2 pre/post smoothing steps, tol 1e-4, at most 100 outer iterations, zero start, "
-                     "Gaussian full-lattice right-hand side",
-            "rows": rows}
+            row["mixed_cg_1e-10"] = {"iters": inf["iters"] + inf["refine_iters"], "s": time.perf_counter() - t}
+            rows.append(row)
+        # extreme Ritz values of Qhat^2 (FP64 CG history at the smallest shift)
+        hist = np.zeros(2 * 8192)
+        xb = [g.spinor()]
+        inf = tm.mms_cg_solve(g.handle, b_odd, 1, [1e-5], xb, rho=1e-8, ab_hist=hist)
+        sg = synth.shift_set(NSHIFT, SIG_LO, SIG_HI)
+        f = tm.tmnd_mlp_features(sg[:8], float(sg[8]), hist, inf["iters"], 1e-5)
+        rec = {"kappa": kappa, "setup_s": t_setup, "bootstrap_s": t_boot, "rows": rows,
+               "ritz_min_max": [10 ** float(f[17]), 10 ** float(f[18])], "fp64_cg_iters_1e-8": inf["iters"]}
+        out["per_kappa"].append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+        for mg in (mg_boot, mg_sap, mg_mr):
+            if mg is not None:
+                tm.tmnd_mg_destroy(mg)
+        del xs, xb, b_odd, rhs
+        g.close()
+    if not args.kappa:   # the single-kappa study's original layout
+        rec = out.pop("per_kappa")[0]
+        out.update(setup_s=rec["setup_s"], bootstrap_s=rec["bootstrap_s"], rows=rec["rows"],
+                   ritz_min_max=rec["ritz_min_max"])
+    return out
 
 
 def run_study_errors(args):
@@ -1068,6 +1093,8 @@ def main():
                     help="--kernel s16: time this launch variant of the 16-bit stencil (tmnd_s16_force_shape) "
                          "instead of the autotuner's choice")
     ap.add_argument("--study", default=None, choices=["hybrid", "learned", "errors", "mg"])
+    ap.add_argument("--kappa", type=float, nargs="+", default=None,
+                    help="--study mg: hopping parameters to run the study at (default: the configs' kappa)")
     args = ap.parse_args()
     if args.study:
         fn = {"hybrid": run_study, "learned": run_study_learned, "errors": run_study_errors,
