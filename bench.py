@@ -409,7 +409,9 @@ def run_form(args):
         per = {}
         for R in range(1, tm.TMND_MAX_BATCH + 1):
             sh, tms = tm.tmnd_autotune(g.handle, R, stream)
-            per[R] = {"shape": sh, "ms": [round(float(v), 4) for v in tms]}
+            shm, tmm = tm.tmnd_autotune_mms(g.handle, R, stream)
+            per[R] = {"shape": sh, "ms": [round(float(v), 4) for v in tms],
+                      "shape_mms": shm, "ms_mms": [round(float(v), 4) for v in tmm]}
         extra["autotune"] = {"shapes": [tm.tmnd_s16_shape_info(i) for i in range(tm.S16_SHAPES)],
                              "shape_fields": ["threads per block", "blocks per SM", "next-direction prefetch",
                                               "loop order (0 chunk, sites outside; 1 chunk, RHS outside; "

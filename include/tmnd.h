@@ -184,18 +184,23 @@ tmnd_status tm_nd_apply_noalloc(const tmnd_gauge *g, void *out, const void *in, 
  * once per right-hand side; 2: all blocks sweep the lattice together by grid stride, all
  * right-hand sides of a site in turn; 3: grid stride over (group of 32 sites, right-hand
  * side) items, one per warp, a group's right-hand sides on consecutive warps);
- * tmnd_s16_shape_info.  For each lattice
- * and number of right-hand sides per launch (1..16) the library times every shape once on
- * the current device -- one 16-bit Qhat^2 + sigma sequence of 4 launches on scratch data,
- * CUDA events, best of 3 after a warm-up -- and keeps the fastest for the rest of the
- * process.  This happens on the first 16-bit tm_nd_apply or sloppy solve of that pair
+ * tmnd_s16_shape_info.  For each lattice and number of right-hand sides per launch (1..16)
+ * the library times every variant once on the current device, on scratch data, CUDA events,
+ * best of 3 after a warm-up, for two sequences of 4 launches: (a) one 16-bit Qhat^2 + sigma
+ * as tm_nd_apply runs it, and (b) one iteration of the sloppy multi-shift solver (the same
+ * launches, the last one with the residual-update epilogue on FP32 residual planes); it keeps
+ * the fastest variant of each for the rest of the process: (a) for tm_nd_apply, (b) for the
+ * sloppy solves.  This happens on the first 16-bit tm_nd_apply or sloppy solve of that pair
  * (skipped while the stream is being captured: the default shape 0 is used then), or here,
- * ahead of time.  Synchronous; allocates its scratch for the call (if that allocation fails,
- * the default variant 0 is kept for the pair and its times are reported as 0).
+ * ahead of time.  Synchronous; allocates its scratch for the call, 3 16-bit and 2 FP32
+ * spinors per right-hand side (if that allocation fails, the default variant 0 is kept for
+ * the pair and its times are reported as 0).
  *   shape_out : receives the chosen shape (may be NULL)
- *   ms_out    : TMND_S16_SHAPES doubles, each shape's time in ms (may be NULL) */
+ *   ms_out    : TMND_S16_SHAPES doubles, each shape's time in ms (may be NULL)
+ * tmnd_autotune reports sequence (a), tmnd_autotune_mms sequence (b); either call tunes both. */
 #define TMND_S16_SHAPES 16
 tmnd_status tmnd_autotune(tmnd_gauge *g, int nrhs, int *shape_out, double *ms_out, void *stream);
+tmnd_status tmnd_autotune_mms(tmnd_gauge *g, int nrhs, int *shape_out, double *ms_out, void *stream);
 /* Use shape `shape` for every later 16-bit stencil launch of this process (-1: back to the
  * tuned choice).  For tests and measurements; results do not depend on the shape. */
 tmnd_status tmnd_s16_force_shape(int shape);

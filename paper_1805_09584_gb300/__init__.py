@@ -38,7 +38,8 @@ EXPORTS = ("tmnd_gauge_create", "tmnd_gauge_destroy", "tmnd_spinor_bytes", "tmnd
            "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_zolotarev", "tmnd_rational_apply",
            "tmnd_hybrid_cost", "tmnd_fit_cg_time", "tmnd_fit_mg_time", "tmnd_lincomb_c", "tmnd_site_norm_range",
            "tmnd_lagrange_weights", "tmnd_lagrange_degree", "tmnd_guess_quadratic_form", "tmnd_mg_status",
-           "tmnd_autotune", "tmnd_s16_force_shape", "tmnd_s16_shape_info", "tmnd_mg_bootstrap")
+           "tmnd_autotune", "tmnd_autotune_mms", "tmnd_s16_force_shape", "tmnd_s16_shape_info",
+           "tmnd_mg_bootstrap")
 S16_SHAPES = 16
 TMND_MAX_BATCH = 16
 NOALLOC_MAX_VH = 32768
@@ -165,6 +166,7 @@ def lib() -> ctypes.CDLL:
                                           ctypes.POINTER(SolveInfo), vp]
         L.tmnd_lagrange_weights.argtypes = [pd, i, d, pd, pd]
         L.tmnd_autotune.argtypes = [vp, i, ctypes.POINTER(i), pd, vp]
+        L.tmnd_autotune_mms.argtypes = [vp, i, ctypes.POINTER(i), pd, vp]
         L.tmnd_s16_force_shape.argtypes = [i]
         L.tmnd_s16_shape_info.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                           ctypes.POINTER(i)]
@@ -175,7 +177,8 @@ def lib() -> ctypes.CDLL:
                      "tmnd_fit_cg_time", "tmnd_fit_mg_time",
                      "tmnd_mlp_predict", "tmnd_mlp_features", "tmnd_gram", "tmnd_lincomb", "tmnd_lincomb_c",
                      "tmnd_site_norm_range", "tmnd_lagrange_weights", "tmnd_lagrange_degree",
-                     "tmnd_guess_quadratic_form", "tmnd_autotune", "tmnd_s16_force_shape", "tmnd_s16_shape_info"):
+                     "tmnd_guess_quadratic_form", "tmnd_autotune", "tmnd_autotune_mms", "tmnd_s16_force_shape",
+                     "tmnd_s16_shape_info"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("tmnd_mg_create", "tmnd_mg_restrict", "tmnd_mg_prolong", "mg_coarse_apply", "tmnd_mg_export",
                      "tmnd_mg_status", "tmnd_mg_bootstrap",
@@ -407,10 +410,20 @@ def _pd(a):
 
 
 def tmnd_autotune(h, nrhs: int, stream=None):
-    """(chosen shape, per-shape ms) of the 16-bit stencil for this lattice and nrhs per launch."""
+    """(chosen shape, per-shape ms) of the 16-bit stencil's Qhat^2 + sigma application for
+    this lattice and nrhs per launch."""
     sh = ctypes.c_int()
     ms = np.zeros(S16_SHAPES)
     _check(lib().tmnd_autotune(h, int(nrhs), ctypes.byref(sh), _pd(ms), _stream(stream)))
+    return sh.value, ms
+
+
+def tmnd_autotune_mms(h, nrhs: int, stream=None):
+    """(chosen shape, per-shape ms) of the 16-bit stencil's sloppy multi-shift iteration (the
+    4 launches, the last with the residual-update epilogue) for this lattice and nrhs."""
+    sh = ctypes.c_int()
+    ms = np.zeros(S16_SHAPES)
+    _check(lib().tmnd_autotune_mms(h, int(nrhs), ctypes.byref(sh), _pd(ms), _stream(stream)))
     return sh.value, ms
 
 

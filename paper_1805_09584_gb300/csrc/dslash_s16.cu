@@ -70,9 +70,11 @@ int sm_count() {
 
 // ---------------------------------------------------------------- autotuner state
 // (device, T, X, Y, Z, right-hand sides per launch) -> chosen shape
+// Two objectives per key: [0] a Qhat^2 + sigma application (tm_nd_apply), [1] the four
+// launches of one sloppy multi-shift iteration (the last with the residual-update epilogue).
 std::mutex g_tune_mutex;
-std::map<std::array<int, 6>, int> g_tuned;
-std::map<std::array<int, 6>, std::array<float, NSHAPES>> g_tune_ms;
+std::map<std::array<int, 6>, std::array<int, 2>> g_tuned;
+std::map<std::array<int, 6>, std::array<std::array<float, NSHAPES>, 2>> g_tune_ms;
 int g_forced = -1;
 
 std::array<int, 6> tune_key(const Geom &g, int nrhs) {
@@ -103,12 +105,15 @@ int hop_blocks_s16_max(const Geom &g) {
 }
 
 // the shape for this lattice and number of right-hand sides: forced, else tuned, else 0
-int s16_shape(const Geom &g, int nrhs) {
+// (objective 0: operator applications; 1: sloppy multi-shift iterations)
+static int shape_for(const Geom &g, int nrhs, int objective) {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     if (g_forced >= 0) return g_forced;
     auto it = g_tuned.find(tune_key(g, nrhs));
-    return it == g_tuned.end() ? 0 : it->second;
+    return it == g_tuned.end() ? 0 : it->second[objective];
 }
+int s16_shape(const Geom &g, int nrhs) { return shape_for(g, nrhs, 0); }
+int s16_shape_mms(const Geom &g, int nrhs) { return shape_for(g, nrhs, 1); }
 
 void launch_hop_even_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In in, S16Out out, bool dag,
                          const int *done, cudaStream_t s, const S16Batch &bt_in) {
@@ -141,21 +146,24 @@ void launch_hop_odd_s16(const Geom &g, const SiteTermF &st, const int2 *links, S
     }
 }
 
-// Autotuner: time one 16-bit Qhat^2 + sigma sequence (the 4 launches a solver iteration
-// makes, with the odd kernels' norm partials) of nrhs right-hand sides in every shape on
-// scratch data, CUDA events, best of 3 after one warm-up; keep the fastest shape for this
-// (device, lattice, nrhs).  Skipped (shape 0 stays) while the stream is being captured.
-tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out, float *ms_out) {
+// Autotuner: for every launch variant, on scratch data of nrhs right-hand sides (CUDA events,
+// best of 3 after one warm-up), time (0) one 16-bit Qhat^2 + sigma as tm_nd_apply launches it,
+// and (1) the four launches of a sloppy multi-shift iteration: the same two even and two odd
+// launches, the last one with the residual-update epilogue on FP32 residual planes.  Keep the
+// fastest variant for each for this (device, lattice, nrhs).  Skipped (shape 0 stays) while the
+// stream is being captured; without room for the scratch shape 0 is kept and 0 ms reported.
+tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out, float *ms_out, int objective) {
     TMND_ARG_CHECK(nrhs >= 1 && nrhs <= TMND_MAX_BATCH, "tmnd_autotune: nrhs = %d not in [1, %d]", nrhs,
                    TMND_MAX_BATCH);
+    TMND_ARG_CHECK(objective == 0 || objective == 1, "tmnd_autotune: objective %d", objective);
     const auto key = tune_key(g->geom, nrhs);
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
-            if (shape_out) *shape_out = it->second;
+            if (shape_out) *shape_out = it->second[objective];
             if (ms_out) {
-                const auto &t = g_tune_ms[key];
+                const auto &t = g_tune_ms[key][objective];
                 for (int i = 0; i < NSHAPES; i++) ms_out[i] = t[i];
             }
             return TMND_OK;
@@ -168,35 +176,51 @@ tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out
     }
     const int Vh = g->geom.Vh;
     const size_t sb = spinor_bytes_prec(Vh, TMND_S16);
-    const size_t part_b = sizeof(double) * 2 * (size_t)nrhs * hop_blocks_s16_max(g->geom);
+    const int maxgrid = hop_blocks_s16_max(g->geom);
+    // scratch: in, t, y (16-bit) | partials [nrhs][2][grid] of the norms launch and [nrhs][grid]
+    // of the residual launch | (r, r) per RHS | residual planes in and out (FP32, nrhs each)
+    const size_t off_part = 3 * (size_t)nrhs * sb;
+    const size_t off_rr = (off_part + sizeof(double) * 3 * (size_t)nrhs * maxgrid + 255) & ~(size_t)255;
+    const size_t off_r = (off_rr + sizeof(double) * (size_t)nrhs + 255) & ~(size_t)255;
+    const size_t r_elems = 24 * (size_t)Vh * nrhs;  // float2 per residual set
+    const size_t total = off_r + 2 * sizeof(float2) * r_elems;
     char *buf = nullptr;
-    if (cudaMalloc(&buf, 3 * (size_t)nrhs * sb + part_b + 256) != cudaSuccess) {
+    if (cudaMalloc(&buf, total) != cudaSuccess) {
         // no room for the scratch: keep the default shape for this pair (tuning is an optimisation)
         cudaGetLastError();
         std::lock_guard<std::mutex> lk(g_tune_mutex);
-        g_tuned[key] = 0;
-        g_tune_ms[key].fill(0.0f);
+        g_tuned[key] = {0, 0};
+        g_tune_ms[key][0].fill(0.0f);
+        g_tune_ms[key][1].fill(0.0f);
         if (shape_out) *shape_out = 0;
         if (ms_out)
             for (int i = 0; i < NSHAPES; i++) ms_out[i] = 0.0f;
         return TMND_OK;
     }
-    // biased 16-bit words of 0x4000 and unit scales: finite, data-independent timing
-    cudaMemsetAsync(buf, 0x40, 3 * (size_t)nrhs * sb, s);
+    // biased 16-bit words of 0x4000 and unit scales: finite, data-independent timing; partials
+    // and residuals zero, (r, r) = the double of bytes 0x3f (a small positive number)
+    cudaMemsetAsync(buf, 0x40, off_part, s);
+    cudaMemsetAsync(buf + off_part, 0, off_rr - off_part, s);
+    cudaMemsetAsync(buf + off_rr, 0x3f, sizeof(double) * (size_t)nrhs, s);
+    cudaMemsetAsync(buf + off_r, 0, 2 * sizeof(float2) * r_elems, s);
     const S16In in = s16_in(buf, Vh);
     const S16Out te = s16_out(buf + (size_t)nrhs * sb, Vh), y = s16_out(buf + 2 * (size_t)nrhs * sb, Vh);
     const S16In tei{te.q, te.nrm}, yi{y.q, y.nrm};
-    double *part = (double *)(buf + 3 * (size_t)nrhs * sb);
+    double *part = (double *)(buf + off_part);
+    double *part_r = part + 2 * (size_t)nrhs * maxgrid;
+    const double *rr = (const double *)(buf + off_rr);
+    float2 *r_in = (float2 *)(buf + off_r), *r_out = r_in + r_elems;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    std::array<float, NSHAPES> best;
-    int choice = 0;
+    std::array<std::array<float, NSHAPES>, 2> best;
+    int choice[2] = {0, 0};
     cudaError_t err = cudaSuccess;
     for (int sh = 0; sh < NSHAPES && err == cudaSuccess; sh++) {
         if (nrhs == 1 && (sh / NCOMPILED == 1 || sh / NCOMPILED == 3)) {
             // one right-hand side: orders 0 and 1 are the same launch, and so are orders 2 and 3
-            best[sh] = best[sh - NCOMPILED];
+            best[0][sh] = best[0][sh - NCOMPILED];
+            best[1][sh] = best[1][sh - NCOMPILED];
             continue;
         }
         S16Batch bt;
@@ -205,23 +229,40 @@ tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out
         bt.shape = sh;
         S16EpiArgs e1a = {};
         e1a.part_out = part;
-        S16EpiArgs e2a = {};
+        S16EpiArgs e2a = {};  // the application's sigma term
         e2a.sigma = 0.01;
         e2a.aux = in;
-        best[sh] = 1e30f;
-        for (int rep = 0; rep < 4 && err == cudaSuccess; rep++) {
-            cudaEventRecord(e0, s);
-            launch_hop_even_s16(g->geom, g->stf, g->links_s16, in, te, false, nullptr, s, bt);
-            launch_hop_odd_s16(g->geom, g->stf, g->links_s16, in, tei, y, false, EPI_STORE_NORMS, e1a, s, bt);
-            launch_hop_even_s16(g->geom, g->stf, g->links_s16, yi, te, true, nullptr, s, bt);
-            launch_hop_odd_s16(g->geom, g->stf, g->links_s16, yi, tei, te, true, EPI_SHIFT, e2a, s, bt);
-            cudaEventRecord(e1, s);
-            err = cudaEventSynchronize(e1);
-            float ms = 0;
-            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0 && ms < best[sh]) best[sh] = ms;
+        S16EpiArgs e3a = {};  // the multi-shift iteration's residual update
+        e3a.sigma = 0.01;
+        e3a.aux = in;
+        e3a.r_in = r_in;
+        e3a.r = r_out;
+        e3a.r_stride = 24L * Vh;
+        e3a.part_out = part_r;
+        e3a.part_in = part;
+        e3a.npart_in = hop_blocks_s16(g->geom, sh);
+        e3a.rr = rr;
+        e3a.rr_stride = 1;
+        for (int obj = 0; obj < 2; obj++) {
+            best[obj][sh] = 1e30f;
+            for (int rep = 0; rep < 4 && err == cudaSuccess; rep++) {
+                cudaEventRecord(e0, s);
+                launch_hop_even_s16(g->geom, g->stf, g->links_s16, in, te, false, nullptr, s, bt);
+                launch_hop_odd_s16(g->geom, g->stf, g->links_s16, in, tei, y, false, EPI_STORE_NORMS, e1a, s, bt);
+                launch_hop_even_s16(g->geom, g->stf, g->links_s16, yi, te, true, nullptr, s, bt);
+                if (obj == 0)
+                    launch_hop_odd_s16(g->geom, g->stf, g->links_s16, yi, tei, te, true, EPI_SHIFT, e2a, s, bt);
+                else
+                    launch_hop_odd_s16(g->geom, g->stf, g->links_s16, yi, tei, S16Out{}, true, EPI_MMS_R, e3a, s,
+                                       bt);
+                cudaEventRecord(e1, s);
+                err = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && ms < best[obj][sh]) best[obj][sh] = ms;
+            }
+            if (best[obj][sh] < best[obj][choice[obj]]) choice[obj] = sh;
         }
-        if (best[sh] < best[choice]) choice = sh;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -232,26 +273,35 @@ tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out
     }
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
-        g_tuned[key] = choice;
+        g_tuned[key] = {choice[0], choice[1]};
         g_tune_ms[key] = best;
     }
-    if (shape_out) *shape_out = choice;
+    if (shape_out) *shape_out = choice[objective];
     if (ms_out)
-        for (int i = 0; i < NSHAPES; i++) ms_out[i] = best[i];
+        for (int i = 0; i < NSHAPES; i++) ms_out[i] = best[objective][i];
     return TMND_OK;
 }
 
-extern "C" tmnd_status tmnd_autotune(tmnd_gauge *g, int nrhs, int *shape_out, double *ms_out, void *stream) {
+static tmnd_status autotune_entry(tmnd_gauge *g, int nrhs, int *shape_out, double *ms_out, void *stream,
+                                  int objective) {
     TMND_ARG_CHECK(g, "tmnd_autotune: NULL handle");
     cudaGetLastError();
-    float ms[NSHAPES];
+    float ms[NSHAPES] = {};
     int sh = 0;
-    const tmnd_status st = s16_autotune(g, nrhs, (cudaStream_t)stream, &sh, ms);
+    const tmnd_status st = s16_autotune(g, nrhs, (cudaStream_t)stream, &sh, ms, objective);
     if (st != TMND_OK) return st;
     if (shape_out) *shape_out = sh;
     if (ms_out)
         for (int i = 0; i < NSHAPES; i++) ms_out[i] = ms[i];
     return TMND_OK;
+}
+
+extern "C" tmnd_status tmnd_autotune(tmnd_gauge *g, int nrhs, int *shape_out, double *ms_out, void *stream) {
+    return autotune_entry(g, nrhs, shape_out, ms_out, stream, 0);
+}
+
+extern "C" tmnd_status tmnd_autotune_mms(tmnd_gauge *g, int nrhs, int *shape_out, double *ms_out, void *stream) {
+    return autotune_entry(g, nrhs, shape_out, ms_out, stream, 1);
 }
 
 extern "C" tmnd_status tmnd_s16_force_shape(int shape) {

@@ -881,7 +881,7 @@ static tmnd_status mms_sloppy(tmnd_gauge *g, const MixedWork &m, const double *s
     // any graph capture); every launch of the solve uses it, so the partial counts agree
     tmnd_status ts = s16_autotune(g, R, s, nullptr, nullptr);
     if (ts != TMND_OK) return ts;
-    const int shape = s16_shape(g->geom, R);
+    const int shape = s16_shape_mms(g->geom, R);
     const int nb_hop = hop_blocks_s16(g->geom, shape);
     const int nb_str = stream_blocks(n);
     const int nb_site = site_blocks(Vh);

@@ -269,8 +269,10 @@ struct S16Batch {
 // launch shapes of the 16-bit stencil and their autotuner (dslash_s16.cu)
 int hop_blocks_s16(const Geom &g, int shape);
 int hop_blocks_s16_max(const Geom &g);
-int s16_shape(const Geom &g, int nrhs);
-tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out, float *ms_out);
+int s16_shape(const Geom &g, int nrhs);      // variant for operator applications
+int s16_shape_mms(const Geom &g, int nrhs);  // variant for sloppy multi-shift iterations
+// objective 0: operator applications, 1: sloppy multi-shift iterations (both tuned together)
+tmnd_status s16_autotune(tmnd_gauge *g, int nrhs, cudaStream_t s, int *shape_out, float *ms_out, int objective = 0);
 void launch_hop_even_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In in, S16Out out, bool dag,
                          const int *done, cudaStream_t s, const S16Batch &bt = S16Batch());
 void launch_hop_odd_s16(const Geom &g, const SiteTermF &st, const int2 *links, S16In psi, S16In te, S16Out out,

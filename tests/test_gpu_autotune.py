@@ -35,6 +35,9 @@ def test_shapes_agree_bitwise_and_tuner_picks_one(dims, nrhs):
         assert np.array_equal(outs[sh], outs[0]), sh
     shape, ms = tm.tmnd_autotune(g.handle, nrhs)
     assert 0 <= shape < tm.S16_SHAPES and np.all(ms > 0) and ms[shape] == ms.min()
+    # the sloppy multi-shift iteration's objective, tuned in the same pass
+    shm, msm = tm.tmnd_autotune_mms(g.handle, nrhs)
+    assert 0 <= shm < tm.S16_SHAPES and np.all(msm > 0) and msm[shm] == msm.min()
     g.close()
 
 
