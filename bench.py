@@ -841,9 +841,10 @@ def run_study_mg(args):
     D_ND + i s gamma_5 tau_1 Pi_odd on a Gaussian full-lattice right-hand side, for minimal-
     residual smoothing (test vectors relaxed by 4 MR steps), SAP smoothing with the same
     vectors, and SAP after one round of adaptive setup; next to the mixed CG on the same shift.
-    With --kappa k1 k2 ..., the same for each hopping parameter (harder spectra as kappa grows
-    toward its critical value), SAP after the adaptive setup only, with the extreme Ritz values
-    of Qhat^2 from the CG history."""
+    With --kappa k1 k2 ..., the same for each hopping parameter (the spectrum of Qhat^2 moves
+    with kappa: the Wilson hops and the twisted-mass terms 2 kappa mu_bar, 2 kappa eps_bar all
+    scale with it), SAP after the adaptive setup only, with the extreme Ritz values of Qhat^2
+    from an FP64 CG history."""
     import numpy as np
     import torch
 
