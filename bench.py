@@ -202,6 +202,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_base_name(name):
+    """A kernel's bare function name from a demangled signature, e.g.
+    "void <unnamed>::k_hop_odd_s16<1, 3, 1, 128, 3>(Geom, ...)" -> "k_hop_odd_s16" (CUPTI writes
+    the anonymous namespace as "(anonymous namespace)::" or "<unnamed>::")."""
+    nm = name.replace("(anonymous namespace)::", "").replace("<unnamed>::", "")
+    return nm.split("(")[0].split("<")[0].split(" ")[-1]
+
+
 def count_kernels(fn, prefix=("k_",)):
     """Kernels of this library that one call of fn launches, counted from the CUDA
     activity trace of torch's profiler (CUPTI; kernels replayed inside CUDA graphs
@@ -214,10 +222,8 @@ def count_kernels(fn, prefix=("k_",)):
             torch.cuda.synchronize()
         n, names = 0, {}
         for ev in prof.events():
-            # CUPTI writes the anonymous namespace as "(anonymous namespace)::" or "<unnamed>::"
-            nm = (ev.name or "").replace("(anonymous namespace)::", "").replace("<unnamed>::", "")
             dev = str(getattr(ev, "device_type", ""))
-            base = nm.split("(")[0].split("<")[0].split(" ")[-1]
+            base = kernel_base_name(ev.name or "")
             if "CUDA" in dev and any(base.startswith(p) for p in prefix):
                 n += 1
                 names[base] = names.get(base, 0) + 1

@@ -74,3 +74,36 @@ def test_reference_arm_line(oracle_lib, monkeypatch):
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+
+
+def test_kernel_base_name_and_clock_parsing(tmp_path):
+    """Host helpers of the bench line: kernel names as CUPTI writes them, and the clock
+    record (median SM clock under load, throttle reasons seen) from nvidia-smi's CSV."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    for name, base in (("void <unnamed>::k_hop_odd_s16<1, 3, 1, 128, 3>(Geom, SiteTermF, const int2 *)",
+                        "k_hop_odd_s16"),
+                       ("<unnamed>::k_pupdate_s(int, const <unnamed>::MMSCoef *, unsigned long)", "k_pupdate_s"),
+                       ("void (anonymous namespace)::k_hop_even<double2, 1>(Geom, SiteTerm)", "k_hop_even"),
+                       ("k_resid32(long, const float2 *, const float2 *, float2 *, double *)", "k_resid32")):
+        assert bench.kernel_base_name(name) == base
+    cs = bench.ClockSampler.__new__(bench.ClockSampler)   # no nvidia-smi: feed a recorded CSV
+    f = open(tmp_path / "clocks.csv", "w+")
+    f.write("0, 2070, 2070, 700.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+            "0, 2055, 2070, 1300.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+            "0, 2070, 2070, 1310.2, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+            "garbled line\n")
+    f.flush()
+    cs.f, cs.p = f, None
+    assert cs.stop()["reasons"] == ["nvidia-smi unavailable"]
+    class _Done:                                          # a finished sampler process
+        def terminate(self):
+            pass
+
+        def wait(self):
+            return 0
+    cs.p = _Done()
+    rec = cs.stop()
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]
